@@ -1,0 +1,174 @@
+/*
+ * amfmm.h -- C ABI of the GB300 (sm_103a) angular-momentum-conserving
+ * Cartesian fast multipole method (Marcello 2017, arXiv:1706.06989, a
+ * modification of Dehnen 2000).
+ *
+ * Problem (Sec. 2): N bodies with positions X_n and masses mu_n; find every
+ * body's gravitational acceleration a_n = G sum_m mu_m (X_m - X_n)/|X_m - X_n|^3
+ * approximated by a symmetric (mutual) cell-cell expansion to order P = 3
+ * with the paper's torque-cancelling correction, so that the interactions
+ * conserve linear momentum (Eq. "unit") and angular momentum (Eq. 7 / Eq. 8,
+ * App. A) to rounding.
+ *
+ * Call sequence for one force solve (each call is enqueued on the context's
+ * CUDA stream; calls that must learn a size synchronise that stream and say
+ * so below):
+ *     fmm_build_tree -> fmm_upward -> fmm_interact -> fmm_downward -> fmm_forces
+ * A call out of this order returns FMM_EORDER.  fmm_solve runs all five.
+ *
+ * Memory: every pointer argument named "device" is CUDA device memory owned
+ * by the caller; the library never frees or retains it beyond the call,
+ * except that the body arrays given to fmm_build_tree are read again (not
+ * copied) by fmm_upward .. fmm_forces of the same solve and must stay
+ * unchanged until fmm_forces returns.  The context owns every internal
+ * buffer (tree, lists, expansion slots) and grows them on demand with
+ * cudaMalloc; they are released by fmm_destroy.
+ *
+ * Errors: every int-returning call returns FMM_OK (0) or a negative code;
+ * fmm_last_error gives a one-line message.  A failed call leaves the
+ * context usable for a new fmm_build_tree.  Input validation: n >= 1,
+ * 0 < theta <= 1 (Sec. 2), n_crit >= 1, order_P == 3; a body with a
+ * non-finite coordinate or a mass that is not positive and finite is
+ * detected on the device and reported as FMM_EINVAL by the next call that
+ * synchronises (fmm_build_tree).
+ *
+ * Units and conventions: G from fmm_opts (1 for the paper's units); an
+ * unsoftened 1/R potential; a pair of bodies (or cells) at zero separation
+ * contributes nothing.
+ */
+#ifndef AMFMM_H
+#define AMFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FMM_OK 0
+#define FMM_EINVAL (-1)       /* bad argument or bad body data */
+#define FMM_ENOMEM (-2)       /* device allocation failed */
+#define FMM_ECUDA (-3)        /* a CUDA call or kernel launch failed */
+#define FMM_ETIMEOUT (-4)     /* a bounded device wait expired */
+#define FMM_EORDER (-5)       /* call out of sequence */
+#define FMM_EUNSUPPORTED (-6) /* option not built */
+
+/* Variants of Sec. 3. */
+#define FMM_UC 0  /* uncorrected Dehnen (2000) expansion */
+#define FMM_TC 1  /* torque corrected with D_ijkl (Eq. 7) */
+#define FMM_TCO 2 /* torque corrected with the reduced D'_ijkl (Eq. 8) */
+
+/* Arithmetic of the interaction kernels. */
+#define FMM_FP64 0  /* every stage in FP64 */
+#define FMM_MIXED 1 /* near field and M2L in FP32 on cell-relative coordinates,
+                       FP64 tree geometry, moments and accumulation */
+
+typedef struct fmm_ctx fmm_ctx;
+
+typedef struct {
+  double theta;  /* opening angle, 0 < theta <= 1 (Sec. 2) */
+  int n_crit;    /* a cell with at most n_crit bodies is a leaf (Sec. 2: 25) */
+  int order_P;   /* expansion order; 3 (Eqs. 2-4) */
+  int variant;   /* FMM_UC, FMM_TC or FMM_TCO */
+  int precision; /* FMM_FP64 or FMM_MIXED */
+  double G;      /* gravitational constant applied to the accelerations */
+} fmm_opts;
+
+typedef struct {
+  int64_t n;          /* bodies */
+  int64_t ncell;      /* cells of the octree */
+  int64_t nleaf;      /* leaves */
+  int32_t depth;      /* deepest level (root = 0, at most 21) */
+  int64_t n_m2l;      /* accepted cell pairs (mutual M2L) */
+  int64_t n_p2p;      /* leaf pairs summed directly (mutual P2P) */
+  int64_t n_self;     /* leaves summed directly with themselves */
+  int64_t p2p_body_pairs; /* sum over leaf pairs of n_A n_B plus n(n-1)/2 per self leaf */
+  int64_t launches;   /* kernels launched by the last completed solve */
+  double lo[3];       /* bounding-cube origin used for the Morton keys */
+  double scale;       /* 2^21 / cube extent (0 for a cube of zero extent) */
+  /* per-stage device time in ms of the last solve, when timing is enabled
+     with fmm_set_timing: tree, upward, walk, m2l, p2p, reduce, downward */
+  float ms_tree, ms_upward, ms_walk, ms_m2l, ms_p2p, ms_reduce, ms_downward;
+} fmm_stats;
+
+/* Creates a context bound to `cuda_stream` (a cudaStream_t; NULL = the
+ * legacy default stream) on the current device.  *ctx is set on success. */
+int fmm_create(fmm_ctx **ctx, const fmm_opts *opts, void *cuda_stream);
+void fmm_destroy(fmm_ctx *ctx);
+const char *fmm_last_error(const fmm_ctx *ctx);
+/* Replaces the options between solves (theta, n_crit, variant, precision, G). */
+int fmm_set_opts(fmm_ctx *ctx, const fmm_opts *opts);
+/* 1: record CUDA events around every stage (fmm_get_stats reports them). */
+int fmm_set_timing(fmm_ctx *ctx, int enable);
+
+/* a1-a3 (Sec. 2, first paragraph): bounding cube, 63-bit Morton keys, stable
+ * radix sort by (key, index), octree whose leaves hold at most n_crit bodies
+ * (or sit at level 21), numbered breadth first.  x, y, z, m: device, n
+ * doubles each, caller order.  `theta` overrides opts.theta for this solve
+ * (pass 0 to keep it).  Synchronises the stream (the level sizes are read
+ * back). */
+int fmm_build_tree(fmm_ctx *ctx, const double *x, const double *y, const double *z,
+                   const double *m, int64_t n, double theta);
+
+/* a4 (Eqs. 1-3 and the octupole definition): per cell mass M, centre of
+ * mass Z, R_max (the largest body distance from Z) and moments about Z to
+ * order 3 (leaf P2M from bodies, then M2M shifts).  Asynchronous. */
+int fmm_upward(fmm_ctx *ctx);
+
+/* a5-a8: dual-tree walk under the opening criterion
+ * |Z_A - Z_B| >= (R_A,max + R_B,max)/theta (Sec. 2) producing the accepted
+ * cell pairs and the leaf pairs; mutual M2L of every accepted pair with the
+ * variant's corrective force (Eqs. 3, 4, 7, 8); mutual P2P of every leaf
+ * pair and self leaf; fixed-order segmented sums.  Synchronises the stream
+ * (list lengths are read back). */
+int fmm_interact(fmm_ctx *ctx);
+
+/* a9: L2L shift of the local expansions down the tree and L2P evaluation at
+ * every body, plus the near-field sums.  Asynchronous. */
+int fmm_downward(fmm_ctx *ctx);
+
+/* Writes the accelerations in the caller's body order.  ax, ay, az: device,
+ * n doubles each.  Asynchronous. */
+int fmm_forces(fmm_ctx *ctx, double *ax, double *ay, double *az);
+
+/* The five calls above in order (device pointers as above). */
+int fmm_solve(fmm_ctx *ctx, const double *x, const double *y, const double *z, const double *m,
+              int64_t n, double *ax, double *ay, double *az);
+
+/* The same solve from HOST arrays (pageable or pinned): copies the bodies to
+ * context-owned device buffers, solves, copies the accelerations back and
+ * synchronises the stream before returning. */
+int fmm_solve_host(fmm_ctx *ctx, const double *x, const double *y, const double *z,
+                   const double *m, int64_t n, double *ax, double *ay, double *az);
+
+/* Counts (and stage timings) of the last solve; synchronises the stream. */
+int fmm_get_stats(fmm_ctx *ctx, fmm_stats *out);
+
+/* ---- exports for bit-exact checks (device outputs, caller-sized from
+ *      fmm_get_stats; synchronise nothing) ---------------------------------- */
+
+/* keys: n uint64 (sorted); order: n int32 (sorted position -> caller index) */
+int fmm_export_keys(fmm_ctx *ctx, uint64_t *keys, int32_t *order);
+/* per cell (ncell each): begin, count, level, parent, first_child, nchild
+ * (int32), M, Rmax (double), Z (ncell x 3 double, row major) */
+int fmm_export_tree(fmm_ctx *ctx, int32_t *begin, int32_t *count, int32_t *level,
+                    int32_t *parent, int32_t *first_child, int32_t *nchild, double *M,
+                    double *Z, double *Rmax);
+/* moments about Z: ncell x 20 doubles in the order
+ * [M, Mx, My, Mz, Qxx, Qxy, Qxz, Qyy, Qyz, Qzz,
+ *  Oxxx, Oxxy, Oxxz, Oxyy, Oxyz, Oxzz, Oyyy, Oyyz, Oyzz, Ozzz] */
+int fmm_export_moments(fmm_ctx *ctx, double *mom);
+/* m2l: n_m2l x 2, p2p: n_p2p x 2 (each pair (min, max)), self: n_self;
+ * int32, in the library's processing order (sort them to compare) */
+int fmm_export_lists(fmm_ctx *ctx, int32_t *m2l, int32_t *p2p, int32_t *self);
+/* local expansion of every cell after the downward shift: ncell x 20
+ * doubles [C_x, C_y, C_z, C_xx, C_xy, C_xz, C_yy, C_yz, C_zz, C_xxx, C_xxy,
+ * C_xxz, C_xyy, C_xyz, C_xzz, C_yyy, C_yyz, C_yzz, C_zzz, 0]; a body at
+ * offset x from Z receives a = -(C_i + C_ij x_j + C_ijk x_j x_k / 2) plus its
+ * near-field sum. */
+int fmm_export_locals(fmm_ctx *ctx, double *C);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

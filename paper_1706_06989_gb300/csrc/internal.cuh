@@ -1,0 +1,158 @@
+// internal.cuh -- context, device buffers and launch helpers shared by the
+// translation units of libamfmm.so.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/amfmm.h"
+
+namespace amfmm {
+
+constexpr int kMaxLevel = 21;   // 63-bit Morton keys: 21 octal digits
+constexpr int kMomStride = 20;  // M, dipole(3), Q(6), O(10)
+constexpr int kLocStride = 20;  // C_i(3), C_ij(6), C_ijk(10), pad
+
+// Growable device buffer; contents are discarded on growth.
+struct DBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+
+struct Err {
+  int code = FMM_OK;
+  std::string msg;
+};
+
+// Per-solve sizes read back to the host.
+struct Sizes {
+  int64_t n = 0, ncell = 0, nleaf = 0, n_m2l = 0, n_p2p = 0, n_self = 0;
+  int depth = 0;
+  int key_which = 0;             // ping-pong slot holding the sorted keys
+  double lo[3] = {0, 0, 0}, scale = 0;
+  int64_t p2p_body_pairs = 0;
+  std::vector<int64_t> lvl_off;  // cells of level l are [lvl_off[l], lvl_off[l+1])
+};
+
+enum Stage { kNone = 0, kTree = 1, kUp = 2, kInteract = 3, kDown = 4 };
+
+enum TimerSlot {
+  kTreeBeg = 0, kTreeEnd, kUpBeg, kUpEnd, kWalkBeg, kWalkEnd, kM2LBeg, kM2LEnd,
+  kP2PBeg, kP2PEnd, kRedBeg, kRedEnd, kDownBeg, kDownEnd, kNumTimers
+};
+
+}  // namespace amfmm
+
+struct fmm_ctx {
+  fmm_opts opts{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  char errbuf[512] = {0};
+  int stage = amfmm::kNone;
+  bool timing = false;
+  cudaEvent_t ev[amfmm::kNumTimers] = {};
+  int64_t launches = 0, launches_last = 0;
+  float stage_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+
+  // solve inputs (caller-owned device memory)
+  const double *x = nullptr, *y = nullptr, *z = nullptr, *m = nullptr;
+  double theta = 0.5;
+  amfmm::Sizes sz;
+
+  // pinned host scratch for small read-backs
+  void *hpin = nullptr;
+
+  // ---- device buffers ----
+  // bodies
+  amfmm::DBuf key[2], idx[2], order, X, Y, Zb, Mb, cur, flag, incl, lcp, leaf_of, cell_at,
+      near, acc, status, bbox_part, bbox;
+  // cells
+  amfmm::DBuf begin, count, level, parent, first_child, nchild, S, M, Z, invM, Rmax,
+      rmax2, mom, loc, leaves;
+  // walk
+  amfmm::DBuf front[2], action, wcount, woff, m2l, p2p, self_list;
+  // M2L scatter
+  amfmm::DBuf ekey[2], eval[2], m2l_pos, m2l_off, m2l_slots;
+  // P2P grouping
+  amfmm::DBuf pkey[2], pval[2], p2p_A, p2p_offA, p2p_offB, p2p_pos, p2p_poff, p2p_len,
+      p2p_slots;
+  // scan / sort scratch; `totals` holds small device results (1 KiB):
+  // [0,16) scan totals, [64,72) near-field body-pair count, [96,104) slot total
+  amfmm::DBuf scan_tmp, sort_hist, totals;
+  // host-solve staging
+  amfmm::DBuf hx, hy, hz, hm, hax, hay, haz;
+};
+
+namespace amfmm {
+
+// ---------------------------------------------------------------------------
+// errors and allocation
+// ---------------------------------------------------------------------------
+int set_error(fmm_ctx *c, int code, const char *fmt, ...);
+
+#define AMFMM_CUDA(c, call)                                                              \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return ::amfmm::set_error((c), FMM_ECUDA, "%s failed: %s (%s:%d)", #call,          \
+                                cudaGetErrorString(e_), __FILE__, __LINE__);             \
+  } while (0)
+
+#define AMFMM_TRY(expr)        \
+  do {                         \
+    int rc_ = (expr);          \
+    if (rc_ != FMM_OK) return rc_; \
+  } while (0)
+
+int ensure_bytes(fmm_ctx *c, DBuf &b, size_t bytes);
+// Grows keeping the first `used` bytes.
+int ensure_keep_bytes(fmm_ctx *c, DBuf &b, size_t bytes, size_t used);
+
+template <class T>
+inline int ensure(fmm_ctx *c, DBuf &b, size_t count) {
+  return ensure_bytes(c, b, count * sizeof(T));
+}
+template <class T>
+inline T *ptr(DBuf &b) {
+  return static_cast<T *>(b.p);
+}
+
+// Checks the last launch and counts it.
+int launched(fmm_ctx *c, const char *what);
+
+inline unsigned grid_for(int64_t n, int block) {
+  return static_cast<unsigned>((n + block - 1) / block);
+}
+
+// ---------------------------------------------------------------------------
+// primitives (sort.cu)
+// ---------------------------------------------------------------------------
+// Exclusive prefix sums; `total` (device, 1 element) receives the sum.
+int exclusive_scan_i32(fmm_ctx *c, const int32_t *in, int32_t *out, int64_t n, int32_t *total);
+int exclusive_scan_i64(fmm_ctx *c, const int64_t *in, int64_t *out, int64_t n, int64_t *total);
+int exclusive_scan_i4(fmm_ctx *c, const int4 *in, int4 *out, int64_t n, int4 *total);
+// Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
+// Sorted data ends in buffer index *which (0 or 1) of the ping-pong pairs.
+int radix_sort_u64(fmm_ctx *c, DBuf key[2], DBuf val[2], int64_t n, int bits, int *which);
+int radix_sort_u32(fmm_ctx *c, DBuf key[2], DBuf val[2], int64_t n, int bits, int *which);
+
+// ---------------------------------------------------------------------------
+// stages
+// ---------------------------------------------------------------------------
+int build_tree(fmm_ctx *c);         // tree.cu
+int upward(fmm_ctx *c);             // tree.cu
+int walk(fmm_ctx *c);               // walk.cu
+int m2l(fmm_ctx *c);                // m2l.cu (lists -> per-cell locals)
+int p2p(fmm_ctx *c);                // p2p.cu (lists -> per-body near field)
+int downward(fmm_ctx *c);           // down.cu (L2L, L2P into sorted order)
+int forces(fmm_ctx *c, double *ax, double *ay, double *az);  // down.cu (caller order)
+
+void timer(fmm_ctx *c, int slot);
+
+}  // namespace amfmm

@@ -1,0 +1,297 @@
+// m2l.cu -- a7: mutual cell-cell interactions at expansion order 3 with the
+// torque-cancelling correction, and their fixed-order per-cell sums.
+//
+// For an accepted pair (A, B) with r = Z_A - Z_B (the vector from B's centre
+// of mass to A's; the Taylor series of Eqs. 2-4 is an expansion about this r)
+// and the derivatives of G = -1/R (Sec. 2)
+//     D_i   = r_i / R^3
+//     D_ij  = -3 r_i r_j / R^5 + d_ij / R^3
+//     D_ijk = 15 r_i r_j r_k / R^7 - 3 (d_ij r_k + d_jk r_i + d_ki r_j) / R^5,
+// Eq. (3) gives the acceleration of a body of A at offset x from Z_A as
+//     g_i = -(C_i + C_ij x_j + C_ijk x_j x_k / 2)
+// with C^A_i = M_B D_i + Q_B,jk D_ijk / 2, C^A_ij = M_B D_ij, C^A_ijk = M_B D_ijk,
+// and Eq. (4) gives the same form for B with
+//     C^B_i = -M_A D_i - Q_A,jk D_ijk / 2, C^B_ij = M_A D_ij, C^B_ijk = -M_A D_ijk.
+// (Q is the extensive quadrupole of Eq. 3; dipoles about the centres of mass
+// vanish and are dropped, as Sec. 2 notes.)  The contraction Q_jk D_ijk is
+// taken through r:  Q_jk D_ijk = 15 r_i (r.Q.r)/R^7 - 3 (2 (Q r)_i + r_i tr Q)/R^5.
+//
+// Torque correction (Eq. 7 with the coefficient of App. A at P = 3):
+//     F_i = (1/6) (M_A O_B,jkl - O_A,jkl M_B) D_ijkl,
+// applied as +F/M_A on A and -F/M_B on B (C^A_i -= F_i/M_A, C^B_i += F_i/M_B).
+// With S = M_A O_B - M_B O_A, u_i = S_ikl r_k r_l, t_i = S_ijj and
+// D_ijkl = -105 rrrr/R^9 + 15 (six d rr terms)/R^7 - 3 (three d d terms)/R^5,
+//     D_ijkl S_jkl = -105 r_i (r.u)/R^9 + 45 (u_i + r_i (r.t))/R^7 - 9 t_i/R^5.
+// The variant of Eq. (8) keeps only the terms of D'_ijkl (those without a
+// factor r_i):  D'_ijkl S_jkl = 45 u_i/R^7 - 9 t_i/R^5.
+//
+// Each pair writes its two local contributions into slots whose positions
+// were fixed by a stable sort of (cell, 2k + side); every cell then sums its
+// slots in that order.  No floating-point atomics: the result is
+// reproducible bit for bit.
+#include "internal.cuh"
+
+namespace amfmm {
+namespace {
+
+constexpr int kBlock = 128;
+
+__device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
+__device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
+
+// Local layout: Cx Cy Cz | Cxx Cxy Cxz Cyy Cyz Czz | Cxxx Cxxy Cxxz Cxyy Cxyz Cxzz Cyyy Cyyz Cyzz Czzz
+// Moment layout: M | Dx Dy Dz | Qxx Qxy Qxz Qyy Qyz Qzz | Oxxx ... Ozzz (same order as locals)
+template <class T, int VARIANT>
+__device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, T iMA, T iMB, const T *QA,
+                                         const T *QB, const T *OA, const T *OB, T *CA, T *CB) {
+  const T x = r[0], y = r[1], z = r[2];
+  const T xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+  const T R2 = xx + yy + zz;
+  const T Ri = rsqrt_t(R2);
+  const T Ri2 = Ri * Ri;
+  const T R3 = Ri * Ri2;   // R^-3
+  const T R5 = R3 * Ri2;   // R^-5
+  const T R7 = R5 * Ri2;   // R^-7
+  const T a2 = T(-3) * R5; // coefficient of r_i r_j in D_ij, of the d-terms in D_ijk
+  const T a3 = T(15) * R7; // coefficient of r_i r_j r_k in D_ijk
+  // D_i
+  const T D1[3] = {x * R3, y * R3, z * R3};
+  // D_ij
+  const T D2[6] = {a2 * xx + R3, a2 * xy, a2 * xz, a2 * yy + R3, a2 * yz, a2 * zz + R3};
+  // D_ijk
+  const T axx = a3 * xx, ayy = a3 * yy, azz = a3 * zz;
+  const T D3[10] = {(axx + T(3) * a2) * x, (axx + a2) * y, (axx + a2) * z, (ayy + a2) * x,
+                    a3 * xy * z,         (azz + a2) * x, (ayy + T(3) * a2) * y, (ayy + a2) * z,
+                    (azz + a2) * y,      (azz + T(3) * a2) * z};
+  // h = Q_jk D_ijk / 2 = r_i (a3 r.Q.r + a2 trQ)/2 + a2 (Q r)_i
+  T hA[3], hB[3];
+  {
+    const T *Q = QB;
+    const T qx = Q[0] * x + Q[1] * y + Q[2] * z;
+    const T qy = Q[1] * x + Q[3] * y + Q[4] * z;
+    const T qz = Q[2] * x + Q[4] * y + Q[5] * z;
+    const T u = T(0.5) * (a3 * (x * qx + y * qy + z * qz) + a2 * (Q[0] + Q[3] + Q[5]));
+    hB[0] = u * x + a2 * qx;
+    hB[1] = u * y + a2 * qy;
+    hB[2] = u * z + a2 * qz;
+  }
+  {
+    const T *Q = QA;
+    const T qx = Q[0] * x + Q[1] * y + Q[2] * z;
+    const T qy = Q[1] * x + Q[3] * y + Q[4] * z;
+    const T qz = Q[2] * x + Q[4] * y + Q[5] * z;
+    const T u = T(0.5) * (a3 * (x * qx + y * qy + z * qz) + a2 * (Q[0] + Q[3] + Q[5]));
+    hA[0] = u * x + a2 * qx;
+    hA[1] = u * y + a2 * qy;
+    hA[2] = u * z + a2 * qz;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    CA[i] = MB * D1[i] + hB[i];
+    CB[i] = -(MA * D1[i] + hA[i]);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    CA[3 + k] = MB * D2[k];
+    CB[3 + k] = MA * D2[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    CA[9 + k] = MB * D3[k];
+    CB[9 + k] = -(MA * D3[k]);
+  }
+  if (VARIANT != FMM_UC) {
+    // S = M_A O_B - M_B O_A (xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)
+    T S[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) S[k] = MA * OB[k] - MB * OA[k];
+    // u_i = S_ikl r_k r_l
+    const T ux = S[0] * xx + S[3] * yy + S[5] * zz + T(2) * (S[1] * xy + S[2] * xz + S[4] * yz);
+    const T uy = S[1] * xx + S[6] * yy + S[8] * zz + T(2) * (S[3] * xy + S[4] * xz + S[7] * yz);
+    const T uz = S[2] * xx + S[7] * yy + S[9] * zz + T(2) * (S[4] * xy + S[5] * xz + S[8] * yz);
+    // t_i = S_ijj
+    const T tx = S[0] + S[3] + S[5];
+    const T ty = S[1] + S[6] + S[8];
+    const T tz = S[2] + S[7] + S[9];
+    // F = (1/6) D S: (a3/2) u + (a2/2) t [+ r (-105 R^-9 r.u + 45 R^-7 r.t)/6 for TC]
+    const T ha3 = T(0.5) * a3, ha2 = T(0.5) * a2;
+    T F[3] = {ha3 * ux + ha2 * tx, ha3 * uy + ha2 * ty, ha3 * uz + ha2 * tz};
+    if (VARIANT == FMM_TC) {
+      const T R9 = R7 * Ri2;
+      const T w = (T(-17.5) * R9) * (x * ux + y * uy + z * uz) + ha3 * (x * tx + y * ty + z * tz);
+      F[0] += w * x;
+      F[1] += w * y;
+      F[2] += w * z;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      CA[i] -= F[i] * iMA;
+      CB[i] += F[i] * iMB;
+    }
+  }
+}
+
+// One thread per accepted pair.  Slots are kLocStride wide (19 used).
+template <class T, int VARIANT>
+__global__ void __launch_bounds__(kBlock) k_m2l(int64_t K, const int2 *__restrict__ pairs,
+                                                 const double *__restrict__ Z,
+                                                 const double *__restrict__ M,
+                                                 const double *__restrict__ invM,
+                                                 const double *__restrict__ mom,
+                                                 const int32_t *__restrict__ pos, T *__restrict__ slots) {
+  const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (k >= K) return;
+  const int A = pairs[k].x, B = pairs[k].y;
+  T CA[kLocStride], CB[kLocStride];
+  const double rx = Z[3 * A] - Z[3 * B], ry = Z[3 * A + 1] - Z[3 * B + 1], rz = Z[3 * A + 2] - Z[3 * B + 2];
+  if (rx == 0.0 && ry == 0.0 && rz == 0.0) {
+#pragma unroll
+    for (int q = 0; q < kLocStride; ++q) CA[q] = CB[q] = T(0);
+  } else {
+    const T r[3] = {T(rx), T(ry), T(rz)};
+    const double *mA = mom + static_cast<int64_t>(A) * kMomStride;
+    const double *mB = mom + static_cast<int64_t>(B) * kMomStride;
+    T QA[6], QB[6], OA[10], OB[10];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      QA[q] = T(mA[4 + q]);
+      QB[q] = T(mB[4 + q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+      OA[q] = VARIANT == FMM_UC ? T(0) : T(mA[10 + q]);
+      OB[q] = VARIANT == FMM_UC ? T(0) : T(mB[10 + q]);
+    }
+    m2l_pair<T, VARIANT>(r, T(M[A]), T(M[B]), T(invM[A]), T(invM[B]), QA, QB, OA, OB, CA, CB);
+    CA[19] = CB[19] = T(0);
+  }
+  T *sa = slots + static_cast<int64_t>(pos[2 * k]) * kLocStride;
+  T *sb = slots + static_cast<int64_t>(pos[2 * k + 1]) * kLocStride;
+#pragma unroll
+  for (int q = 0; q < kLocStride; ++q) {
+    sa[q] = CA[q];
+    sb[q] = CB[q];
+  }
+}
+
+// entries: (cell, 2k + side) for the stable sort
+__global__ void k_m2l_entries(int64_t K, const int2 *__restrict__ pairs, uint32_t *__restrict__ key,
+                              uint32_t *__restrict__ val, int32_t *__restrict__ cnt) {
+  const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (k >= K) return;
+  const int2 p = pairs[k];
+  key[2 * k] = static_cast<uint32_t>(p.x);
+  val[2 * k] = static_cast<uint32_t>(2 * k);
+  key[2 * k + 1] = static_cast<uint32_t>(p.y);
+  val[2 * k + 1] = static_cast<uint32_t>(2 * k + 1);
+  atomicAdd(&cnt[p.x], 1);
+  atomicAdd(&cnt[p.y], 1);
+}
+
+__global__ void k_inverse(int64_t E, const uint32_t *__restrict__ sval, int32_t *__restrict__ pos) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (s < E) pos[sval[s]] = static_cast<int32_t>(s);
+}
+
+// Every cell sums its slots in sorted (pair index) order.
+template <class T>
+__global__ void k_m2l_reduce(int32_t ncell, const int32_t *__restrict__ off, const T *__restrict__ slots,
+                             double *__restrict__ loc) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  double acc[kLocStride];
+#pragma unroll
+  for (int q = 0; q < kLocStride; ++q) acc[q] = 0.0;
+  for (int s = off[c]; s < off[c + 1]; ++s) {
+    const T *p = slots + static_cast<int64_t>(s) * kLocStride;
+#pragma unroll
+    for (int q = 0; q < kLocStride; ++q) acc[q] += static_cast<double>(p[q]);
+  }
+  double *o = loc + static_cast<int64_t>(c) * kLocStride;
+#pragma unroll
+  for (int q = 0; q < kLocStride; ++q) o[q] = acc[q];
+}
+
+template <class T>
+int launch_m2l(fmm_ctx *c, int64_t K, int32_t *pos, void *slots) {
+  const int2 *pairs = ptr<int2>(c->m2l);
+  const unsigned g = grid_for(K, kBlock);
+  cudaStream_t st = c->stream;
+  switch (c->opts.variant) {
+    case FMM_UC:
+      k_m2l<T, FMM_UC><<<g, kBlock, 0, st>>>(K, pairs, ptr<double>(c->Z), ptr<double>(c->M),
+                                              ptr<double>(c->invM), ptr<double>(c->mom), pos,
+                                              static_cast<T *>(slots));
+      break;
+    case FMM_TC:
+      k_m2l<T, FMM_TC><<<g, kBlock, 0, st>>>(K, pairs, ptr<double>(c->Z), ptr<double>(c->M),
+                                              ptr<double>(c->invM), ptr<double>(c->mom), pos,
+                                              static_cast<T *>(slots));
+      break;
+    default:
+      k_m2l<T, FMM_TCO><<<g, kBlock, 0, st>>>(K, pairs, ptr<double>(c->Z), ptr<double>(c->M),
+                                               ptr<double>(c->invM), ptr<double>(c->mom), pos,
+                                               static_cast<T *>(slots));
+      break;
+  }
+  return launched(c, "m2l");
+}
+
+int bits_for(int64_t v) {
+  int b = 1;
+  while ((int64_t(1) << b) <= v) ++b;
+  return b;
+}
+
+}  // namespace
+
+int m2l(fmm_ctx *c) {
+  cudaStream_t st = c->stream;
+  const int64_t K = c->sz.n_m2l, nc = c->sz.ncell, E = 2 * K;
+  AMFMM_TRY(ensure<double>(c, c->loc, static_cast<size_t>(kLocStride) * nc));
+  AMFMM_TRY(ensure<int32_t>(c, c->m2l_off, nc + 1));
+  if (E > 0x7fffffffLL) return set_error(c, FMM_EUNSUPPORTED, "too many M2L pairs (%lld)", (long long)K);
+  timer(c, kM2LBeg);
+  int32_t *off = ptr<int32_t>(c->m2l_off);
+  AMFMM_CUDA(c, cudaMemsetAsync(off, 0, sizeof(int32_t) * (nc + 1), st));
+  if (K > 0) {
+    AMFMM_TRY(ensure<uint32_t>(c, c->ekey[0], E));
+    AMFMM_TRY(ensure<uint32_t>(c, c->eval[0], E));
+    AMFMM_TRY(ensure<int32_t>(c, c->m2l_pos, E));
+    // counts go to off[] and are then scanned in place via incl scratch
+    AMFMM_TRY(ensure<int32_t>(c, c->incl, std::max<int64_t>(nc + 1, c->sz.n + 1)));
+    int32_t *cnt = ptr<int32_t>(c->incl);
+    AMFMM_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nc + 1), st));
+    k_m2l_entries<<<grid_for(K, 256), 256, 0, st>>>(K, ptr<int2>(c->m2l), ptr<uint32_t>(c->ekey[0]),
+                                                    ptr<uint32_t>(c->eval[0]), cnt);
+    AMFMM_TRY(launched(c, "m2l_entries"));
+    AMFMM_TRY(exclusive_scan_i32(c, cnt, off, nc + 1, nullptr));
+    int which = 0;
+    AMFMM_TRY(radix_sort_u32(c, c->ekey, c->eval, E, bits_for(nc), &which));
+    k_inverse<<<grid_for(E, 256), 256, 0, st>>>(E, ptr<uint32_t>(c->eval[which]), ptr<int32_t>(c->m2l_pos));
+    AMFMM_TRY(launched(c, "m2l_inverse"));
+    const bool fp32 = c->opts.precision == FMM_MIXED;
+    const size_t esz = fp32 ? sizeof(float) : sizeof(double);
+    AMFMM_TRY(ensure_bytes(c, c->m2l_slots, static_cast<size_t>(E) * kLocStride * esz));
+    if (fp32) AMFMM_TRY(launch_m2l<float>(c, K, ptr<int32_t>(c->m2l_pos), c->m2l_slots.p));
+    else AMFMM_TRY(launch_m2l<double>(c, K, ptr<int32_t>(c->m2l_pos), c->m2l_slots.p));
+    timer(c, kM2LEnd);
+    timer(c, kRedBeg);
+    if (fp32)
+      k_m2l_reduce<float><<<grid_for(nc, 128), 128, 0, st>>>(static_cast<int32_t>(nc), off,
+                                                              ptr<float>(c->m2l_slots), ptr<double>(c->loc));
+    else
+      k_m2l_reduce<double><<<grid_for(nc, 128), 128, 0, st>>>(static_cast<int32_t>(nc), off,
+                                                               ptr<double>(c->m2l_slots), ptr<double>(c->loc));
+    AMFMM_TRY(launched(c, "m2l_reduce"));
+    timer(c, kRedEnd);
+  } else {
+    AMFMM_CUDA(c, cudaMemsetAsync(c->loc.p, 0, sizeof(double) * kLocStride * nc, st));
+    timer(c, kM2LEnd);
+    timer(c, kRedBeg);
+    timer(c, kRedEnd);
+  }
+  return FMM_OK;
+}
+
+}  // namespace amfmm

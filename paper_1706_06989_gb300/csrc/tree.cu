@@ -1,0 +1,567 @@
+// tree.cu -- a1-a4: bounding cube, Morton keys, sort, octree, centres of mass,
+// R_max and moments.
+//
+// Sec. 2 of the paper: the bodies are decomposed into an oct-tree whose cells
+// hold at most n_crit bodies; the opening criterion uses each cell's centre
+// of mass Z and R_max, the largest distance from one of its bodies to Z.
+// Because the interaction lists depend on exact comparisons of Z and R_max,
+// every operation on that path is an explicitly rounded FP64 operation in a
+// fixed order (no FMA contraction): leaf sums run over the bodies in sorted
+// order, other cells sum their children in octant order, Z = S / M, and R_max
+// is the exact maximum over the cell's bodies.
+#include "internal.cuh"
+
+namespace amfmm {
+namespace {
+
+constexpr int kBlock = 256;
+
+// ---------------------------------------------------------------------------
+// a1: bounding cube and keys
+// ---------------------------------------------------------------------------
+__global__ void k_bbox_partial(const double *__restrict__ x, const double *__restrict__ y,
+                               const double *__restrict__ z, const double *__restrict__ m,
+                               int64_t n, double *__restrict__ part, int *__restrict__ status) {
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  bool bad = false;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double p[3] = {x[i], y[i], z[i]};
+    const double mi = m[i];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      bad |= !isfinite(p[d]);
+      lo[d] = fmin(lo[d], p[d]);
+      hi[d] = fmax(hi[d], p[d]);
+    }
+    bad |= !(mi > 0.0) || !isfinite(mi);
+  }
+  if (bad) atomicOr(status, 1);
+  __shared__ double sh[6][kBlock / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+      hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+    }
+    if (lane == 0) {
+      sh[d][w] = lo[d];
+      sh[3 + d][w] = hi[d];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int k = threadIdx.x;
+    double v = sh[k][0];
+    for (int q = 1; q < kBlock / 32; ++q) v = k < 3 ? fmin(v, sh[k][q]) : fmax(v, sh[k][q]);
+    part[blockIdx.x * 6 + k] = v;
+  }
+}
+
+// bbox[0..2] = lo, bbox[3] = scale = 2^21 / ext (0 when ext == 0)
+__global__ void k_bbox_final(const double *__restrict__ part, int nb, double *__restrict__ bbox) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = part[d];
+    hi[d] = part[3 + d];
+  }
+  for (int b = 1; b < nb; ++b)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = fmin(lo[d], part[b * 6 + d]);
+      hi[d] = fmax(hi[d], part[b * 6 + 3 + d]);
+    }
+  double ext = __dsub_rn(hi[0], lo[0]);
+  ext = fmax(ext, __dsub_rn(hi[1], lo[1]));
+  ext = fmax(ext, __dsub_rn(hi[2], lo[2]));
+  for (int d = 0; d < 3; ++d) bbox[d] = lo[d];
+  bbox[3] = ext > 0.0 ? __ddiv_rn(2097152.0, ext) : 0.0;
+}
+
+__device__ __forceinline__ uint64_t quantise(double v, double lo, double scale) {
+  double t = __dmul_rn(__dsub_rn(v, lo), scale);
+  double f = floor(t);
+  f = fmin(f, 2097151.0);
+  return static_cast<uint64_t>(f);
+}
+
+// bit b of q -> bit 3b
+__device__ __forceinline__ uint64_t spread3(uint64_t q) {
+  q &= 0x1fffffull;
+  q = (q | (q << 32)) & 0x1f00000000ffffull;
+  q = (q | (q << 16)) & 0x1f0000ff0000ffull;
+  q = (q | (q << 8)) & 0x100f00f00f00f00full;
+  q = (q | (q << 4)) & 0x10c30c30c30c30c3ull;
+  q = (q | (q << 2)) & 0x1249249249249249ull;
+  return q;
+}
+
+__global__ void k_keys(const double *__restrict__ x, const double *__restrict__ y,
+                       const double *__restrict__ z, int64_t n, const double *__restrict__ bbox,
+                       uint64_t *__restrict__ key, uint32_t *__restrict__ idx) {
+  int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const double s = bbox[3];
+  uint64_t qx = quantise(x[i], bbox[0], s), qy = quantise(y[i], bbox[1], s),
+           qz = quantise(z[i], bbox[2], s);
+  key[i] = spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
+  idx[i] = static_cast<uint32_t>(i);
+}
+
+// Gather the bodies into key order; lcp[s] = octal digits shared by keys s-1, s.
+__global__ void k_permute(const double *__restrict__ x, const double *__restrict__ y,
+                          const double *__restrict__ z, const double *__restrict__ m,
+                          const uint64_t *__restrict__ key, const uint32_t *__restrict__ idx,
+                          int64_t n, double *__restrict__ X, double *__restrict__ Y,
+                          double *__restrict__ Zb, double *__restrict__ Mb,
+                          int32_t *__restrict__ order, int32_t *__restrict__ lcp,
+                          int32_t *__restrict__ cur) {
+  int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (s >= n) return;
+  const uint32_t o = idx[s];
+  X[s] = x[o];
+  Y[s] = y[o];
+  Zb[s] = z[o];
+  Mb[s] = m[o];
+  order[s] = static_cast<int32_t>(o);
+  int l = 0;
+  if (s > 0) {
+    uint64_t d = key[s - 1] ^ key[s];
+    l = d == 0 ? kMaxLevel : (__clzll(static_cast<long long>(d)) - 1) / 3;
+  }
+  lcp[s] = l;
+  cur[s] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// a3: octree, one level per pass
+// ---------------------------------------------------------------------------
+// A body starts a child cell at level lev+1 when its cell at level lev is split
+// and it is the cell's first body or its key differs from its predecessor's
+// in digit lev+1.
+__global__ void k_level_flags(int64_t n, int lev, int n_crit, const int32_t *__restrict__ lcp,
+                              const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+                              const int32_t *__restrict__ cur, int32_t *__restrict__ flag,
+                              int32_t *__restrict__ cell_at_lev, int32_t *__restrict__ leaf_of) {
+  int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const int c = cur[i];
+  cell_at_lev[i] = c;
+  int f = 0;
+  if (c >= 0) {
+    const bool leaf = count[c] <= n_crit || lev == kMaxLevel;
+    if (leaf) leaf_of[i] = c;
+    else f = (i == begin[c]) || (lcp[i] == lev);
+  }
+  flag[i] = f;
+}
+
+__global__ void k_make_cells(int64_t n, int lev, int32_t off, const int32_t *__restrict__ flag,
+                             const int32_t *__restrict__ excl, const int32_t *__restrict__ cur,
+                             int32_t *__restrict__ begin, int32_t *__restrict__ level,
+                             int32_t *__restrict__ parent, int32_t *__restrict__ first_child,
+                             int32_t *__restrict__ nchild) {
+  int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n || !flag[i]) return;
+  const int c = cur[i];
+  const int id = off + excl[i];
+  begin[id] = static_cast<int32_t>(i);
+  level[id] = lev + 1;
+  parent[id] = c;
+  first_child[id] = -1;
+  nchild[id] = 0;
+  if (i == begin[c]) first_child[c] = id;
+}
+
+__global__ void k_cell_counts(int32_t off, int32_t nnew, int32_t *__restrict__ begin,
+                              int32_t *__restrict__ count, const int32_t *__restrict__ parent,
+                              int32_t *__restrict__ nchild) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnew) return;
+  const int id = off + k;
+  const int p = parent[id];
+  int end = begin[p] + count[p];
+  if (k + 1 < nnew) end = min(end, begin[id + 1]);
+  count[id] = end - begin[id];
+  atomicAdd(&nchild[p], 1);
+}
+
+__global__ void k_update_cur(int64_t n, int32_t off, const int32_t *__restrict__ flag,
+                             const int32_t *__restrict__ excl, int32_t *__restrict__ cur) {
+  int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  if (cur[i] < 0) return;
+  // Bodies of leaves were retired; a body of a split cell moves to the child
+  // that starts at the last flagged body at or before it (same cell).
+  cur[i] = off + excl[i] + flag[i] - 1;
+}
+
+// cur[i] after k_update_cur must be -1 for bodies of leaves: mark them first
+__global__ void k_retire_leaf_bodies(int64_t n, int lev, int n_crit, const int32_t *__restrict__ count,
+                                     int32_t *__restrict__ cur) {
+  int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const int c = cur[i];
+  if (c >= 0 && (count[c] <= n_crit || lev == kMaxLevel)) cur[i] = -1;
+}
+
+__global__ void k_leaf_flags(int32_t ncell, const int32_t *__restrict__ nchild, int32_t *__restrict__ f) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < ncell) f[c] = nchild[c] == 0;
+}
+__global__ void k_leaf_compact(int32_t ncell, const int32_t *__restrict__ nchild,
+                               const int32_t *__restrict__ excl, int32_t *__restrict__ leaves) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < ncell && nchild[c] == 0) leaves[excl[c]] = c;
+}
+
+// ---------------------------------------------------------------------------
+// a4: centres of mass, moments, R_max
+// ---------------------------------------------------------------------------
+// Moments about Z in the order M, x, y, z, xx, xy, xz, yy, yz, zz, xxx, xxy,
+// xxz, xyy, xyz, xzz, yyy, yyz, yzz, zzz.
+__device__ __forceinline__ void add_body_moments(double *mo, double mu, double x, double y, double z) {
+  const double mx = mu * x, my = mu * y, mz = mu * z;
+  mo[0] += mu;
+  mo[1] += mx;
+  mo[2] += my;
+  mo[3] += mz;
+  const double mxx = mx * x, mxy = mx * y, mxz = mx * z, myy = my * y, myz = my * z, mzz = mz * z;
+  mo[4] += mxx;
+  mo[5] += mxy;
+  mo[6] += mxz;
+  mo[7] += myy;
+  mo[8] += myz;
+  mo[9] += mzz;
+  mo[10] += mxx * x;
+  mo[11] += mxx * y;
+  mo[12] += mxx * z;
+  mo[13] += myy * x;
+  mo[14] += mxy * z;
+  mo[15] += mzz * x;
+  mo[16] += myy * y;
+  mo[17] += myy * z;
+  mo[18] += mzz * y;
+  mo[19] += mzz * z;
+}
+
+__global__ void k_leaf_upward(int32_t nleaf, const int32_t *__restrict__ leaves,
+                              const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+                              const double *__restrict__ X, const double *__restrict__ Y,
+                              const double *__restrict__ Zb, const double *__restrict__ Mb,
+                              double *__restrict__ S, double *__restrict__ M, double *__restrict__ Z,
+                              double *__restrict__ invM, double *__restrict__ mom) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nleaf) return;
+  const int c = leaves[q];
+  const int b = begin[c], e = b + count[c];
+  double sx = 0.0, sy = 0.0, sz = 0.0, mm = 0.0;
+  for (int i = b; i < e; ++i) {
+    const double mu = Mb[i];
+    sx = __dadd_rn(sx, __dmul_rn(mu, X[i]));
+    sy = __dadd_rn(sy, __dmul_rn(mu, Y[i]));
+    sz = __dadd_rn(sz, __dmul_rn(mu, Zb[i]));
+    mm = __dadd_rn(mm, mu);
+  }
+  const double zx = __ddiv_rn(sx, mm), zy = __ddiv_rn(sy, mm), zz = __ddiv_rn(sz, mm);
+  S[3 * c] = sx;
+  S[3 * c + 1] = sy;
+  S[3 * c + 2] = sz;
+  M[c] = mm;
+  Z[3 * c] = zx;
+  Z[3 * c + 1] = zy;
+  Z[3 * c + 2] = zz;
+  invM[c] = 1.0 / mm;
+  double mo[kMomStride];
+#pragma unroll
+  for (int k = 0; k < kMomStride; ++k) mo[k] = 0.0;
+  for (int i = b; i < e; ++i) add_body_moments(mo, Mb[i], X[i] - zx, Y[i] - zy, Zb[i] - zz);
+  mo[0] = mm;
+  double *out = mom + static_cast<int64_t>(c) * kMomStride;
+#pragma unroll
+  for (int k = 0; k < kMomStride; ++k) out[k] = mo[k];
+}
+
+// One level of internal cells: S, M from the children in octant order, then
+// the moments shifted from each child centre to Z (M2M, exact algebra):
+//   with s = Z_child - Z,
+//   D_i   += D_i' + M' s_i
+//   Q_ij  += Q_ij' + D_i' s_j + D_j' s_i + M' s_i s_j
+//   O_ijk += O_ijk' + (Q_ij' s_k + Q_ik' s_j + Q_jk' s_i)
+//            + (D_i' s_j s_k + D_j' s_i s_k + D_k' s_i s_j) + M' s_i s_j s_k
+__global__ void k_internal_upward(int32_t c0, int32_t c1, const int32_t *__restrict__ first_child,
+                                  const int32_t *__restrict__ nchild, double *__restrict__ S,
+                                  double *__restrict__ M, double *__restrict__ Z,
+                                  double *__restrict__ invM, double *__restrict__ mom) {
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= c1) return;
+  const int nch = nchild[c];
+  if (nch == 0) return;
+  const int f = first_child[c];
+  double sx = 0.0, sy = 0.0, sz = 0.0, mm = 0.0;
+  for (int k = f; k < f + nch; ++k) {
+    sx = __dadd_rn(sx, S[3 * k]);
+    sy = __dadd_rn(sy, S[3 * k + 1]);
+    sz = __dadd_rn(sz, S[3 * k + 2]);
+    mm = __dadd_rn(mm, M[k]);
+  }
+  const double zx = __ddiv_rn(sx, mm), zy = __ddiv_rn(sy, mm), zz = __ddiv_rn(sz, mm);
+  S[3 * c] = sx;
+  S[3 * c + 1] = sy;
+  S[3 * c + 2] = sz;
+  M[c] = mm;
+  Z[3 * c] = zx;
+  Z[3 * c + 1] = zy;
+  Z[3 * c + 2] = zz;
+  invM[c] = 1.0 / mm;
+  double p[kMomStride];
+#pragma unroll
+  for (int k = 0; k < kMomStride; ++k) p[k] = 0.0;
+  for (int k = f; k < f + nch; ++k) {
+    const double *q = mom + static_cast<int64_t>(k) * kMomStride;
+    const double s[3] = {Z[3 * k] - zx, Z[3 * k + 1] - zy, Z[3 * k + 2] - zz};
+    const double Mc = q[0];
+    const double D[3] = {q[1], q[2], q[3]};
+    // symmetric Q' as a full matrix
+    const double Q[3][3] = {{q[4], q[5], q[6]}, {q[5], q[7], q[8]}, {q[6], q[8], q[9]}};
+    p[0] += Mc;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) p[1 + i] += D[i] + Mc * s[i];
+    // Q: xx xy xz yy yz zz
+    const int qi[6] = {0, 0, 0, 1, 1, 2}, qj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+      const int i = qi[t], j = qj[t];
+      p[4 + t] += Q[i][j] + D[i] * s[j] + D[j] * s[i] + Mc * s[i] * s[j];
+    }
+    // O: xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
+    const int oi[10] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 2};
+    const int oj[10] = {0, 0, 0, 1, 1, 2, 1, 1, 2, 2};
+    const int ok[10] = {0, 1, 2, 1, 2, 2, 1, 2, 2, 2};
+#pragma unroll
+    for (int t = 0; t < 10; ++t) {
+      const int i = oi[t], j = oj[t], l = ok[t];
+      p[10 + t] += q[10 + t] + (Q[i][j] * s[l] + Q[i][l] * s[j] + Q[j][l] * s[i]) +
+                   (D[i] * s[j] * s[l] + D[j] * s[i] * s[l] + D[l] * s[i] * s[j]) +
+                   Mc * s[i] * s[j] * s[l];
+    }
+  }
+  p[0] = mm;
+  double *out = mom + static_cast<int64_t>(c) * kMomStride;
+#pragma unroll
+  for (int k = 0; k < kMomStride; ++k) out[k] = p[k];
+}
+
+// R_max^2 of every cell: for each level, each body's squared distance to the
+// centre of its cell at that level; a segmented warp maximum (bodies of one
+// cell are contiguous) and one atomicMax per segment on the bit pattern
+// (monotone for non-negative doubles).  max is exact, so the order of
+// combination does not matter.
+__global__ void k_rmax_bodies(int64_t n, const int32_t *__restrict__ cell_at,
+                              const double *__restrict__ X, const double *__restrict__ Y,
+                              const double *__restrict__ Zb, const double *__restrict__ Z,
+                              unsigned long long *__restrict__ rmax2) {
+  const int lev = blockIdx.y;
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int c = -1;
+  double d2 = 0.0;
+  if (i < n) {
+    c = cell_at[static_cast<int64_t>(lev) * n + i];
+    if (c >= 0) {
+      const double dx = __dsub_rn(X[i], Z[3 * c]);
+      const double dy = __dsub_rn(Y[i], Z[3 * c + 1]);
+      const double dz = __dsub_rn(Zb[i], Z[3 * c + 2]);
+      d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double v = __shfl_down_sync(0xffffffffu, d2, o);
+    const int co = __shfl_down_sync(0xffffffffu, c, o);
+    if (lane + o < 32 && co == c) d2 = fmax(d2, v);
+  }
+  const int cprev = __shfl_up_sync(0xffffffffu, c, 1);
+  const bool head = (lane == 0) || (cprev != c);
+  if (c >= 0 && head) atomicMax(&rmax2[c], static_cast<unsigned long long>(__double_as_longlong(d2)));
+}
+
+__global__ void k_rmax_final(int32_t ncell, const unsigned long long *__restrict__ rmax2,
+                             double *__restrict__ Rmax) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < ncell) Rmax[c] = __dsqrt_rn(__longlong_as_double(static_cast<long long>(rmax2[c])));
+}
+
+int ensure_cells(fmm_ctx *c, int64_t need, int64_t used) {
+  DBuf *ib[] = {&c->begin, &c->count, &c->level, &c->parent, &c->first_child, &c->nchild};
+  for (DBuf *b : ib) AMFMM_TRY(ensure_keep_bytes(c, *b, need * sizeof(int32_t), used * sizeof(int32_t)));
+  return FMM_OK;
+}
+
+}  // namespace
+
+int build_tree(fmm_ctx *c) {
+  const int64_t n = c->sz.n;
+  cudaStream_t st = c->stream;
+  // body buffers
+  AMFMM_TRY(ensure<uint64_t>(c, c->key[0], n));
+  AMFMM_TRY(ensure<uint32_t>(c, c->idx[0], n));
+  AMFMM_TRY(ensure<double>(c, c->X, n));
+  AMFMM_TRY(ensure<double>(c, c->Y, n));
+  AMFMM_TRY(ensure<double>(c, c->Zb, n));
+  AMFMM_TRY(ensure<double>(c, c->Mb, n));
+  AMFMM_TRY(ensure<int32_t>(c, c->order, n));
+  AMFMM_TRY(ensure<int32_t>(c, c->cur, n));
+  AMFMM_TRY(ensure<int32_t>(c, c->flag, n));
+  AMFMM_TRY(ensure<int32_t>(c, c->incl, n + 1));
+  AMFMM_TRY(ensure<int32_t>(c, c->leaf_of, n));
+  AMFMM_TRY(ensure<int32_t>(c, c->cell_at, static_cast<size_t>(kMaxLevel + 1) * n));
+  AMFMM_TRY(ensure<int>(c, c->status, 4));
+  const int nbb = std::max(1, std::min<int>(c->num_sms * 4, static_cast<int>((n + kBlock - 1) / kBlock)));
+  AMFMM_TRY(ensure<double>(c, c->bbox_part, 6 * nbb));
+  AMFMM_TRY(ensure<double>(c, c->bbox, 8));
+  
+
+  int *status = ptr<int>(c->status);
+  AMFMM_CUDA(c, cudaMemsetAsync(status, 0, sizeof(int) * 4, st));
+  k_bbox_partial<<<nbb, kBlock, 0, st>>>(c->x, c->y, c->z, c->m, n, ptr<double>(c->bbox_part), status);
+  AMFMM_TRY(launched(c, "bbox_partial"));
+  k_bbox_final<<<1, 32, 0, st>>>(ptr<double>(c->bbox_part), nbb, ptr<double>(c->bbox));
+  AMFMM_TRY(launched(c, "bbox_final"));
+  k_keys<<<grid_for(n, kBlock), kBlock, 0, st>>>(c->x, c->y, c->z, n, ptr<double>(c->bbox),
+                                                 ptr<uint64_t>(c->key[0]), ptr<uint32_t>(c->idx[0]));
+  AMFMM_TRY(launched(c, "keys"));
+  int which = 0;
+  AMFMM_TRY(radix_sort_u64(c, c->key, c->idx, n, 63, &which));
+  const uint64_t *skey = ptr<uint64_t>(c->key[which]);
+  const uint32_t *sidx = ptr<uint32_t>(c->idx[which]);
+  AMFMM_TRY(ensure<int32_t>(c, c->lcp, n));
+  int32_t *lcp = ptr<int32_t>(c->lcp);
+  k_permute<<<grid_for(n, kBlock), kBlock, 0, st>>>(c->x, c->y, c->z, c->m, skey, sidx, n,
+                                                    ptr<double>(c->X), ptr<double>(c->Y),
+                                                    ptr<double>(c->Zb), ptr<double>(c->Mb),
+                                                    ptr<int32_t>(c->order), lcp, ptr<int32_t>(c->cur));
+  AMFMM_TRY(launched(c, "permute"));
+  c->sz.key_which = which;
+
+  // octree level by level
+  int64_t cap_cells = std::max<int64_t>(1024, n / 2 + 64);
+  AMFMM_TRY(ensure_cells(c, cap_cells, 0));
+  {
+    // root
+    int32_t root[6] = {0, static_cast<int32_t>(n), 0, -1, -1, 0};
+    int32_t *h = static_cast<int32_t *>(c->hpin);
+    for (int k = 0; k < 6; ++k) h[k] = root[k];
+    DBuf *ib[] = {&c->begin, &c->count, &c->level, &c->parent, &c->first_child, &c->nchild};
+    for (int k = 0; k < 6; ++k)
+      AMFMM_CUDA(c, cudaMemcpyAsync(ib[k]->p, h + k, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  }
+  c->sz.lvl_off.assign({0, 1});
+  int32_t *flag = ptr<int32_t>(c->flag);
+  int32_t *excl = ptr<int32_t>(c->incl);
+  int32_t *total = ptr<int32_t>(c->totals);
+  int lev = 0;
+  for (;; ++lev) {
+    const int64_t off = c->sz.lvl_off.back();
+    k_level_flags<<<grid_for(n, kBlock), kBlock, 0, st>>>(
+        n, lev, c->opts.n_crit, lcp, ptr<int32_t>(c->begin), ptr<int32_t>(c->count),
+        ptr<int32_t>(c->cur), flag, ptr<int32_t>(c->cell_at) + static_cast<int64_t>(lev) * n,
+        ptr<int32_t>(c->leaf_of));
+    AMFMM_TRY(launched(c, "level_flags"));
+    AMFMM_TRY(exclusive_scan_i32(c, flag, excl, n, total));
+    int32_t *h = static_cast<int32_t *>(c->hpin);
+    AMFMM_CUDA(c, cudaMemcpyAsync(h, total, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    AMFMM_CUDA(c, cudaStreamSynchronize(st));
+    const int64_t nnew = h[0];
+    if (nnew == 0) break;
+    if (off + nnew > cap_cells) {
+      int64_t want = std::max<int64_t>(cap_cells * 2, off + nnew + 1024);
+      AMFMM_TRY(ensure_cells(c, want, off));
+      cap_cells = want;
+    }
+    k_make_cells<<<grid_for(n, kBlock), kBlock, 0, st>>>(
+        n, lev, static_cast<int32_t>(off), flag, excl, ptr<int32_t>(c->cur), ptr<int32_t>(c->begin),
+        ptr<int32_t>(c->level), ptr<int32_t>(c->parent), ptr<int32_t>(c->first_child),
+        ptr<int32_t>(c->nchild));
+    AMFMM_TRY(launched(c, "make_cells"));
+    k_cell_counts<<<grid_for(nnew, kBlock), kBlock, 0, st>>>(
+        static_cast<int32_t>(off), static_cast<int32_t>(nnew), ptr<int32_t>(c->begin),
+        ptr<int32_t>(c->count), ptr<int32_t>(c->parent), ptr<int32_t>(c->nchild));
+    AMFMM_TRY(launched(c, "cell_counts"));
+    k_retire_leaf_bodies<<<grid_for(n, kBlock), kBlock, 0, st>>>(n, lev, c->opts.n_crit,
+                                                                 ptr<int32_t>(c->count), ptr<int32_t>(c->cur));
+    AMFMM_TRY(launched(c, "retire_leaf_bodies"));
+    k_update_cur<<<grid_for(n, kBlock), kBlock, 0, st>>>(n, static_cast<int32_t>(off), flag, excl,
+                                                         ptr<int32_t>(c->cur));
+    AMFMM_TRY(launched(c, "update_cur"));
+    c->sz.lvl_off.push_back(off + nnew);
+  }
+  c->sz.depth = lev;
+  c->sz.ncell = c->sz.lvl_off.back();
+  // leaves in id order
+  const int64_t nc = c->sz.ncell;
+  AMFMM_TRY(ensure<int32_t>(c, c->leaves, nc + 1));
+  // a tree of single-child chains can have more cells than bodies
+  AMFMM_TRY(ensure<int32_t>(c, c->flag, std::max(n, nc) + 1));
+  AMFMM_TRY(ensure<int32_t>(c, c->incl, std::max(n, nc) + 1));
+  flag = ptr<int32_t>(c->flag);
+  excl = ptr<int32_t>(c->incl);
+  k_leaf_flags<<<grid_for(nc, kBlock), kBlock, 0, st>>>(static_cast<int32_t>(nc), ptr<int32_t>(c->nchild), flag);
+  AMFMM_TRY(launched(c, "leaf_flags"));
+  AMFMM_TRY(exclusive_scan_i32(c, flag, excl, nc, total));
+  k_leaf_compact<<<grid_for(nc, kBlock), kBlock, 0, st>>>(static_cast<int32_t>(nc), ptr<int32_t>(c->nchild),
+                                                          excl, ptr<int32_t>(c->leaves));
+  AMFMM_TRY(launched(c, "leaf_compact"));
+  {
+    int32_t *h = static_cast<int32_t *>(c->hpin);
+    AMFMM_CUDA(c, cudaMemcpyAsync(h, total, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    AMFMM_CUDA(c, cudaMemcpyAsync(h + 1, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    double *hb = reinterpret_cast<double *>(h + 4);
+    AMFMM_CUDA(c, cudaMemcpyAsync(hb, c->bbox.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    AMFMM_CUDA(c, cudaStreamSynchronize(st));
+    c->sz.nleaf = h[0];
+    for (int d = 0; d < 3; ++d) c->sz.lo[d] = hb[d];
+    c->sz.scale = hb[3];
+    if (h[1] != 0)
+      return set_error(c, FMM_EINVAL, "a body has a non-finite coordinate or a mass that is not positive and finite");
+  }
+  return FMM_OK;
+}
+
+int upward(fmm_ctx *c) {
+  const int64_t n = c->sz.n, nc = c->sz.ncell;
+  cudaStream_t st = c->stream;
+  AMFMM_TRY(ensure<double>(c, c->S, 3 * nc));
+  AMFMM_TRY(ensure<double>(c, c->M, nc));
+  AMFMM_TRY(ensure<double>(c, c->Z, 3 * nc));
+  AMFMM_TRY(ensure<double>(c, c->invM, nc));
+  AMFMM_TRY(ensure<double>(c, c->Rmax, nc));
+  AMFMM_TRY(ensure<unsigned long long>(c, c->rmax2, nc));
+  AMFMM_TRY(ensure<double>(c, c->mom, static_cast<size_t>(kMomStride) * nc));
+  k_leaf_upward<<<grid_for(c->sz.nleaf, 128), 128, 0, st>>>(
+      static_cast<int32_t>(c->sz.nleaf), ptr<int32_t>(c->leaves), ptr<int32_t>(c->begin),
+      ptr<int32_t>(c->count), ptr<double>(c->X), ptr<double>(c->Y), ptr<double>(c->Zb),
+      ptr<double>(c->Mb), ptr<double>(c->S), ptr<double>(c->M), ptr<double>(c->Z),
+      ptr<double>(c->invM), ptr<double>(c->mom));
+  AMFMM_TRY(launched(c, "leaf_upward"));
+  for (int lev = c->sz.depth - 1; lev >= 0; --lev) {
+    const int64_t c0 = c->sz.lvl_off[lev], c1 = c->sz.lvl_off[lev + 1];
+    k_internal_upward<<<grid_for(c1 - c0, 128), 128, 0, st>>>(
+        static_cast<int32_t>(c0), static_cast<int32_t>(c1), ptr<int32_t>(c->first_child),
+        ptr<int32_t>(c->nchild), ptr<double>(c->S), ptr<double>(c->M), ptr<double>(c->Z),
+        ptr<double>(c->invM), ptr<double>(c->mom));
+    AMFMM_TRY(launched(c, "internal_upward"));
+  }
+  AMFMM_CUDA(c, cudaMemsetAsync(c->rmax2.p, 0, sizeof(unsigned long long) * nc, st));
+  dim3 g(grid_for(n, kBlock), static_cast<unsigned>(c->sz.depth + 1));
+  k_rmax_bodies<<<g, kBlock, 0, st>>>(n, ptr<int32_t>(c->cell_at), ptr<double>(c->X), ptr<double>(c->Y),
+                                      ptr<double>(c->Zb), ptr<double>(c->Z),
+                                      ptr<unsigned long long>(c->rmax2));
+  AMFMM_TRY(launched(c, "rmax_bodies"));
+  k_rmax_final<<<grid_for(nc, kBlock), kBlock, 0, st>>>(static_cast<int32_t>(nc),
+                                                        ptr<unsigned long long>(c->rmax2), ptr<double>(c->Rmax));
+  return launched(c, "rmax_final");
+}
+
+}  // namespace amfmm

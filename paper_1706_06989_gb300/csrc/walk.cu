@@ -1,0 +1,200 @@
+// walk.cu -- a5, a6: the dual-tree walk of Dehnen (2000) under the opening
+// criterion of Sec. 2,
+//     |Z_A - Z_B| >= (R_A,max + R_B,max) / theta,
+// evaluated as theta^2 |Z_A - Z_B|^2 >= (R_A,max + R_B,max)^2 (equality
+// accepted) with explicitly rounded FP64 operations, so that the GPU and any
+// serial evaluation of the same expression agree bit for bit.
+//
+// Rules for a pair of cells (A, B):
+//   A == B, leaf        -> the leaf is summed directly with itself;
+//   A == B, not a leaf  -> (c_i, c_i) for every child and (c_i, c_j), i < j;
+//   accepted            -> one mutual M2L interaction;
+//   both leaves         -> one mutual P2P interaction;
+//   otherwise           -> split one cell (the non-leaf if only one is; else
+//                          the larger R_max, then the shallower, then the
+//                          smaller id) and visit (child, other) for each child.
+// The set of emitted pairs depends only on these per-pair decisions, so it is
+// independent of the traversal order.  The walk proceeds one generation of
+// pairs at a time; an exclusive scan of the per-pair output counts places
+// every output, which makes the list order deterministic.
+#include "internal.cuh"
+
+namespace amfmm {
+namespace {
+
+constexpr int kBlock = 256;
+
+enum Action : int32_t { kSelfLeaf = 0, kSelfSplit = 1, kAccept = 2, kNear = 3, kSplitA = 4, kSplitB = 5 };
+
+__device__ __forceinline__ bool well_separated(int A, int B, const double *__restrict__ Z,
+                                               const double *__restrict__ Rmax, double theta) {
+  const double dx = __dsub_rn(Z[3 * A], Z[3 * B]);
+  const double dy = __dsub_rn(Z[3 * A + 1], Z[3 * B + 1]);
+  const double dz = __dsub_rn(Z[3 * A + 2], Z[3 * B + 2]);
+  const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  const double th2 = __dmul_rn(theta, theta);
+  const double s = __dadd_rn(Rmax[A], Rmax[B]);
+  return __dmul_rn(th2, d2) >= __dmul_rn(s, s);
+}
+
+__global__ void k_classify(int64_t nf, const int2 *__restrict__ front, const int32_t *__restrict__ nchild,
+                           const int32_t *__restrict__ level, const double *__restrict__ Z,
+                           const double *__restrict__ Rmax, double theta, int32_t *__restrict__ action,
+                           int4 *__restrict__ counts) {
+  int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= nf) return;
+  const int A = front[t].x, B = front[t].y;
+  int act;
+  int4 cnt = make_int4(0, 0, 0, 0);
+  if (A == B) {
+    const int k = nchild[A];
+    if (k == 0) {
+      act = kSelfLeaf;
+      cnt.w = 1;
+    } else {
+      act = kSelfSplit;
+      cnt.x = k + k * (k - 1) / 2;
+    }
+  } else if (well_separated(A, B, Z, Rmax, theta)) {
+    act = kAccept;
+    cnt.y = 1;
+  } else {
+    const int ka = nchild[A], kb = nchild[B];
+    if (ka == 0 && kb == 0) {
+      act = kNear;
+      cnt.z = 1;
+    } else {
+      bool pickA;
+      if (kb == 0) pickA = true;
+      else if (ka == 0) pickA = false;
+      else {
+        const double ra = Rmax[A], rb = Rmax[B];
+        if (ra != rb) pickA = ra > rb;
+        else if (level[A] != level[B]) pickA = level[A] < level[B];
+        else pickA = A < B;
+      }
+      act = pickA ? kSplitA : kSplitB;
+      cnt.x = pickA ? ka : kb;
+    }
+  }
+  action[t] = act;
+  counts[t] = cnt;
+}
+
+__global__ void k_emit(int64_t nf, const int2 *__restrict__ front, const int32_t *__restrict__ action,
+                       const int4 *__restrict__ offs, const int32_t *__restrict__ first_child,
+                       const int32_t *__restrict__ nchild, int2 *__restrict__ next,
+                       int2 *__restrict__ m2l, int64_t m2l_base, int2 *__restrict__ p2p,
+                       int64_t p2p_base, int32_t *__restrict__ self, int64_t self_base) {
+  int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= nf) return;
+  const int A = front[t].x, B = front[t].y;
+  const int4 o = offs[t];
+  switch (action[t]) {
+    case kSelfLeaf:
+      self[self_base + o.w] = A;
+      break;
+    case kSelfSplit: {
+      const int f = first_child[A], k = nchild[A];
+      int q = o.x;
+      for (int i = 0; i < k; ++i) next[q++] = make_int2(f + i, f + i);
+      for (int i = 0; i < k; ++i)
+        for (int j = i + 1; j < k; ++j) next[q++] = make_int2(f + i, f + j);
+      break;
+    }
+    case kAccept:
+      m2l[m2l_base + o.y] = make_int2(min(A, B), max(A, B));
+      break;
+    case kNear:
+      p2p[p2p_base + o.z] = make_int2(min(A, B), max(A, B));
+      break;
+    case kSplitA: {
+      const int f = first_child[A], k = nchild[A];
+      for (int i = 0; i < k; ++i) next[o.x + i] = make_int2(f + i, B);
+      break;
+    }
+    default: {
+      const int f = first_child[B], k = nchild[B];
+      for (int i = 0; i < k; ++i) next[o.x + i] = make_int2(A, f + i);
+      break;
+    }
+  }
+}
+
+}  // namespace
+
+int walk(fmm_ctx *c) {
+  cudaStream_t st = c->stream;
+  const int64_t n = c->sz.n;
+  int64_t cap_front = std::max<int64_t>(4096, n / 4);
+  AMFMM_TRY(ensure<int2>(c, c->front[0], cap_front));
+  AMFMM_TRY(ensure<int2>(c, c->front[1], cap_front));
+  int64_t cap_m2l = c->m2l.cap / sizeof(int2), cap_p2p = c->p2p.cap / sizeof(int2),
+          cap_self = c->self_list.cap / sizeof(int32_t);
+  if (cap_m2l < 1024) {
+    cap_m2l = std::max<int64_t>(1024, 8 * n);
+    AMFMM_TRY(ensure<int2>(c, c->m2l, cap_m2l));
+  }
+  if (cap_p2p < 1024) {
+    cap_p2p = std::max<int64_t>(1024, 2 * n);
+    AMFMM_TRY(ensure<int2>(c, c->p2p, cap_p2p));
+  }
+  if (cap_self < 1024) {
+    cap_self = std::max<int64_t>(1024, n / 4 + 64);
+    AMFMM_TRY(ensure<int32_t>(c, c->self_list, cap_self));
+  }
+
+  int4 *total = ptr<int4>(c->totals);
+  {
+    int2 root = make_int2(0, 0);
+    int2 *h = static_cast<int2 *>(c->hpin);
+    *h = root;
+    AMFMM_CUDA(c, cudaMemcpyAsync(c->front[0].p, h, sizeof(int2), cudaMemcpyHostToDevice, st));
+  }
+  int64_t nf = 1, n_m2l = 0, n_p2p = 0, n_self = 0;
+  int cur = 0;
+  while (nf > 0) {
+    AMFMM_TRY(ensure<int32_t>(c, c->action, nf));
+    AMFMM_TRY(ensure<int4>(c, c->wcount, nf));
+    AMFMM_TRY(ensure<int4>(c, c->woff, nf));
+    k_classify<<<grid_for(nf, kBlock), kBlock, 0, st>>>(
+        nf, ptr<int2>(c->front[cur]), ptr<int32_t>(c->nchild), ptr<int32_t>(c->level),
+        ptr<double>(c->Z), ptr<double>(c->Rmax), c->theta, ptr<int32_t>(c->action), ptr<int4>(c->wcount));
+    AMFMM_TRY(launched(c, "walk_classify"));
+    AMFMM_TRY(exclusive_scan_i4(c, ptr<int4>(c->wcount), ptr<int4>(c->woff), nf, total));
+    int4 *h = static_cast<int4 *>(c->hpin);
+    AMFMM_CUDA(c, cudaMemcpyAsync(h, total, sizeof(int4), cudaMemcpyDeviceToHost, st));
+    AMFMM_CUDA(c, cudaStreamSynchronize(st));
+    const int4 tot = *h;
+    if (tot.x > 0 && tot.x > static_cast<int64_t>(c->front[cur ^ 1].cap / sizeof(int2)))
+      AMFMM_TRY(ensure<int2>(c, c->front[cur ^ 1], std::max<int64_t>(tot.x, 2 * (c->front[cur ^ 1].cap / sizeof(int2)))));
+    if (n_m2l + tot.y > cap_m2l) {
+      cap_m2l = std::max<int64_t>(2 * cap_m2l, n_m2l + tot.y);
+      AMFMM_TRY(ensure_keep_bytes(c, c->m2l, cap_m2l * sizeof(int2), n_m2l * sizeof(int2)));
+    }
+    if (n_p2p + tot.z > cap_p2p) {
+      cap_p2p = std::max<int64_t>(2 * cap_p2p, n_p2p + tot.z);
+      AMFMM_TRY(ensure_keep_bytes(c, c->p2p, cap_p2p * sizeof(int2), n_p2p * sizeof(int2)));
+    }
+    if (n_self + tot.w > cap_self) {
+      cap_self = std::max<int64_t>(2 * cap_self, n_self + tot.w);
+      AMFMM_TRY(ensure_keep_bytes(c, c->self_list, cap_self * sizeof(int32_t), n_self * sizeof(int32_t)));
+    }
+    k_emit<<<grid_for(nf, kBlock), kBlock, 0, st>>>(
+        nf, ptr<int2>(c->front[cur]), ptr<int32_t>(c->action), ptr<int4>(c->woff),
+        ptr<int32_t>(c->first_child), ptr<int32_t>(c->nchild), ptr<int2>(c->front[cur ^ 1]),
+        ptr<int2>(c->m2l), n_m2l, ptr<int2>(c->p2p), n_p2p, ptr<int32_t>(c->self_list), n_self);
+    AMFMM_TRY(launched(c, "walk_emit"));
+    n_m2l += tot.y;
+    n_p2p += tot.z;
+    n_self += tot.w;
+    nf = tot.x;
+    cur ^= 1;
+  }
+  c->sz.n_m2l = n_m2l;
+  c->sz.n_p2p = n_p2p;
+  c->sz.n_self = n_self;
+  return FMM_OK;
+}
+
+}  // namespace amfmm

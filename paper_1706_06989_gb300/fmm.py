@@ -1,0 +1,291 @@
+"""Thin ctypes binding of libamfmm.so (the C ABI of include/amfmm.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the current CUDA stream.  The
+binding raises if the library has not been built; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libamfmm.so")
+
+FMM_OK, FMM_EINVAL, FMM_ENOMEM, FMM_ECUDA, FMM_ETIMEOUT, FMM_EORDER, FMM_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+UC, TC, TCO = 0, 1, 2
+FP64, MIXED = 0, 1
+VARIANTS = {"UC": UC, "TC": TC, "TCO": TCO}
+PRECISIONS = {"fp64": FP64, "mixed": MIXED}
+MOMENT_NAMES = ["M", "x", "y", "z", "xx", "xy", "xz", "yy", "yz", "zz", "xxx", "xxy", "xxz", "xyy",
+                "xyz", "xzz", "yyy", "yyz", "yzz", "zzz"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FMMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_double), ("n_crit", ctypes.c_int), ("order_P", ctypes.c_int),
+                ("variant", ctypes.c_int), ("precision", ctypes.c_int), ("G", ctypes.c_double)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("ncell", ctypes.c_int64), ("nleaf", ctypes.c_int64),
+                ("depth", ctypes.c_int32), ("n_m2l", ctypes.c_int64), ("n_p2p", ctypes.c_int64),
+                ("n_self", ctypes.c_int64), ("p2p_body_pairs", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("lo", ctypes.c_double * 3), ("scale", ctypes.c_double),
+                ("ms_tree", ctypes.c_float), ("ms_upward", ctypes.c_float), ("ms_walk", ctypes.c_float),
+                ("ms_m2l", ctypes.c_float), ("ms_p2p", ctypes.c_float), ("ms_reduce", ctypes.c_float),
+                ("ms_downward", ctypes.c_float)]
+
+
+def load() -> ctypes.CDLL:
+    """Loads libamfmm.so from the package directory (raises if absent)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+            lib = ctypes.CDLL(LIB_PATH)
+            P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+            sig = {
+                "fmm_create": [ctypes.POINTER(P), ctypes.POINTER(_Opts), P],
+                "fmm_set_opts": [P, ctypes.POINTER(_Opts)],
+                "fmm_set_timing": [P, I],
+                "fmm_build_tree": [P, P, P, P, P, I64, D],
+                "fmm_upward": [P],
+                "fmm_interact": [P],
+                "fmm_downward": [P],
+                "fmm_forces": [P, P, P, P],
+                "fmm_solve": [P, P, P, P, P, I64, P, P, P],
+                "fmm_solve_host": [P, P, P, P, P, I64, P, P, P],
+                "fmm_get_stats": [P, ctypes.POINTER(_Stats)],
+                "fmm_export_keys": [P, P, P],
+                "fmm_export_tree": [P, P, P, P, P, P, P, P, P, P],
+                "fmm_export_moments": [P, P],
+                "fmm_export_lists": [P, P, P, P],
+                "fmm_export_locals": [P, P],
+            }
+            for name, args in sig.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = I
+            lib.fmm_destroy.argtypes = [P]
+            lib.fmm_destroy.restype = None
+            lib.fmm_last_error.argtypes = [P]
+            lib.fmm_last_error.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+def _dptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class Stats:
+    n: int
+    ncell: int
+    nleaf: int
+    depth: int
+    n_m2l: int
+    n_p2p: int
+    n_self: int
+    p2p_body_pairs: int
+    launches: int
+    lo: tuple
+    scale: float
+    ms: dict
+
+
+class FMM:
+    """One solver context on the current CUDA device and stream.
+
+    ``FMM(theta=0.5, n_crit=25, variant="TC", precision="fp64", G=1.0)``;
+    ``solve(x, y, z, m)`` takes float64 CUDA tensors (caller order) and returns
+    the accelerations (ax, ay, az).  The five stage methods mirror the C ABI.
+    """
+
+    def __init__(self, theta: float = 0.5, n_crit: int = 25, variant="TC", precision="fp64",
+                 G: float = 1.0, order_P: int = 3, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load()
+        self.opts = _Opts(float(theta), int(n_crit), int(order_P),
+                          VARIANTS[variant] if isinstance(variant, str) else int(variant),
+                          PRECISIONS[precision] if isinstance(precision, str) else int(precision), float(G))
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        h = ctypes.c_void_p()
+        rc = self.lib.fmm_create(ctypes.byref(h), ctypes.byref(self.opts), ctypes.c_void_p(s.cuda_stream))
+        if rc != FMM_OK:
+            raise FMMError(rc, "fmm_create failed")
+        self._h = h
+        self._bodies = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.fmm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int, what: str):
+        if rc != FMM_OK:
+            msg = self.lib.fmm_last_error(self._h)
+            raise FMMError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def set_opts(self, theta=None, n_crit=None, variant=None, precision=None, G=None):
+        o = self.opts
+        if theta is not None:
+            o.theta = float(theta)
+        if n_crit is not None:
+            o.n_crit = int(n_crit)
+        if variant is not None:
+            o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        if precision is not None:
+            o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        if G is not None:
+            o.G = float(G)
+        self._check(self.lib.fmm_set_opts(self._h, ctypes.byref(o)), "fmm_set_opts")
+
+    def set_timing(self, on: bool = True):
+        self._check(self.lib.fmm_set_timing(self._h, int(bool(on))), "fmm_set_timing")
+
+    # ---- stages ------------------------------------------------------------
+    def _as_dev(self, a):
+        t = self._torch
+        a = a if isinstance(a, t.Tensor) else t.as_tensor(a)
+        if a.dtype != t.float64 or not a.is_cuda or not a.is_contiguous():
+            raise ValueError("body arrays must be contiguous float64 CUDA tensors")
+        return a
+
+    def build_tree(self, x, y, z, m, theta: float = 0.0):
+        x, y, z, m = (self._as_dev(a) for a in (x, y, z, m))
+        n = x.shape[0]
+        if not (y.shape[0] == z.shape[0] == m.shape[0] == n):
+            raise ValueError("x, y, z, m must have the same length")
+        self._bodies = (x, y, z, m)  # read again by the later stages
+        self._check(self.lib.fmm_build_tree(self._h, _dptr(x), _dptr(y), _dptr(z), _dptr(m), n,
+                                            float(theta)), "fmm_build_tree")
+
+    def upward(self):
+        self._check(self.lib.fmm_upward(self._h), "fmm_upward")
+
+    def interact(self):
+        self._check(self.lib.fmm_interact(self._h), "fmm_interact")
+
+    def downward(self):
+        self._check(self.lib.fmm_downward(self._h), "fmm_downward")
+
+    def forces(self, out=None):
+        t = self._torch
+        n = self._bodies[0].shape[0]
+        if out is None:
+            out = tuple(t.empty(n, dtype=t.float64, device=self._bodies[0].device) for _ in range(3))
+        self._check(self.lib.fmm_forces(self._h, *(_dptr(o) for o in out)), "fmm_forces")
+        return out
+
+    def solve(self, x, y, z, m, out=None):
+        x, y, z, m = (self._as_dev(a) for a in (x, y, z, m))
+        t = self._torch
+        n = x.shape[0]
+        if out is None:
+            out = tuple(t.empty(n, dtype=t.float64, device=x.device) for _ in range(3))
+        self._bodies = (x, y, z, m)
+        self._check(self.lib.fmm_solve(self._h, _dptr(x), _dptr(y), _dptr(z), _dptr(m), n,
+                                       *(_dptr(o) for o in out)), "fmm_solve")
+        return out
+
+    def solve_host(self, x, y, z, m, out=None):
+        """Solve from host arrays (numpy float64 or pinned CPU tensors)."""
+        import numpy as np
+
+        def hp(a):
+            if isinstance(a, np.ndarray):
+                if a.dtype != np.float64 or not a.flags.c_contiguous:
+                    raise ValueError("host arrays must be contiguous float64")
+                return ctypes.c_void_p(a.ctypes.data)
+            return ctypes.c_void_p(a.data_ptr())
+
+        n = x.shape[0]
+        if out is None:
+            out = tuple(np.empty(n) for _ in range(3))
+        self._check(self.lib.fmm_solve_host(self._h, hp(x), hp(y), hp(z), hp(m), n, *(hp(o) for o in out)),
+                    "fmm_solve_host")
+        return out
+
+    # ---- introspection -------------------------------------------------------
+    def stats(self) -> Stats:
+        s = _Stats()
+        self._check(self.lib.fmm_get_stats(self._h, ctypes.byref(s)), "fmm_get_stats")
+        ms = {k: float(getattr(s, "ms_" + k)) for k in ("tree", "upward", "walk", "m2l", "p2p", "reduce",
+                                                         "downward")}
+        return Stats(s.n, s.ncell, s.nleaf, s.depth, s.n_m2l, s.n_p2p, s.n_self, s.p2p_body_pairs,
+                     s.launches, tuple(s.lo), s.scale, ms)
+
+    def export_keys(self):
+        t = self._torch
+        n = self._bodies[0].shape[0]
+        dev = self._bodies[0].device
+        keys = t.empty(n, dtype=t.int64, device=dev)
+        order = t.empty(n, dtype=t.int32, device=dev)
+        self._check(self.lib.fmm_export_keys(self._h, _dptr(keys), _dptr(order)), "fmm_export_keys")
+        return keys, order
+
+    def export_tree(self, geometry: bool = True):
+        t = self._torch
+        st = self.stats()
+        nc = st.ncell
+        dev = self._bodies[0].device
+        ints = [t.empty(nc, dtype=t.int32, device=dev) for _ in range(6)]
+        if geometry:
+            M = t.empty(nc, dtype=t.float64, device=dev)
+            Z = t.empty((nc, 3), dtype=t.float64, device=dev)
+            R = t.empty(nc, dtype=t.float64, device=dev)
+            g = [_dptr(M), _dptr(Z), _dptr(R)]
+        else:
+            M = Z = R = None
+            g = [None, None, None]
+        self._check(self.lib.fmm_export_tree(self._h, *(_dptr(a) for a in ints), *g), "fmm_export_tree")
+        names = ["begin", "count", "level", "parent", "first_child", "nchild"]
+        out = dict(zip(names, ints))
+        out.update(M=M, Z=Z, Rmax=R)
+        return out
+
+    def export_moments(self):
+        t = self._torch
+        nc = self.stats().ncell
+        mom = t.empty((nc, 20), dtype=t.float64, device=self._bodies[0].device)
+        self._check(self.lib.fmm_export_moments(self._h, _dptr(mom)), "fmm_export_moments")
+        return mom
+
+    def export_lists(self):
+        t = self._torch
+        st = self.stats()
+        dev = self._bodies[0].device
+        m2l = t.empty((max(st.n_m2l, 1), 2), dtype=t.int32, device=dev)
+        p2p = t.empty((max(st.n_p2p, 1), 2), dtype=t.int32, device=dev)
+        slf = t.empty(max(st.n_self, 1), dtype=t.int32, device=dev)
+        self._check(self.lib.fmm_export_lists(self._h, _dptr(m2l), _dptr(p2p), _dptr(slf)), "fmm_export_lists")
+        return m2l[:st.n_m2l], p2p[:st.n_p2p], slf[:st.n_self]
+
+    def export_locals(self):
+        t = self._torch
+        nc = self.stats().ncell
+        C = t.empty((nc, 20), dtype=t.float64, device=self._bodies[0].device)
+        self._check(self.lib.fmm_export_locals(self._h, _dptr(C)), "fmm_export_locals")
+        return C

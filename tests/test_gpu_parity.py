@@ -1,0 +1,243 @@
+"""CUDA path against the CPU oracle, through the C ABI (needs a GB300).
+
+Bit-exact: Morton keys, sort order, tree topology, M, Z, R_max (the opening
+criterion consumes them) and the interaction lists after a canonical sort.
+FP64 accelerations: within 1e-12 relative per body.  Conservation: net force
+and torque balance (Sec. 3 metric) at rounding level for TC / TCO.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1706_06989_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _dev(b):
+    return tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (b.x, b.y, b.z, b.m))
+
+
+def _solver(**kw):
+    from paper_1706_06989_gb300 import fmm
+    return fmm.FMM(**kw)
+
+
+def _solve(b, theta=0.5, n_crit=25, variant="TC", precision="fp64"):
+    s = _solver(theta=theta, n_crit=n_crit, variant=variant, precision=precision)
+    x, y, z, m = _dev(b)
+    ax, ay, az = s.solve(x, y, z, m)
+    torch.cuda.synchronize()
+    return s, torch.stack([ax, ay, az], 1).cpu().numpy()
+
+
+def _canon_pairs(p):
+    p = np.asarray(p, dtype=np.int64).reshape(-1, 2)
+    lo, hi = np.minimum(p[:, 0], p[:, 1]), np.maximum(p[:, 0], p[:, 1])
+    k = lo * (1 << 32) + hi
+    return np.sort(k)
+
+
+def _rel_dev(got, ref):
+    return np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+
+
+def _compare_tree(s, o):
+    st = s.stats()
+    assert st.ncell == o.ncell
+    key, order = s.export_keys()
+    okey, oorder, lo, scale = o.keys()
+    assert np.array_equal(key.cpu().numpy().view(np.uint64), okey)
+    assert np.array_equal(order.cpu().numpy(), oorder)
+    assert np.array_equal(np.array(st.lo), lo) and st.scale == scale
+    t = s.export_tree()
+    oc = o.cells()
+    for name in ("begin", "count", "level", "parent", "first_child", "nchild"):
+        assert np.array_equal(t[name].cpu().numpy(), getattr(oc, name)), name
+    M, Z, R, mom = o.geometry()
+    # bit-exact: compare the IEEE bit patterns
+    assert np.array_equal(t["M"].cpu().numpy().view(np.int64), M.view(np.int64))
+    assert np.array_equal(t["Z"].cpu().numpy().view(np.int64), Z.view(np.int64))
+    assert np.array_equal(t["Rmax"].cpu().numpy().view(np.int64), R.view(np.int64))
+    return mom
+
+
+def _compare_lists(s, o):
+    m2l, p2p, slf = s.export_lists()
+    om2l, op2p, oslf = o.lists()
+    assert np.array_equal(_canon_pairs(m2l.cpu().numpy()), _canon_pairs(om2l))
+    assert np.array_equal(_canon_pairs(p2p.cpu().numpy()), _canon_pairs(op2p))
+    assert np.array_equal(np.sort(slf.cpu().numpy()), np.sort(oslf))
+
+
+@pytest.mark.parametrize("variant", ["UC", "TC", "TCO"])
+def test_plummer_2000_matches_oracle(variant):
+    b = ics.plummer(2000, seed=0)
+    s, got = _solve(b, variant=variant)
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25)
+    _compare_tree(s, o)
+    _compare_lists(s, o)
+    ref = o.accel(variant)
+    rel = _rel_dev(got, ref)
+    assert rel.max() <= 1e-12, rel.max()
+    fb, tb = oracle.balance(b.x, b.y, b.z, b.m, got)
+    assert fb <= 1e-13
+    if variant != "UC":
+        assert tb <= 1e-13
+
+
+def test_moments_match_definition():
+    b = ics.plummer(2000, seed=3)
+    s, _ = _solve(b)
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25)
+    _, _, R, omom = o.geometry()
+    mom = s.export_moments().cpu().numpy()
+    M = mom[:, 0]
+    # the oracle's multi-index order for orders 0..3 equals the library layout
+    for n_ord, sl in ((1, slice(1, 4)), (2, slice(4, 10)), (3, slice(10, 20))):
+        ref = omom[:, sl]
+        tol = 1e-12 * (M * np.maximum(R, 1e-300) ** n_ord)[:, None] + 1e-300
+        assert np.all(np.abs(mom[:, sl] - ref) <= tol), n_ord
+
+
+def test_uniform_masses_spread_65536():
+    b = ics.uniform_cube(65536, seed=5, mass_spread=True)
+    s, got = _solve(b, theta=0.6, variant="TC")
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.6, 25)
+    _compare_tree(s, o)
+    _compare_lists(s, o)
+    t = ics.error_subset(b.n, 2048, seed=7)
+    ref = o.accel("TC", targets=t)
+    assert _rel_dev(got[t], ref).max() <= 1e-12
+
+
+def test_deterministic_bits():
+    b = ics.plummer(30000, seed=2)
+    s = _solver(theta=0.5, n_crit=25, variant="TC")
+    x, y, z, m = _dev(b)
+    a1 = torch.stack(s.solve(x, y, z, m), 1).clone()
+    a2 = torch.stack(s.solve(x, y, z, m), 1).clone()
+    assert torch.equal(a1.view(torch.int64), a2.view(torch.int64))
+
+
+def test_host_entry_point_matches_device():
+    b = ics.plummer(5000, seed=4)
+    s, got = _solve(b)
+    hx = s.solve_host(b.x, b.y, b.z, b.m)
+    assert np.array_equal(np.stack(hx, 1), got)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 25, 26, 200])
+def test_small_n_against_direct(n):
+    b = ics.plummer(n, seed=11)
+    s, got = _solve(b, theta=0.5)
+    ref = oracle.direct(b.x, b.y, b.z, b.m)
+    if n == 1:
+        assert np.all(got == 0.0)
+        return
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25)
+    assert _rel_dev(got, o.accel("TC")).max() <= 1e-12
+    if n <= 25:
+        assert _rel_dev(got, ref).max() <= 1e-13
+
+
+def test_coincident_bodies_depth_cap():
+    # 40 bodies at one point (depth cap 21, zero-separation pairs skipped)
+    # plus a cloud around it
+    rng = np.random.default_rng(0)
+    p = np.concatenate([np.zeros((40, 3)) + 0.25, rng.uniform(-1, 1, (500, 3))])
+    m = np.full(p.shape[0], 1.0 / p.shape[0])
+    b = ics.Bodies(p[:, 0].copy(), p[:, 1].copy(), p[:, 2].copy(), m)
+    s, got = _solve(b, theta=0.5)
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25)
+    _compare_tree(s, o)
+    _compare_lists(s, o)
+    assert s.stats().depth == 21
+    ref = o.accel("TC")
+    assert np.all(np.isfinite(got))
+    assert _rel_dev(got, ref).max() <= 1e-12
+
+
+def test_all_bodies_coincident():
+    n = 100
+    b = ics.Bodies(np.full(n, 0.5), np.full(n, -0.25), np.full(n, 2.0), np.full(n, 0.01))
+    s, got = _solve(b)
+    assert np.all(got == 0.0)
+    assert s.stats().depth == 21
+
+
+def test_theta_to_zero_is_direct_summation():
+    b = ics.plummer(600, seed=9)
+    s, got = _solve(b, theta=1e-7)
+    ref = oracle.direct(b.x, b.y, b.z, b.m)
+    assert _rel_dev(got, ref).max() <= 1e-12
+
+
+def test_invalid_inputs_rejected():
+    from paper_1706_06989_gb300 import fmm
+    with pytest.raises(fmm.FMMError) as e:
+        _solver(theta=1.5)
+    assert e.value.code == fmm.FMM_EINVAL
+    b = ics.plummer(100, seed=1)
+    b.x[7] = np.nan
+    s = _solver(theta=0.5)
+    x, y, z, m = _dev(b)
+    with pytest.raises(fmm.FMMError) as e:
+        s.solve(x, y, z, m)
+    assert e.value.code == fmm.FMM_EINVAL
+    b = ics.plummer(100, seed=1)
+    b.m[3] = 0.0
+    x, y, z, m = _dev(b)
+    with pytest.raises(fmm.FMMError) as e:
+        s.solve(x, y, z, m)
+    assert e.value.code == fmm.FMM_EINVAL
+    # the context stays usable
+    b = ics.plummer(100, seed=1)
+    x, y, z, m = _dev(b)
+    s.solve(x, y, z, m)
+    with pytest.raises(fmm.FMMError) as e:
+        s2 = _solver(theta=0.5)
+        s2.upward()
+    assert e.value.code == fmm.FMM_EORDER
+
+
+def test_stage_by_stage_equals_solve():
+    b = ics.plummer(3000, seed=6)
+    s, got = _solve(b)
+    s2 = _solver(theta=0.5)
+    x, y, z, m = _dev(b)
+    s2.build_tree(x, y, z, m)
+    s2.upward()
+    s2.interact()
+    s2.downward()
+    a = torch.stack(s2.forces(), 1).cpu().numpy()
+    assert np.array_equal(a, got)
+
+
+def test_locals_l2l_consistent():
+    """L2L is exact: evaluating a leaf's expansion equals evaluating the
+    oracle's far field at the leaf's bodies (within rounding)."""
+    b = ics.plummer(4000, seed=8)
+    s, got = _solve(b)
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25)
+    far = o.accel("TC", parts=oracle.PART_FAR)
+    near = o.accel("TC", parts=oracle.PART_NEAR)
+    assert _rel_dev(got, far + near).max() <= 1e-12
+
+
+@pytest.mark.slow
+def test_plummer_1m_full_size():
+    """Plummer N = 1,048,576, theta = 0.5, n_crit = 25: keys, tree, geometry and
+    lists bit-exact; 4096 sampled accelerations within 1e-12; balance."""
+    b = ics.plummer(1 << 20, seed=0)
+    s, got = _solve(b, theta=0.5)
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25)
+    _compare_tree(s, o)
+    _compare_lists(s, o)
+    t = ics.error_subset(b.n, 4096, seed=1)
+    ref = o.accel("TC", targets=t)
+    assert _rel_dev(got[t], ref).max() <= 1e-12
+    fb, tb = oracle.balance(b.x, b.y, b.z, b.m, got)
+    assert fb <= 1e-13 and tb <= 1e-13
