@@ -1,0 +1,361 @@
+"""Benchmark: bodies/s of one full force solve of the angular-momentum-
+conserving FMM on a Plummer sphere of N = 1,048,576 equal-mass bodies
+(theta = 0.5, n_crit = 25, torque-corrected variant), one GB300 per rank.
+
+A step is one complete solve through the C ABI (fmm_build_tree, fmm_upward,
+fmm_interact, fmm_downward, fmm_forces) on bodies already resident in HBM.
+Each rank solves its own independent replica (a single solve is not sharded),
+so the aggregate scales weakly.  Between timed steps a 256 MiB buffer is
+written to flush the 129 MB L2.  The e2e figure is the same solve through
+fmm_solve_host from pinned host buffers (copies inside the timed region).
+
+--impl reference times the CPU oracle (the paper's serial method, plain C,
+FP64) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "bodies/s per full force solve at 1M–4M bodies; rms force err; fraction of FP32/FP64 peak"
+UNIT = "bodies/s"
+N_DEFAULT = 1 << 20
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+# FP64: 2 DFMA per clock per SM (4 flop); FP32: 128 FFMA per clock per SM (256 flop)
+FP64_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 4
+FP32_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 256
+# algorithmic flops (FMA = 2, rsqrt = 1) per unit of work; derivation in the design doc
+M2L_FLOPS = {"UC": 165, "TC": 281, "TCO": 260}
+P2P_FLOPS_PER_BODY_PAIR = 25
+ORACLE_SAMPLE_N = 131072
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=N_DEFAULT)
+    p.add_argument("--theta", type=float, default=0.5)
+    p.add_argument("--n-crit", type=int, default=25)
+    p.add_argument("--variant", default="TC", choices=["UC", "TC", "TCO"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-other", action="store_true", help="skip timing the other precision form")
+    return p.parse_args()
+
+
+def _workload(a) -> str:
+    return (f"plummer_n{a.n}_theta{a.theta}_ncrit{a.n_crit}_{a.variant.lower()}_{a.precision}")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reported baseline; also the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(a, n_sample: int):
+    """One oracle solve of a Plummer sphere of n_sample bodies (same recipe)."""
+    import oracle
+    from paper_1706_06989_gb300 import ics
+    b = ics.plummer(n_sample, seed=0)
+    t0 = time.perf_counter()
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, a.theta, a.n_crit)
+    o.accel(a.variant)
+    dt = time.perf_counter() - t0
+    return n_sample / dt, dt
+
+
+def cpu_baseline(a) -> dict:
+    v, dt = oracle_sample(a, ORACLE_SAMPLE_N)
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"one serial FP64 oracle solve of a Plummer sphere N={ORACLE_SAMPLE_N} (seed 0), "
+                       f"theta={a.theta}, n_crit={a.n_crit}, {a.variant}: tree, walk, order-3 far field "
+                       f"evaluated at every body, near field; {dt:.1f} s"),
+            "seconds": dt}
+
+
+def run_reference(a):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    n_sample = 32768
+    times = []
+    for _ in range(a.warmup):
+        oracle_sample(a, n_sample)
+    for _ in range(a.steps):
+        v, dt = oracle_sample(a, n_sample)
+        times.append(dt)
+    value = n_sample * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": _workload(a), "n": a.n, "theta": a.theta,
+                                            "n_crit": a.n_crit, "variant": a.variant,
+                                            "precision": "fp64", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": (f"each step one serial FP64 oracle solve of a Plummer sphere "
+                                        f"N={n_sample} (seed 0), theta={a.theta}, n_crit={a.n_crit}, "
+                                        f"{a.variant}")},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(a):
+    import torch
+    from paper_1706_06989_gb300 import fmm, ics
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    b = ics.plummer(a.n, seed=rank)  # one independent replica per rank
+    x, y, z, m = (torch.from_numpy(v).to(dev) for v in (b.x, b.y, b.z, b.m))
+    out = tuple(torch.empty(a.n, dtype=torch.float64, device=dev) for _ in range(3))
+    stream = torch.cuda.current_stream()
+    solver = fmm.FMM(theta=a.theta, n_crit=a.n_crit, variant=a.variant, precision=a.precision,
+                     stream=stream)
+    solver.set_timing(True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    for _ in range(max(3, a.warmup)):
+        solver.solve(x, y, z, m, out)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    kern = {"m2l": [], "p2p": [], "reduce": [], "walk": [], "tree": [], "upward": [], "downward": []}
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    t_wall = time.perf_counter()
+    for k in range(a.steps):
+        flush.fill_(k & 0xff)  # write 256 MiB > L2 between timed steps
+        ev[k][0].record(stream)
+        solver.solve(x, y, z, m, out)
+        ev[k][1].record(stream)
+        st = solver.stats()  # synchronises; per-stage event times of this solve
+        for key in kern:
+            kern[key].append(st.ms[key])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = ws * a.n * a.steps / total_s
+    st = solver.stats()
+
+    # roofline of the dominant interaction kernel (alu bound, FP64 or FP32)
+    m2l_ms = statistics.mean(kern["m2l"])
+    p2p_ms = statistics.mean(kern["p2p"])
+    m2l_flops = M2L_FLOPS[a.variant] * st.n_m2l
+    p2p_flops = P2P_FLOPS_PER_BODY_PAIR * st.p2p_body_pairs
+    peak = FP64_PEAK if a.precision == "fp64" else FP32_PEAK
+    if m2l_ms >= p2p_ms:
+        dom, dom_ms, dom_flops = "m2l", m2l_ms, m2l_flops
+    else:
+        dom, dom_ms, dom_flops = "p2p", p2p_ms, p2p_flops
+    achieved = dom_flops / (dom_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / (peak / 1e12), "traffic": None,
+                "peak_source": ("derived: 152 SMs x 2070 MHz x %s flop/clk/SM (FMA = 2)"
+                                % ("4 FP64" if a.precision == "fp64" else "256 FP32")),
+                "other": {"m2l": {"ms": m2l_ms, "tflops": m2l_flops / (m2l_ms * 1e-3) / 1e12 if m2l_ms > 0 else None},
+                          "p2p": {"ms": p2p_ms, "tflops": p2p_flops / (p2p_ms * 1e-3) / 1e12 if p2p_ms > 0 else None}}}
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not a.no_e2e:
+        hb = [torch.from_numpy(v).pin_memory() for v in (b.x, b.y, b.z, b.m)]
+        ho = [torch.empty(a.n, dtype=torch.float64).pin_memory() for _ in range(3)]
+        solver.solve_host(*hb, out=ho)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        es = []
+        for k in range(a.steps):
+            flush.fill_(k & 0xff)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            solver.solve_host(*hb, out=ho)
+            es.append(time.perf_counter() - t0)
+        etot = sum(es)
+        if dist:
+            t = torch.tensor([etot], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            etot = float(t.item())
+        e2e = {"value": ws * a.n * a.steps / etot, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * a.n,
+               "d2h_bytes_per_step": 3 * 8 * a.n, "ms_per_step": 1e3 * etot / a.steps}
+
+    # accuracy of this solve: rms relative force error against exact direct
+    # summation on 4096 bodies (seed 1), and the Sec. 3 balance metric
+    tg = ics.error_subset(a.n, 4096, seed=1)
+    solver.solve(x, y, z, m, out)
+    ref = torch.stack(solver.direct(x, y, z, m, tg), 1)
+    got = torch.stack(out, 1)[torch.as_tensor(tg, device=dev)]
+    rel = (torch.linalg.norm(got - ref, dim=1) / torch.linalg.norm(ref, dim=1)).cpu().numpy()
+    fbal, tbal = solver.balance(x, y, z, m, *out)
+    accuracy = {"rms_force_err": float(np.sqrt(np.mean(rel ** 2))), "mean_force_err": float(rel.mean()),
+                "subset": "4096 bodies drawn without replacement, seed 1; exact FP64 direct sum on the GPU",
+                "force_balance": fbal, "torque_balance": tbal}
+
+    # the other precision form of the same workload, same timing rules
+    other = None
+    if not a.no_other:
+        oprec = "mixed" if a.precision == "fp64" else "fp64"
+        s2 = fmm.FMM(theta=a.theta, n_crit=a.n_crit, variant=a.variant, precision=oprec, stream=stream)
+        s2.set_timing(True)
+        out2 = tuple(torch.empty(a.n, dtype=torch.float64, device=dev) for _ in range(3))
+        for _ in range(max(3, a.warmup)):
+            s2.solve(x, y, z, m, out2)
+        torch.cuda.synchronize()
+        t2, k2 = [], {"m2l": [], "p2p": []}
+        for k in range(a.steps):
+            flush.fill_(k & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s2.solve(x, y, z, m, out2)
+            e1.record(stream)
+            st2 = s2.stats()
+            k2["m2l"].append(st2.ms["m2l"])
+            k2["p2p"].append(st2.ms["p2p"])
+            t2.append(e0.elapsed_time(e1))
+        got2 = torch.stack(out2, 1)[torch.as_tensor(tg, device=dev)]
+        rel2 = (torch.linalg.norm(got2 - ref, dim=1) / torch.linalg.norm(ref, dim=1)).cpu().numpy()
+        dev2 = (torch.linalg.norm(got2 - got, dim=1) / torch.linalg.norm(got, dim=1)).cpu().numpy()
+        fb2, tb2 = s2.balance(x, y, z, m, *out2)
+        m2l2, p2p2 = statistics.mean(k2["m2l"]), statistics.mean(k2["p2p"])
+        pk2 = FP64_PEAK if oprec == "fp64" else FP32_PEAK
+        other = {"precision": oprec, "value": ws * a.n * len(t2) / (sum(t2) / 1e3) if ws == 1 else None,
+                 "ms_per_step": statistics.mean(t2), "rms_force_err": float(np.sqrt(np.mean(rel2 ** 2))),
+                 "rms_rel_dev_from_fp64": float(np.sqrt(np.mean(dev2 ** 2))) if oprec == "mixed" else None,
+                 "force_balance": fb2, "torque_balance": tb2,
+                 "m2l": {"ms": m2l2, "tflops": m2l_flops / (m2l2 * 1e-3) / 1e12,
+                         "frac": m2l_flops / (m2l2 * 1e-3) / pk2},
+                 "p2p": {"ms": p2p2, "tflops": p2p_flops / (p2p2 * 1e-3) / 1e12,
+                         "frac": p2p_flops / (p2p2 * 1e-3) / pk2}}
+        s2.close()
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(a)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": 1e3 * total_s / a.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": _workload(a), "n": a.n, "theta": a.theta, "n_crit": a.n_crit,
+                           "variant": a.variant, "precision": a.precision, "order_P": 3,
+                           "ics": "Plummer sphere, equal masses, G=1, M=1, a=1, seed=rank",
+                           "l2": "flushed (256 MiB write between timed steps)",
+                           "parallelism": f"replicas x{ws}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "accuracy": accuracy,
+                "other_form": other,
+                "gpu_launches": int(st.launches) * a.steps, "clocks": clocks,
+                "counts": {"ncell": st.ncell, "nleaf": st.nleaf, "depth": st.depth, "n_m2l": st.n_m2l,
+                           "n_p2p": st.n_p2p, "p2p_body_pairs": st.p2p_body_pairs},
+                "stage_ms": {k: statistics.mean(v) for k, v in kern.items()},
+                "wall_s_timed": t_wall}
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -141,6 +141,26 @@ int fmm_solve(fmm_ctx *ctx, const double *x, const double *y, const double *z, c
 int fmm_solve_host(fmm_ctx *ctx, const double *x, const double *y, const double *z,
                    const double *m, int64_t n, double *ax, double *ay, double *az);
 
+/* ---- a10 diagnostics (Sec. 3) ---------------------------------------------- */
+
+/* Exact accelerations of nt target bodies by direct summation over all n
+ * bodies (Sec. 3: the error of the method is measured against "the exact,
+ * directly computed force"), FP64 with Neumaier-compensated sums in a fixed
+ * order (reproducible).  x, y, z, m: device, n doubles, any body order;
+ * targets: device, nt int32 indices into them; ax, ay, az: device, nt
+ * doubles (G = 1; the context's G is not applied).  A body at zero
+ * separation from the target contributes nothing.  Asynchronous. */
+int fmm_direct(fmm_ctx *ctx, const double *x, const double *y, const double *z, const double *m,
+               int64_t n, const int32_t *targets, int64_t nt, double *ax, double *ay, double *az);
+
+/* Net force and torque balance of Sec. 3,
+ *   sqrt( sum_d (sum_n mu_n A_nd)^2 / sum_d (sum_n mu_n |A_nd|)^2 ),
+ * with A = (ax, ay, az) for the force and A = X x a (about the origin) for the
+ * torque.  All arrays device, n doubles; out: HOST, 2 doubles {force, torque}.
+ * FP64, compensated, fixed order.  Synchronises the stream. */
+int fmm_balance(fmm_ctx *ctx, const double *x, const double *y, const double *z, const double *m,
+                const double *ax, const double *ay, const double *az, int64_t n, double *out);
+
 /* Counts (and stage timings) of the last solve; synchronises the stream. */
 int fmm_get_stats(fmm_ctx *ctx, fmm_stats *out);
 

@@ -152,9 +152,9 @@ void fmm_destroy(fmm_ctx *c) {
                  &c->first_child, &c->nchild, &c->S, &c->M, &c->Z, &c->invM, &c->Rmax, &c->rmax2, &c->mom,
                  &c->loc, &c->leaves, &c->front[0], &c->front[1], &c->action, &c->wcount, &c->woff,
                  &c->m2l, &c->p2p, &c->self_list, &c->ekey[0], &c->ekey[1], &c->eval[0], &c->eval[1],
-                 &c->m2l_pos, &c->m2l_off, &c->m2l_slots, &c->pkey[0], &c->pkey[1], &c->pval[0],
+                 &c->m2l_pos, &c->m2l_off, &c->m2l_slots, &c->cell32, &c->pkey[0], &c->pkey[1], &c->pval[0],
                  &c->pval[1], &c->p2p_A, &c->p2p_offA, &c->p2p_offB, &c->p2p_pos, &c->p2p_poff,
-                 &c->p2p_len, &c->p2p_slots, &c->scan_tmp, &c->sort_hist, &c->totals, &c->hx, &c->hy,
+                 &c->p2p_len, &c->p2p_slots, &c->p2p_colOff, &c->p2p_cols, &c->p2p_nb, &c->p2p_pre, &c->scan_tmp, &c->sort_hist, &c->totals, &c->diag, &c->hx, &c->hy,
                  &c->hz, &c->hm, &c->hax, &c->hay, &c->haz};
   for (DBuf *b : all) free_buf(*b);
   for (int k = 0; k < kNumTimers; ++k)
@@ -224,9 +224,19 @@ int fmm_interact(fmm_ctx *c) {
   AMFMM_TRY(need_stage(c, kUp, "fmm_interact"));
   timer(c, kWalkBeg);
   AMFMM_TRY(walk(c));
+  AMFMM_TRY(m2l_prepare(c));
+  AMFMM_TRY(p2p_prepare(c));
   timer(c, kWalkEnd);
-  AMFMM_TRY(m2l(c));
-  AMFMM_TRY(p2p(c));
+  timer(c, kM2LBeg);
+  AMFMM_TRY(m2l_run(c));
+  timer(c, kM2LEnd);
+  timer(c, kP2PBeg);
+  AMFMM_TRY(p2p_run(c));
+  timer(c, kP2PEnd);
+  timer(c, kRedBeg);
+  AMFMM_TRY(m2l_reduce(c));
+  AMFMM_TRY(p2p_reduce(c));
+  timer(c, kRedEnd);
   c->stage = kInteract;
   return FMM_OK;
 }

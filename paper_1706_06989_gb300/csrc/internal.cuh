@@ -78,13 +78,14 @@ struct fmm_ctx {
   // walk
   amfmm::DBuf front[2], action, wcount, woff, m2l, p2p, self_list;
   // M2L scatter
-  amfmm::DBuf ekey[2], eval[2], m2l_pos, m2l_off, m2l_slots;
+  amfmm::DBuf ekey[2], eval[2], m2l_pos, m2l_off, m2l_slots, cell32;
   // P2P grouping
   amfmm::DBuf pkey[2], pval[2], p2p_A, p2p_offA, p2p_offB, p2p_pos, p2p_poff, p2p_len,
-      p2p_slots;
+      p2p_slots, p2p_colOff, p2p_cols, p2p_nb, p2p_pre;
   // scan / sort scratch; `totals` holds small device results (1 KiB):
-  // [0,16) scan totals, [64,72) near-field body-pair count, [96,104) slot total
-  amfmm::DBuf scan_tmp, sort_hist, totals;
+  // [0,16) scan totals, [64,72) near-field body-pair count, [96,104) slot total,
+  // [128,132) near-field column total
+  amfmm::DBuf scan_tmp, sort_hist, totals, diag;
   // host-solve staging
   amfmm::DBuf hx, hy, hz, hm, hax, hay, haz;
 };
@@ -148,8 +149,12 @@ int radix_sort_u32(fmm_ctx *c, DBuf key[2], DBuf val[2], int64_t n, int bits, in
 int build_tree(fmm_ctx *c);         // tree.cu
 int upward(fmm_ctx *c);             // tree.cu
 int walk(fmm_ctx *c);               // walk.cu
-int m2l(fmm_ctx *c);                // m2l.cu (lists -> per-cell locals)
-int p2p(fmm_ctx *c);                // p2p.cu (lists -> per-body near field)
+int m2l_prepare(fmm_ctx *c);        // m2l.cu: slot positions (sort by cell)
+int m2l_run(fmm_ctx *c);            // m2l.cu: mutual M2L into slots
+int m2l_reduce(fmm_ctx *c);         // m2l.cu: per-cell fixed-order sums
+int p2p_prepare(fmm_ctx *c);        // p2p.cu: grouping by leaf, partial slots
+int p2p_run(fmm_ctx *c);            // p2p.cu: mutual near field
+int p2p_reduce(fmm_ctx *c);         // p2p.cu: per-body fixed-order sums
 int downward(fmm_ctx *c);           // down.cu (L2L, L2P into sorted order)
 int forces(fmm_ctx *c, double *ax, double *ay, double *az);  // down.cu (caller order)
 

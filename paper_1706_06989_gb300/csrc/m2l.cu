@@ -35,6 +35,7 @@ namespace amfmm {
 namespace {
 
 constexpr int kBlock = 128;
+constexpr int kCell32 = 24;  // floats per cell in the mixed form's copy
 
 __device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
 __device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
@@ -132,46 +133,94 @@ __device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, T iMA, T iMB,
 }
 
 // One thread per accepted pair.  Slots are kLocStride wide (19 used).
-template <class T, int VARIANT>
-__global__ void __launch_bounds__(kBlock) k_m2l(int64_t K, const int2 *__restrict__ pairs,
-                                                 const double *__restrict__ Z,
-                                                 const double *__restrict__ M,
-                                                 const double *__restrict__ invM,
-                                                 const double *__restrict__ mom,
-                                                 const int32_t *__restrict__ pos, T *__restrict__ slots) {
+// FP64 form: reads the FP64 cell data.
+template <int VARIANT>
+__global__ void __launch_bounds__(kBlock) k_m2l64(int64_t K, const int2 *__restrict__ pairs,
+                                                   const double *__restrict__ Z,
+                                                   const double *__restrict__ M,
+                                                   const double *__restrict__ invM,
+                                                   const double *__restrict__ mom,
+                                                   const int32_t *__restrict__ pos, double *__restrict__ slots) {
   const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (k >= K) return;
   const int A = pairs[k].x, B = pairs[k].y;
-  T CA[kLocStride], CB[kLocStride];
+  double CA[kLocStride], CB[kLocStride];
   const double rx = Z[3 * A] - Z[3 * B], ry = Z[3 * A + 1] - Z[3 * B + 1], rz = Z[3 * A + 2] - Z[3 * B + 2];
   if (rx == 0.0 && ry == 0.0 && rz == 0.0) {
 #pragma unroll
-    for (int q = 0; q < kLocStride; ++q) CA[q] = CB[q] = T(0);
+    for (int q = 0; q < kLocStride; ++q) CA[q] = CB[q] = 0.0;
   } else {
-    const T r[3] = {T(rx), T(ry), T(rz)};
+    const double r[3] = {rx, ry, rz};
     const double *mA = mom + static_cast<int64_t>(A) * kMomStride;
     const double *mB = mom + static_cast<int64_t>(B) * kMomStride;
-    T QA[6], QB[6], OA[10], OB[10];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      QA[q] = T(mA[4 + q]);
-      QB[q] = T(mB[4 + q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 10; ++q) {
-      OA[q] = VARIANT == FMM_UC ? T(0) : T(mA[10 + q]);
-      OB[q] = VARIANT == FMM_UC ? T(0) : T(mB[10 + q]);
-    }
-    m2l_pair<T, VARIANT>(r, T(M[A]), T(M[B]), T(invM[A]), T(invM[B]), QA, QB, OA, OB, CA, CB);
-    CA[19] = CB[19] = T(0);
+    m2l_pair<double, VARIANT>(r, M[A], M[B], invM[A], invM[B], mA + 4, mB + 4, mA + 10, mB + 10, CA, CB);
+    CA[19] = CB[19] = 0.0;
   }
-  T *sa = slots + static_cast<int64_t>(pos[2 * k]) * kLocStride;
-  T *sb = slots + static_cast<int64_t>(pos[2 * k + 1]) * kLocStride;
+  double *sa = slots + static_cast<int64_t>(pos[2 * k]) * kLocStride;
+  double *sb = slots + static_cast<int64_t>(pos[2 * k + 1]) * kLocStride;
 #pragma unroll
-  for (int q = 0; q < kLocStride; ++q) {
-    sa[q] = CA[q];
-    sb[q] = CB[q];
+  for (int q = 0; q < kLocStride; q += 2) {
+    *reinterpret_cast<double2 *>(sa + q) = make_double2(CA[q], CA[q + 1]);
+    *reinterpret_cast<double2 *>(sb + q) = make_double2(CB[q], CB[q + 1]);
   }
+}
+
+// Mixed form: reads the FP32 copy of the cell data (kCell32 floats per cell:
+// Z as hi/lo float pairs, M, 1/M, Q, O).  r = Z_A - Z_B is formed from the
+// pairs, (hi_A - hi_B) + (lo_A - lo_B), accurate to FP32 relative to |r|.
+template <int VARIANT>
+__global__ void __launch_bounds__(kBlock) k_m2l32(int64_t K, const int2 *__restrict__ pairs,
+                                                   const float *__restrict__ cell32,
+                                                   const int32_t *__restrict__ pos, float *__restrict__ slots) {
+  const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (k >= K) return;
+  const int A = pairs[k].x, B = pairs[k].y;
+  float a[kCell32], b[kCell32];
+  const float4 *pa = reinterpret_cast<const float4 *>(cell32 + static_cast<int64_t>(A) * kCell32);
+  const float4 *pb = reinterpret_cast<const float4 *>(cell32 + static_cast<int64_t>(B) * kCell32);
+#pragma unroll
+  for (int u = 0; u < kCell32 / 4; ++u) {
+    const float4 va = pa[u], vb = pb[u];
+    a[4 * u] = va.x; a[4 * u + 1] = va.y; a[4 * u + 2] = va.z; a[4 * u + 3] = va.w;
+    b[4 * u] = vb.x; b[4 * u + 1] = vb.y; b[4 * u + 2] = vb.z; b[4 * u + 3] = vb.w;
+  }
+  float CA[kLocStride], CB[kLocStride];
+  const float r[3] = {(a[0] - b[0]) + (a[3] - b[3]), (a[1] - b[1]) + (a[4] - b[4]), (a[2] - b[2]) + (a[5] - b[5])};
+  if (r[0] == 0.f && r[1] == 0.f && r[2] == 0.f) {
+#pragma unroll
+    for (int q = 0; q < kLocStride; ++q) CA[q] = CB[q] = 0.f;
+  } else {
+    m2l_pair<float, VARIANT>(r, a[6], b[6], a[7], b[7], a + 8, b + 8, a + 14, b + 14, CA, CB);
+    CA[19] = CB[19] = 0.f;
+  }
+  float *sa = slots + static_cast<int64_t>(pos[2 * k]) * kLocStride;
+  float *sb = slots + static_cast<int64_t>(pos[2 * k + 1]) * kLocStride;
+#pragma unroll
+  for (int q = 0; q < kLocStride; q += 4) {
+    *reinterpret_cast<float4 *>(sa + q) = make_float4(CA[q], CA[q + 1], CA[q + 2], CA[q + 3]);
+    *reinterpret_cast<float4 *>(sb + q) = make_float4(CB[q], CB[q + 1], CB[q + 2], CB[q + 3]);
+  }
+}
+
+// FP32 copy of the cell data for the mixed form
+__global__ void k_cell32(int32_t ncell, const double *__restrict__ Z, const double *__restrict__ M,
+                         const double *__restrict__ invM, const double *__restrict__ mom,
+                         float *__restrict__ cell32) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  float *o = cell32 + static_cast<int64_t>(c) * kCell32;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double z = Z[3 * c + d];
+    const float hi = static_cast<float>(z);
+    o[d] = hi;
+    o[3 + d] = static_cast<float>(z - static_cast<double>(hi));
+  }
+  o[6] = static_cast<float>(M[c]);
+  o[7] = static_cast<float>(invM[c]);
+  const double *m = mom + static_cast<int64_t>(c) * kMomStride;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) o[8 + q] = static_cast<float>(m[4 + q]);
 }
 
 // entries: (cell, 2k + side) for the stable sort
@@ -193,46 +242,71 @@ __global__ void k_inverse(int64_t E, const uint32_t *__restrict__ sval, int32_t 
   if (s < E) pos[sval[s]] = static_cast<int32_t>(s);
 }
 
-// Every cell sums its slots in sorted (pair index) order.
+// Every cell sums its slots in sorted (pair index) order: one warp per cell,
+// lane q < 20 owns coefficient q, so each slot is read as one contiguous
+// 160-byte (FP64) or 80-byte (FP32) row.  Loads run ahead; the additions keep
+// the slot order.
 template <class T>
 __global__ void k_m2l_reduce(int32_t ncell, const int32_t *__restrict__ off, const T *__restrict__ slots,
                              double *__restrict__ loc) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  double acc[kLocStride];
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int q = threadIdx.x & 31;
+  if (c >= ncell || q >= kLocStride) return;
+  const int s0 = off[c], s1 = off[c + 1];
+  double acc = 0.0;
+  int s = s0;
+  if (sizeof(T) == sizeof(float)) {
+    // FP32 slots: pairwise sums of eight in FP32, accumulated in FP64
+    for (; s + 8 <= s1; s += 8) {
+      T v[8];
 #pragma unroll
-  for (int q = 0; q < kLocStride; ++q) acc[q] = 0.0;
-  for (int s = off[c]; s < off[c + 1]; ++s) {
-    const T *p = slots + static_cast<int64_t>(s) * kLocStride;
-#pragma unroll
-    for (int q = 0; q < kLocStride; ++q) acc[q] += static_cast<double>(p[q]);
+      for (int u = 0; u < 8; ++u) v[u] = slots[static_cast<int64_t>(s + u) * kLocStride + q];
+      const T g = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+      acc += static_cast<double>(g);
+    }
+  } else {
+    for (; s + 4 <= s1; s += 4) {
+      const double v0 = static_cast<double>(slots[static_cast<int64_t>(s) * kLocStride + q]);
+      const double v1 = static_cast<double>(slots[static_cast<int64_t>(s + 1) * kLocStride + q]);
+      const double v2 = static_cast<double>(slots[static_cast<int64_t>(s + 2) * kLocStride + q]);
+      const double v3 = static_cast<double>(slots[static_cast<int64_t>(s + 3) * kLocStride + q]);
+      acc += v0;
+      acc += v1;
+      acc += v2;
+      acc += v3;
+    }
   }
-  double *o = loc + static_cast<int64_t>(c) * kLocStride;
-#pragma unroll
-  for (int q = 0; q < kLocStride; ++q) o[q] = acc[q];
+  for (; s < s1; ++s) acc += static_cast<double>(slots[static_cast<int64_t>(s) * kLocStride + q]);
+  loc[static_cast<int64_t>(c) * kLocStride + q] = acc;
 }
 
-template <class T>
-int launch_m2l(fmm_ctx *c, int64_t K, int32_t *pos, void *slots) {
+int launch_m2l64(fmm_ctx *c, int64_t K) {
   const int2 *pairs = ptr<int2>(c->m2l);
   const unsigned g = grid_for(K, kBlock);
+  const double *Z = ptr<double>(c->Z), *M = ptr<double>(c->M), *iM = ptr<double>(c->invM),
+               *mom = ptr<double>(c->mom);
+  const int32_t *pos = ptr<int32_t>(c->m2l_pos);
+  double *slots = ptr<double>(c->m2l_slots);
   cudaStream_t st = c->stream;
   switch (c->opts.variant) {
-    case FMM_UC:
-      k_m2l<T, FMM_UC><<<g, kBlock, 0, st>>>(K, pairs, ptr<double>(c->Z), ptr<double>(c->M),
-                                              ptr<double>(c->invM), ptr<double>(c->mom), pos,
-                                              static_cast<T *>(slots));
-      break;
-    case FMM_TC:
-      k_m2l<T, FMM_TC><<<g, kBlock, 0, st>>>(K, pairs, ptr<double>(c->Z), ptr<double>(c->M),
-                                              ptr<double>(c->invM), ptr<double>(c->mom), pos,
-                                              static_cast<T *>(slots));
-      break;
-    default:
-      k_m2l<T, FMM_TCO><<<g, kBlock, 0, st>>>(K, pairs, ptr<double>(c->Z), ptr<double>(c->M),
-                                               ptr<double>(c->invM), ptr<double>(c->mom), pos,
-                                               static_cast<T *>(slots));
-      break;
+    case FMM_UC: k_m2l64<FMM_UC><<<g, kBlock, 0, st>>>(K, pairs, Z, M, iM, mom, pos, slots); break;
+    case FMM_TC: k_m2l64<FMM_TC><<<g, kBlock, 0, st>>>(K, pairs, Z, M, iM, mom, pos, slots); break;
+    default: k_m2l64<FMM_TCO><<<g, kBlock, 0, st>>>(K, pairs, Z, M, iM, mom, pos, slots); break;
+  }
+  return launched(c, "m2l");
+}
+
+int launch_m2l32(fmm_ctx *c, int64_t K) {
+  const int2 *pairs = ptr<int2>(c->m2l);
+  const unsigned g = grid_for(K, kBlock);
+  const float *c32 = ptr<float>(c->cell32);
+  const int32_t *pos = ptr<int32_t>(c->m2l_pos);
+  float *slots = ptr<float>(c->m2l_slots);
+  cudaStream_t st = c->stream;
+  switch (c->opts.variant) {
+    case FMM_UC: k_m2l32<FMM_UC><<<g, kBlock, 0, st>>>(K, pairs, c32, pos, slots); break;
+    case FMM_TC: k_m2l32<FMM_TC><<<g, kBlock, 0, st>>>(K, pairs, c32, pos, slots); break;
+    default: k_m2l32<FMM_TCO><<<g, kBlock, 0, st>>>(K, pairs, c32, pos, slots); break;
   }
   return launched(c, "m2l");
 }
@@ -245,53 +319,64 @@ int bits_for(int64_t v) {
 
 }  // namespace
 
-int m2l(fmm_ctx *c) {
+int m2l_prepare(fmm_ctx *c) {
   cudaStream_t st = c->stream;
   const int64_t K = c->sz.n_m2l, nc = c->sz.ncell, E = 2 * K;
   AMFMM_TRY(ensure<double>(c, c->loc, static_cast<size_t>(kLocStride) * nc));
   AMFMM_TRY(ensure<int32_t>(c, c->m2l_off, nc + 1));
   if (E > 0x7fffffffLL) return set_error(c, FMM_EUNSUPPORTED, "too many M2L pairs (%lld)", (long long)K);
-  timer(c, kM2LBeg);
   int32_t *off = ptr<int32_t>(c->m2l_off);
   AMFMM_CUDA(c, cudaMemsetAsync(off, 0, sizeof(int32_t) * (nc + 1), st));
-  if (K > 0) {
-    AMFMM_TRY(ensure<uint32_t>(c, c->ekey[0], E));
-    AMFMM_TRY(ensure<uint32_t>(c, c->eval[0], E));
-    AMFMM_TRY(ensure<int32_t>(c, c->m2l_pos, E));
-    // counts go to off[] and are then scanned in place via incl scratch
-    AMFMM_TRY(ensure<int32_t>(c, c->incl, std::max<int64_t>(nc + 1, c->sz.n + 1)));
-    int32_t *cnt = ptr<int32_t>(c->incl);
-    AMFMM_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nc + 1), st));
-    k_m2l_entries<<<grid_for(K, 256), 256, 0, st>>>(K, ptr<int2>(c->m2l), ptr<uint32_t>(c->ekey[0]),
-                                                    ptr<uint32_t>(c->eval[0]), cnt);
-    AMFMM_TRY(launched(c, "m2l_entries"));
-    AMFMM_TRY(exclusive_scan_i32(c, cnt, off, nc + 1, nullptr));
-    int which = 0;
-    AMFMM_TRY(radix_sort_u32(c, c->ekey, c->eval, E, bits_for(nc), &which));
-    k_inverse<<<grid_for(E, 256), 256, 0, st>>>(E, ptr<uint32_t>(c->eval[which]), ptr<int32_t>(c->m2l_pos));
-    AMFMM_TRY(launched(c, "m2l_inverse"));
-    const bool fp32 = c->opts.precision == FMM_MIXED;
-    const size_t esz = fp32 ? sizeof(float) : sizeof(double);
-    AMFMM_TRY(ensure_bytes(c, c->m2l_slots, static_cast<size_t>(E) * kLocStride * esz));
-    if (fp32) AMFMM_TRY(launch_m2l<float>(c, K, ptr<int32_t>(c->m2l_pos), c->m2l_slots.p));
-    else AMFMM_TRY(launch_m2l<double>(c, K, ptr<int32_t>(c->m2l_pos), c->m2l_slots.p));
-    timer(c, kM2LEnd);
-    timer(c, kRedBeg);
-    if (fp32)
-      k_m2l_reduce<float><<<grid_for(nc, 128), 128, 0, st>>>(static_cast<int32_t>(nc), off,
-                                                              ptr<float>(c->m2l_slots), ptr<double>(c->loc));
-    else
-      k_m2l_reduce<double><<<grid_for(nc, 128), 128, 0, st>>>(static_cast<int32_t>(nc), off,
-                                                               ptr<double>(c->m2l_slots), ptr<double>(c->loc));
-    AMFMM_TRY(launched(c, "m2l_reduce"));
-    timer(c, kRedEnd);
-  } else {
-    AMFMM_CUDA(c, cudaMemsetAsync(c->loc.p, 0, sizeof(double) * kLocStride * nc, st));
-    timer(c, kM2LEnd);
-    timer(c, kRedBeg);
-    timer(c, kRedEnd);
+  if (K == 0) return FMM_OK;
+  AMFMM_TRY(ensure<uint32_t>(c, c->ekey[0], E));
+  AMFMM_TRY(ensure<uint32_t>(c, c->eval[0], E));
+  AMFMM_TRY(ensure<int32_t>(c, c->m2l_pos, E));
+  AMFMM_TRY(ensure<int32_t>(c, c->incl, std::max<int64_t>(nc + 1, c->sz.n + 1)));
+  int32_t *cnt = ptr<int32_t>(c->incl);
+  AMFMM_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nc + 1), st));
+  k_m2l_entries<<<grid_for(K, 256), 256, 0, st>>>(K, ptr<int2>(c->m2l), ptr<uint32_t>(c->ekey[0]),
+                                                  ptr<uint32_t>(c->eval[0]), cnt);
+  AMFMM_TRY(launched(c, "m2l_entries"));
+  AMFMM_TRY(exclusive_scan_i32(c, cnt, off, nc + 1, nullptr));
+  int which = 0;
+  AMFMM_TRY(radix_sort_u32(c, c->ekey, c->eval, E, bits_for(nc), &which));
+  k_inverse<<<grid_for(E, 256), 256, 0, st>>>(E, ptr<uint32_t>(c->eval[which]), ptr<int32_t>(c->m2l_pos));
+  AMFMM_TRY(launched(c, "m2l_inverse"));
+  const bool fp32 = c->opts.precision == FMM_MIXED;
+  const size_t esz = fp32 ? sizeof(float) : sizeof(double);
+  AMFMM_TRY(ensure_bytes(c, c->m2l_slots, static_cast<size_t>(E) * kLocStride * esz));
+  if (fp32) {
+    AMFMM_TRY(ensure<float>(c, c->cell32, static_cast<size_t>(kCell32) * nc));
+    k_cell32<<<grid_for(nc, 256), 256, 0, st>>>(static_cast<int32_t>(nc), ptr<double>(c->Z), ptr<double>(c->M),
+                                                ptr<double>(c->invM), ptr<double>(c->mom), ptr<float>(c->cell32));
+    AMFMM_TRY(launched(c, "cell32"));
   }
   return FMM_OK;
+}
+
+int m2l_run(fmm_ctx *c) {
+  const int64_t K = c->sz.n_m2l;
+  if (K == 0) return FMM_OK;
+  if (c->opts.precision == FMM_MIXED) return launch_m2l32(c, K);
+  return launch_m2l64(c, K);
+}
+
+int m2l_reduce(fmm_ctx *c) {
+  cudaStream_t st = c->stream;
+  const int64_t K = c->sz.n_m2l, nc = c->sz.ncell;
+  if (K == 0) {
+    AMFMM_CUDA(c, cudaMemsetAsync(c->loc.p, 0, sizeof(double) * kLocStride * nc, st));
+    return FMM_OK;
+  }
+  int32_t *off = ptr<int32_t>(c->m2l_off);
+  const unsigned g = grid_for(nc * 32, 256);
+  if (c->opts.precision == FMM_MIXED)
+    k_m2l_reduce<float><<<g, 256, 0, st>>>(static_cast<int32_t>(nc), off, ptr<float>(c->m2l_slots),
+                                           ptr<double>(c->loc));
+  else
+    k_m2l_reduce<double><<<g, 256, 0, st>>>(static_cast<int32_t>(nc), off, ptr<double>(c->m2l_slots),
+                                            ptr<double>(c->loc));
+  return launched(c, "m2l_reduce");
 }
 
 }  // namespace amfmm

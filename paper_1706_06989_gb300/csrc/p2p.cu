@@ -8,145 +8,119 @@
 // conserved pair by pair).  A leaf with itself sums every ordered pair i != j
 // once on the side of i.  A pair at zero separation contributes nothing.
 //
-// Work layout: one warp per leaf A, over A's self interaction and every leaf
-// pair whose smaller id is A (pairs sorted by A, stable).  Lane = (row body i
-// of A, column phase g): with n_A rows, R = 32 / n_A lanes share a row and take
-// every R-th body of the partner, so small leaves still fill the warp.  The
-// A-side sum stays in registers across all partners; the B-side sums are
-// column sums through shared memory, b_j = sum_i s_ij (x_i - x_j) written as
-// T_j - x_j S_j with S_j = sum_i s_ij and T_j = sum_i s_ij x_i (x relative to
-// Z_A), one partial per (pair, body of B).  Each body then adds its partials in
-// the order of the stable sort.  Every sum has a fixed order; no atomics.
+// Work layout: one warp per leaf A.  Its columns are A's own bodies (summed
+// one-sided, i != j) followed by the bodies of every leaf B paired with A as
+// the smaller id (pairs sorted by A, stable), packed 32 columns to a step so
+// that small leaves still fill the warp.  Each lane owns one column body j and
+// loops over the rows i of A: the B-side sum b_j = sum_i m_i s_ij (X_i - X_j)
+// stays in a register and is complete when the loop ends; the A-side term
+// -m_j s_ij (X_i - X_j) goes to a per-(row, lane) partial in shared memory,
+// summed over the lanes in lane order once per leaf.  b_j is written to the
+// slot of (pair, body j); each body then adds its slots in the order of the
+// stable sort.  Every sum has a fixed order; no atomics.
 //
-// FP64 form: everything in FP64.  Mixed form: coordinates relative to Z_A
-// rounded to FP32, pair terms in FP32, the per-lane running sum over all
-// partners compensated (Kahan) in FP32, lanes and partials combined in FP64.
+// FP64 form: absolute coordinates, everything in FP64.  Mixed form:
+// coordinates relative to Z_A computed in FP64 and rounded to FP32, pair terms
+// and the short sums (over the rows of one leaf, over one lane's columns) in
+// FP32, every longer sum (lanes, slots, partners) in FP64.
 #include "internal.cuh"
 
 namespace amfmm {
 namespace {
 
 constexpr int kWarps = 4;
-constexpr int kCH = 32;
+constexpr int kRows = 32;  // rows of A held in shared memory per pass
 
 __device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
 __device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
 
+// Shared memory per warp: the rows (bodies of A) and, per row and component,
+// one running partial of the A-side sum for every lane.
 template <class T>
-struct Acc3 {
-  T s[3] = {T(0), T(0), T(0)};
-  __device__ __forceinline__ void add(int d, T v) { s[d] += v; }
-  __device__ __forceinline__ double get(int d) const { return static_cast<double>(s[d]); }
+struct P2PSmem {
+  T row[kRows][4];       // x, y, z, m of the current row chunk
+  T acc[kRows * 3][32];  // A-side partial sums, [3 i + d][lane]
 };
-// compensated running sum for the FP32 form
+
+// Coordinates a lane works with: absolute in FP64; relative to Z_A (computed
+// in FP64, rounded once) in the mixed form.
+template <class T>
+__device__ __forceinline__ T coord(double v, double z);
 template <>
-struct Acc3<float> {
-  float s[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
-  __device__ __forceinline__ void add(int d, float v) {
-    const float y = __fsub_rn(v, c[d]);
-    const float t = __fadd_rn(s[d], y);
-    c[d] = __fsub_rn(__fsub_rn(t, s[d]), y);
-    s[d] = t;
-  }
-  __device__ __forceinline__ double get(int d) const {
-    return static_cast<double>(s[d]) - static_cast<double>(c[d]);
-  }
-};
+__device__ __forceinline__ double coord<double>(double v, double) { return v; }
+template <>
+__device__ __forceinline__ float coord<float>(double v, double z) { return static_cast<float>(v - z); }
 
 template <class T>
 __global__ void __launch_bounds__(kWarps * 32) k_p2p(
     int32_t nleaf, int64_t n, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin,
     const int32_t *__restrict__ count, const double *__restrict__ Zc, const double *__restrict__ X,
     const double *__restrict__ Y, const double *__restrict__ Zb, const double *__restrict__ Mb,
-    const int32_t *__restrict__ offA, const int2 *__restrict__ pairs, const int32_t *__restrict__ pos,
-    const int64_t *__restrict__ poff, double *__restrict__ near, T *__restrict__ slots,
-    unsigned long long *__restrict__ stat_pairs) {
-  __shared__ T sS[kWarps][kCH][33];
-  __shared__ T sX[kWarps][32][3];
-  __shared__ double sR[kWarps][32][3];
+    const int32_t *__restrict__ colOff, const int2 *__restrict__ cols, double *__restrict__ near,
+    T *__restrict__ slots) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  P2PSmem<T> &sm = reinterpret_cast<P2PSmem<T> *>(smem_raw)[w];
   const int q = blockIdx.x * kWarps + w;
   if (q >= nleaf) return;
   const int L = leaves[q];
   const int bA = begin[L], nA = count[L];
   const double zx = Zc[3 * L], zy = Zc[3 * L + 1], zz = Zc[3 * L + 2];
-  const int kb = offA[L], ke = offA[L + 1];
-  unsigned long long npairs = static_cast<unsigned long long>(nA) * (nA - 1) / 2;
-
-  for (int r0 = 0; r0 < nA; r0 += 32) {
-    const int nrow = min(32, nA - r0);
-    const int R = 32 / nrow;
-    const int il = l / R, g = l % R;
-    const bool active = il < nrow;
-    T xi = T(0), yi = T(0), zi = T(0), mi = T(0);
-    if (active) {
-      const int i = bA + r0 + il;
-      xi = T(X[i] - zx);
-      yi = T(Y[i] - zy);
-      zi = T(Zb[i] - zz);
-      mi = T(Mb[i]);
-      if (g == 0) {
-        sX[w][il][0] = xi;
-        sX[w][il][1] = yi;
-        sX[w][il][2] = zi;
-      }
+  const int cb = colOff[L], ce = colOff[L + 1];
+  for (int t = l; t < nA; t += 32) {
+    near[bA + t] = 0.0;
+    near[n + bA + t] = 0.0;
+    near[2 * n + bA + t] = 0.0;
+  }
+  __syncwarp();
+  for (int r0 = 0; r0 < nA; r0 += kRows) {
+    const int nr = min(kRows, nA - r0);
+    if (l < nr) {
+      const int i = bA + r0 + l;
+      sm.row[l][0] = coord<T>(X[i], zx);
+      sm.row[l][1] = coord<T>(Y[i], zy);
+      sm.row[l][2] = coord<T>(Zb[i], zz);
+      sm.row[l][3] = T(Mb[i]);
     }
-    Acc3<T> a;
-    // self: ordered pairs i != j, one-sided
-    if (active) {
-      for (int j = g; j < nA; j += R) {
-        const int jb = bA + j;
-        const T dx = T(X[jb] - zx) - xi, dy = T(Y[jb] - zy) - yi, dz = T(Zb[jb] - zz) - zi;
+    for (int v = 0; v < 3 * nr; ++v) sm.acc[v][l] = T(0);
+    __syncwarp();
+    // columns: A's own bodies (one-sided, self) then the bodies of every
+    // partner leaf B with A < B, packed 32 to a step
+    for (int c0 = cb; c0 < ce; c0 += 32) {
+      const int c = c0 + l;
+      const bool valid = c < ce;
+      int2 col = make_int2(0, -2);
+      T xj = T(0), yj = T(0), zj = T(0), mj = T(0);
+      if (valid) {
+        col = cols[c];
+        xj = coord<T>(X[col.x], zx);
+        yj = coord<T>(Y[col.x], zy);
+        zj = coord<T>(Zb[col.x], zz);
+        mj = T(Mb[col.x]);
+      }
+      const bool mutual = col.y >= 0;
+      T bx = T(0), by = T(0), bz = T(0);
+      for (int i = 0; i < nr; ++i) {
+        const T dx = sm.row[i][0] - xj, dy = sm.row[i][1] - yj, dz = sm.row[i][2] - zj;
         const T r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 > T(0)) {
+        if (valid && r2 > T(0)) {
           const T ri = rsqrt_t(r2);
-          const T sj = T(Mb[jb]) * (ri * ri * ri);
-          a.add(0, sj * dx);
-          a.add(1, sj * dy);
-          a.add(2, sj * dz);
+          const T r3 = ri * ri * ri;
+          const T si = sm.row[i][3] * r3;
+          bx += si * dx;
+          by += si * dy;
+          bz += si * dz;
+          if (mutual) {
+            const T sj = mj * r3;
+            sm.acc[3 * i][l] -= sj * dx;
+            sm.acc[3 * i + 1][l] -= sj * dy;
+            sm.acc[3 * i + 2][l] -= sj * dz;
+          }
         }
       }
-    }
-    // leaf pairs with A as the smaller id
-    for (int k = kb; k < ke; ++k) {
-      const int B = pairs[k].y;
-      const int bB = begin[B], nB = count[B];
-      if (r0 == 0 && l == 0) npairs += static_cast<unsigned long long>(nA) * nB;
-      T *out = slots + poff[pos[k]];
-      for (int j0 = 0; j0 < nB; j0 += kCH) {
-        const int ncol = min(kCH, nB - j0);
-        if (active) {
-          for (int jj = g; jj < ncol; jj += R) {
-            const int jb = bB + j0 + jj;
-            const T dx = T(X[jb] - zx) - xi, dy = T(Y[jb] - zy) - yi, dz = T(Zb[jb] - zz) - zi;
-            const T r2 = dx * dx + dy * dy + dz * dz;
-            T si = T(0);
-            if (r2 > T(0)) {
-              const T ri = rsqrt_t(r2);
-              const T r3 = ri * ri * ri;
-              const T sj = T(Mb[jb]) * r3;
-              a.add(0, sj * dx);
-              a.add(1, sj * dy);
-              a.add(2, sj * dz);
-              si = mi * r3;
-            }
-            sS[w][jj][il] = si;
-          }
-        }
-        __syncwarp();
-        if (l < ncol) {
-          const int jb = bB + j0 + l;
-          const T xj = T(X[jb] - zx), yj = T(Y[jb] - zy), zj = T(Zb[jb] - zz);
-          T S = T(0), Tx = T(0), Ty = T(0), Tz = T(0);
-          for (int r = 0; r < nrow; ++r) {
-            const T s = sS[w][l][r];
-            S += s;
-            Tx += s * sX[w][r][0];
-            Ty += s * sX[w][r][1];
-            Tz += s * sX[w][r][2];
-          }
-          T *o = out + 3 * (j0 + l);
-          const T bx = Tx - xj * S, by = Ty - yj * S, bz = Tz - zj * S;
+      if (valid) {
+        if (mutual) {
+          T *o = slots + col.y;
           if (r0 == 0) {
             o[0] = bx;
             o[1] = by;
@@ -156,29 +130,33 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
             o[1] += by;
             o[2] += bz;
           }
+        } else {
+          near[col.x] += static_cast<double>(bx);
+          near[n + col.x] += static_cast<double>(by);
+          near[2 * n + col.x] += static_cast<double>(bz);
         }
-        __syncwarp();
       }
     }
-    sR[w][l][0] = a.get(0);
-    sR[w][l][1] = a.get(1);
-    sR[w][l][2] = a.get(2);
     __syncwarp();
-    if (l < nrow) {
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-      for (int t = 0; t < R; ++t) {
-        s0 += sR[w][l * R + t][0];
-        s1 += sR[w][l * R + t][1];
-        s2 += sR[w][l * R + t][2];
+    // A-side: every row's partials summed over the lanes in a fixed order
+    // (FP64: sequential; mixed: pairwise in FP32 over groups of eight lanes,
+    // the four group sums in FP64)
+    for (int v = l; v < 3 * nr; v += 32) {
+      double s = 0.0;
+      if (sizeof(T) == sizeof(float)) {
+#pragma unroll
+        for (int g0 = 0; g0 < 32; g0 += 8) {
+          const T *a = &sm.acc[v][g0];
+          s += static_cast<double>(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
+        }
+      } else {
+#pragma unroll 8
+        for (int t = 0; t < 32; ++t) s += static_cast<double>(sm.acc[v][t]);
       }
-      const int64_t i = bA + r0 + l;
-      near[i] = s0;
-      near[n + i] = s1;
-      near[2 * n + i] = s2;
+      near[static_cast<int64_t>(v % 3) * n + bA + r0 + v / 3] += s;
     }
     __syncwarp();
   }
-  if (l == 0) atomicAdd(stat_pairs, npairs);
 }
 
 // Each body adds, in sorted order, the partials that the pairs in which its
@@ -236,45 +214,114 @@ int bits_for(int64_t v) {
   return b;
 }
 
+// Columns of every leaf: first its own bodies (marked -1: one-sided), then the
+// bodies of its partner leaves in the A-sorted pair order, each with the slot
+// that receives its B-side partial.
+__global__ void k_col_count_pairs(int64_t K, const int2 *__restrict__ pairs, const int32_t *__restrict__ count,
+                                  int32_t *__restrict__ ccount, int32_t *__restrict__ nb) {
+  const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (k >= K) return;
+  const int2 p = pairs[k];
+  nb[k] = count[p.y];
+  atomicAdd(&ccount[p.x], count[p.y]);
+}
+
+__global__ void k_col_count_leaves(int32_t nleaf, const int32_t *__restrict__ leaves,
+                                   const int32_t *__restrict__ count, int32_t *__restrict__ ccount) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nleaf) ccount[leaves[q]] += count[leaves[q]];
+}
+
+__global__ void k_cols_self(int32_t nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin,
+                            const int32_t *__restrict__ count, const int32_t *__restrict__ colOff,
+                            int2 *__restrict__ cols) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nleaf) return;
+  const int L = leaves[q];
+  const int b = begin[L], c0 = colOff[L];
+  for (int t = 0; t < count[L]; ++t) cols[c0 + t] = make_int2(b + t, -1);
+}
+
+__global__ void k_cols_pairs(int64_t K, const int2 *__restrict__ pairs, const int32_t *__restrict__ begin,
+                             const int32_t *__restrict__ count, const int32_t *__restrict__ colOff,
+                             const int32_t *__restrict__ offA, const int32_t *__restrict__ pre,
+                             const int32_t *__restrict__ pos, const int64_t *__restrict__ poff,
+                             int2 *__restrict__ cols) {
+  const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (k >= K) return;
+  const int2 p = pairs[k];
+  const int base = colOff[p.x] + count[p.x] + (pre[k] - pre[offA[p.x]]);
+  const int bB = begin[p.y];
+  const int64_t o = poff[pos[k]];
+  for (int t = 0; t < count[p.y]; ++t) cols[base + t] = make_int2(bB + t, static_cast<int32_t>(o + 3 * t));
+}
+
+// near-field work: n_A n_B per leaf pair plus n (n - 1) / 2 per leaf
+__global__ void k_p2p_work(int64_t K, const int2 *__restrict__ pairs, int32_t nleaf,
+                           const int32_t *__restrict__ leaves, const int32_t *__restrict__ count,
+                           unsigned long long *__restrict__ out) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  unsigned long long v = 0;
+  if (t < K) v = static_cast<unsigned long long>(count[pairs[t].x]) * count[pairs[t].y];
+  else if (t < K + nleaf) {
+    const unsigned long long a = count[leaves[t - K]];
+    v = a * (a - 1) / 2;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+}
+
 template <class T>
-int launch_p2p(fmm_ctx *c, int64_t K) {
-  cudaStream_t st = c->stream;
+int launch_p2p(fmm_ctx *c) {
   const int64_t n = c->sz.n;
   const int32_t nleaf = static_cast<int32_t>(c->sz.nleaf);
-  k_p2p<T><<<grid_for(nleaf, kWarps), kWarps * 32, 0, st>>>(
+  const size_t shm = kWarps * sizeof(P2PSmem<T>);
+  static bool attr_set = false;  // per T instantiation
+  if (!attr_set) {
+    AMFMM_CUDA(c, cudaFuncSetAttribute(k_p2p<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
+    attr_set = true;
+  }
+  k_p2p<T><<<grid_for(nleaf, kWarps), kWarps * 32, shm, c->stream>>>(
       nleaf, n, ptr<int32_t>(c->leaves), ptr<int32_t>(c->begin), ptr<int32_t>(c->count),
       ptr<double>(c->Z), ptr<double>(c->X), ptr<double>(c->Y), ptr<double>(c->Zb), ptr<double>(c->Mb),
-      ptr<int32_t>(c->p2p_offA), ptr<int2>(c->p2p_A), ptr<int32_t>(c->p2p_pos), ptr<int64_t>(c->p2p_poff),
-      ptr<double>(c->near), static_cast<T *>(c->p2p_slots.p),
-      ptr<unsigned long long>(c->totals) + 8);
-  AMFMM_TRY(launched(c, "p2p"));
-  timer(c, kP2PEnd);
-  if (K > 0) {
-    k_p2p_reduce<T><<<grid_for(n, 256), 256, 0, st>>>(n, ptr<int32_t>(c->leaf_of), ptr<int32_t>(c->begin),
-                                                       ptr<int32_t>(c->p2p_offB), ptr<int64_t>(c->p2p_poff),
-                                                       static_cast<T *>(c->p2p_slots.p), ptr<double>(c->near));
-    AMFMM_TRY(launched(c, "p2p_reduce"));
-  }
-  return FMM_OK;
+      ptr<int32_t>(c->p2p_colOff), ptr<int2>(c->p2p_cols), ptr<double>(c->near),
+      static_cast<T *>(c->p2p_slots.p));
+  return launched(c, "p2p");
+}
+
+template <class T>
+int launch_p2p_reduce(fmm_ctx *c) {
+  const int64_t n = c->sz.n;
+  k_p2p_reduce<T><<<grid_for(n, 256), 256, 0, c->stream>>>(n, ptr<int32_t>(c->leaf_of), ptr<int32_t>(c->begin),
+                                                           ptr<int32_t>(c->p2p_offB), ptr<int64_t>(c->p2p_poff),
+                                                           static_cast<T *>(c->p2p_slots.p), ptr<double>(c->near));
+  return launched(c, "p2p_reduce");
 }
 
 }  // namespace
 
-int p2p(fmm_ctx *c) {
+int p2p_prepare(fmm_ctx *c) {
   cudaStream_t st = c->stream;
   const int64_t K = c->sz.n_p2p, nc = c->sz.ncell, n = c->sz.n;
+  const int32_t nleaf = static_cast<int32_t>(c->sz.nleaf);
   const bool fp32 = c->opts.precision == FMM_MIXED;
   AMFMM_TRY(ensure<double>(c, c->near, 3 * n));
   AMFMM_TRY(ensure<int32_t>(c, c->p2p_offA, nc + 1));
   AMFMM_TRY(ensure<int32_t>(c, c->p2p_offB, nc + 1));
+  AMFMM_TRY(ensure<int32_t>(c, c->p2p_colOff, nc + 1));
   AMFMM_TRY(ensure<int64_t>(c, c->p2p_poff, K + 1));
   AMFMM_TRY(ensure<int32_t>(c, c->p2p_pos, K + 1));
   AMFMM_TRY(ensure<int2>(c, c->p2p_A, K + 1));
   AMFMM_TRY(ensure<int32_t>(c, c->incl, std::max<int64_t>(nc + 1, n + 1)));
   int32_t *cnt = ptr<int32_t>(c->incl);
   int32_t *offA = ptr<int32_t>(c->p2p_offA), *offB = ptr<int32_t>(c->p2p_offB);
-  int64_t *stat = ptr<int64_t>(c->totals) + 8;
-  AMFMM_CUDA(c, cudaMemsetAsync(stat, 0, sizeof(int64_t), st));
+  int32_t *colOff = ptr<int32_t>(c->p2p_colOff);
+  unsigned long long *stat = ptr<unsigned long long>(c->totals) + 8;
+  int32_t *ctot = ptr<int32_t>(c->totals) + 32;
+  AMFMM_CUDA(c, cudaMemsetAsync(stat, 0, sizeof(unsigned long long), st));
+  int64_t *h = static_cast<int64_t *>(c->hpin);
+  h[0] = 0;
   if (K > 0) {
     AMFMM_TRY(ensure<uint32_t>(c, c->pkey[0], K));
     AMFMM_TRY(ensure<uint32_t>(c, c->pval[0], K));
@@ -296,7 +343,7 @@ int p2p(fmm_ctx *c) {
     AMFMM_TRY(launched(c, "p2p_keysB"));
     AMFMM_TRY(exclusive_scan_i32(c, cnt, offB, nc + 1, nullptr));
     AMFMM_TRY(radix_sort_u32(c, c->pkey, c->pval, K, bits_for(nc), &which));
-    // lengths into a temporary int64 array, then scanned into poff
+    // B-side slot offsets: 3 n_B doubles per pair, in B-CSR order
     AMFMM_TRY(ensure<int64_t>(c, c->p2p_len, K + 1));
     int64_t *len = ptr<int64_t>(c->p2p_len);
     k_b_positions<<<grid_for(K, 256), 256, 0, st>>>(K, ptr<uint32_t>(c->pval[which]), ptr<int2>(c->p2p_A),
@@ -304,18 +351,53 @@ int p2p(fmm_ctx *c) {
     AMFMM_TRY(launched(c, "p2p_bpos"));
     int64_t *ptot = ptr<int64_t>(c->totals) + 12;
     AMFMM_TRY(exclusive_scan_i64(c, len, ptr<int64_t>(c->p2p_poff), K, ptot));
-    int64_t *h = static_cast<int64_t *>(c->hpin);
     AMFMM_CUDA(c, cudaMemcpyAsync(h, ptot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    AMFMM_CUDA(c, cudaStreamSynchronize(st));
-    AMFMM_TRY(ensure_bytes(c, c->p2p_slots, static_cast<size_t>(h[0] + 3) * (fp32 ? sizeof(float) : sizeof(double))));
-  } else {
-    AMFMM_CUDA(c, cudaMemsetAsync(offA, 0, sizeof(int32_t) * (nc + 1), st));
-    AMFMM_CUDA(c, cudaMemsetAsync(offB, 0, sizeof(int32_t) * (nc + 1), st));
-    AMFMM_TRY(ensure_bytes(c, c->p2p_slots, 64));
   }
-  timer(c, kP2PBeg);
-  if (fp32) return launch_p2p<float>(c, K);
-  return launch_p2p<double>(c, K);
+  // column stream per leaf
+  AMFMM_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nc + 1), st));
+  AMFMM_TRY(ensure<int32_t>(c, c->p2p_nb, K + 1));
+  int32_t *nb = ptr<int32_t>(c->p2p_nb);
+  if (K > 0) {
+    k_col_count_pairs<<<grid_for(K, 256), 256, 0, st>>>(K, ptr<int2>(c->p2p_A), ptr<int32_t>(c->count), cnt, nb);
+    AMFMM_TRY(launched(c, "p2p_col_count_pairs"));
+  }
+  k_col_count_leaves<<<grid_for(nleaf, 256), 256, 0, st>>>(nleaf, ptr<int32_t>(c->leaves), ptr<int32_t>(c->count), cnt);
+  AMFMM_TRY(launched(c, "p2p_col_count_leaves"));
+  AMFMM_TRY(exclusive_scan_i32(c, cnt, colOff, nc + 1, ctot));
+  k_p2p_work<<<grid_for(K + nleaf, 256), 256, 0, st>>>(K, ptr<int2>(c->p2p_A), nleaf, ptr<int32_t>(c->leaves),
+                                                       ptr<int32_t>(c->count), stat);
+  AMFMM_TRY(launched(c, "p2p_work"));
+  int32_t *hc = reinterpret_cast<int32_t *>(h + 1);
+  AMFMM_CUDA(c, cudaMemcpyAsync(hc, ctot, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  AMFMM_CUDA(c, cudaStreamSynchronize(st));
+  const int64_t nslot = h[0], ncol = hc[0];
+  if (nslot + 3 > 0x7fffffffLL) return set_error(c, FMM_EUNSUPPORTED, "too many near-field slots (%lld)", (long long)nslot);
+  AMFMM_TRY(ensure_bytes(c, c->p2p_slots, static_cast<size_t>(nslot + 3) * (fp32 ? sizeof(float) : sizeof(double))));
+  AMFMM_TRY(ensure<int2>(c, c->p2p_cols, ncol + 1));
+  k_cols_self<<<grid_for(nleaf, 256), 256, 0, st>>>(nleaf, ptr<int32_t>(c->leaves), ptr<int32_t>(c->begin),
+                                                    ptr<int32_t>(c->count), colOff, ptr<int2>(c->p2p_cols));
+  AMFMM_TRY(launched(c, "p2p_cols_self"));
+  if (K > 0) {
+    AMFMM_TRY(ensure<int32_t>(c, c->p2p_pre, K + 1));
+    AMFMM_TRY(exclusive_scan_i32(c, nb, ptr<int32_t>(c->p2p_pre), K, nullptr));
+    k_cols_pairs<<<grid_for(K, 256), 256, 0, st>>>(K, ptr<int2>(c->p2p_A), ptr<int32_t>(c->begin),
+                                                   ptr<int32_t>(c->count), colOff, offA, ptr<int32_t>(c->p2p_pre),
+                                                   ptr<int32_t>(c->p2p_pos), ptr<int64_t>(c->p2p_poff),
+                                                   ptr<int2>(c->p2p_cols));
+    AMFMM_TRY(launched(c, "p2p_cols_pairs"));
+  }
+  return FMM_OK;
+}
+
+int p2p_run(fmm_ctx *c) {
+  if (c->opts.precision == FMM_MIXED) return launch_p2p<float>(c);
+  return launch_p2p<double>(c);
+}
+
+int p2p_reduce(fmm_ctx *c) {
+  if (c->sz.n_p2p == 0) return FMM_OK;
+  if (c->opts.precision == FMM_MIXED) return launch_p2p_reduce<float>(c);
+  return launch_p2p_reduce<double>(c);
 }
 
 }  // namespace amfmm

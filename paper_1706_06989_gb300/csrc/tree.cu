@@ -59,19 +59,32 @@ __global__ void k_bbox_partial(const double *__restrict__ x, const double *__res
   }
 }
 
-// bbox[0..2] = lo, bbox[3] = scale = 2^21 / ext (0 when ext == 0)
+// bbox[0..2] = lo, bbox[3] = scale = 2^21 / ext (0 when ext == 0).  One block;
+// min and max are exact, so the order of combination does not matter.
 __global__ void k_bbox_final(const double *__restrict__ part, int nb, double *__restrict__ bbox) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  __shared__ double sh[6][kBlock / 32];
+  double v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+    for (int k = 0; k < 6; ++k) v[k] = k < 3 ? fmin(v[k], part[b * 6 + k]) : fmax(v[k], part[b * 6 + k]);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k = 0; k < 6; ++k) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const double u = __shfl_xor_sync(0xffffffffu, v[k], o);
+      v[k] = k < 3 ? fmin(v[k], u) : fmax(v[k], u);
+    }
+    if (lane == 0) sh[k][w] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   double lo[3], hi[3];
   for (int d = 0; d < 3; ++d) {
-    lo[d] = part[d];
-    hi[d] = part[3 + d];
-  }
-  for (int b = 1; b < nb; ++b)
-    for (int d = 0; d < 3; ++d) {
-      lo[d] = fmin(lo[d], part[b * 6 + d]);
-      hi[d] = fmax(hi[d], part[b * 6 + 3 + d]);
+    lo[d] = sh[d][0];
+    hi[d] = sh[3 + d][0];
+    for (int q = 1; q < kBlock / 32; ++q) {
+      lo[d] = fmin(lo[d], sh[d][q]);
+      hi[d] = fmax(hi[d], sh[3 + d][q]);
     }
+  }
   double ext = __dsub_rn(hi[0], lo[0]);
   ext = fmax(ext, __dsub_rn(hi[1], lo[1]));
   ext = fmax(ext, __dsub_rn(hi[2], lo[2]));
@@ -427,7 +440,7 @@ int build_tree(fmm_ctx *c) {
   AMFMM_CUDA(c, cudaMemsetAsync(status, 0, sizeof(int) * 4, st));
   k_bbox_partial<<<nbb, kBlock, 0, st>>>(c->x, c->y, c->z, c->m, n, ptr<double>(c->bbox_part), status);
   AMFMM_TRY(launched(c, "bbox_partial"));
-  k_bbox_final<<<1, 32, 0, st>>>(ptr<double>(c->bbox_part), nbb, ptr<double>(c->bbox));
+  k_bbox_final<<<1, kBlock, 0, st>>>(ptr<double>(c->bbox_part), nbb, ptr<double>(c->bbox));
   AMFMM_TRY(launched(c, "bbox_final"));
   k_keys<<<grid_for(n, kBlock), kBlock, 0, st>>>(c->x, c->y, c->z, n, ptr<double>(c->bbox),
                                                  ptr<uint64_t>(c->key[0]), ptr<uint32_t>(c->idx[0]));

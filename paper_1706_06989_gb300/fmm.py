@@ -74,6 +74,8 @@ def load() -> ctypes.CDLL:
                 "fmm_export_moments": [P, P],
                 "fmm_export_lists": [P, P, P, P],
                 "fmm_export_locals": [P, P],
+                "fmm_direct": [P, P, P, P, P, I64, P, I64, P, P, P],
+                "fmm_balance": [P, P, P, P, P, P, P, P, I64, P],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -227,6 +229,25 @@ class FMM:
         self._check(self.lib.fmm_solve_host(self._h, hp(x), hp(y), hp(z), hp(m), n, *(hp(o) for o in out)),
                     "fmm_solve_host")
         return out
+
+    # ---- diagnostics (Sec. 3) ---------------------------------------------------
+    def direct(self, x, y, z, m, targets):
+        """Exact FP64 accelerations of the target bodies by direct summation."""
+        t = self._torch
+        x, y, z, m = (self._as_dev(a) for a in (x, y, z, m))
+        tg = t.as_tensor(targets, dtype=t.int32, device=x.device).contiguous()
+        out = tuple(t.empty(tg.shape[0], dtype=t.float64, device=x.device) for _ in range(3))
+        self._check(self.lib.fmm_direct(self._h, _dptr(x), _dptr(y), _dptr(z), _dptr(m), x.shape[0],
+                                        _dptr(tg), tg.shape[0], *(_dptr(o) for o in out)), "fmm_direct")
+        return out
+
+    def balance(self, x, y, z, m, ax, ay, az):
+        """(net force balance, net torque balance) of Sec. 3."""
+        x, y, z, m, ax, ay, az = (self._as_dev(a) for a in (x, y, z, m, ax, ay, az))
+        out = (ctypes.c_double * 2)()
+        self._check(self.lib.fmm_balance(self._h, _dptr(x), _dptr(y), _dptr(z), _dptr(m), _dptr(ax), _dptr(ay),
+                                         _dptr(az), x.shape[0], ctypes.cast(out, ctypes.c_void_p)), "fmm_balance")
+        return float(out[0]), float(out[1])
 
     # ---- introspection -------------------------------------------------------
     def stats(self) -> Stats:

@@ -241,3 +241,54 @@ def test_plummer_1m_full_size():
     assert _rel_dev(got[t], ref).max() <= 1e-12
     fb, tb = oracle.balance(b.x, b.y, b.z, b.m, got)
     assert fb <= 1e-13 and tb <= 1e-13
+
+
+@pytest.mark.parametrize("variant", ["TC", "TCO"])
+def test_mixed_precision_against_oracle(variant):
+    """Mixed form: FP32 interactions on cell-relative coordinates, FP64 tree,
+    moments and accumulation.  rms relative force error against the FP64
+    oracle <= 1e-6; force and torque balance <= 1e-6."""
+    b = ics.plummer(65536, seed=0)
+    s, got = _solve(b, theta=0.5, variant=variant, precision="mixed")
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25)
+    _compare_tree(s, o)
+    _compare_lists(s, o)
+    t = ics.error_subset(b.n, 4096, seed=1)
+    ref = o.accel(variant, targets=t)
+    rel = _rel_dev(got[t], ref)
+    assert np.sqrt(np.mean(rel ** 2)) <= 1e-6, np.sqrt(np.mean(rel ** 2))
+    fb, tb = oracle.balance(b.x, b.y, b.z, b.m, got)
+    assert fb <= 1e-6 and tb <= 1e-6, (fb, tb)
+
+
+def test_mixed_precision_small_exact_cases():
+    b = ics.plummer(2000, seed=0)
+    s, got = _solve(b, theta=0.5, precision="mixed")
+    ref = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25).accel("TC")
+    rel = _rel_dev(got, ref)
+    assert np.sqrt(np.mean(rel ** 2)) <= 1e-6
+    s2, got2 = _solve(b, theta=0.5, precision="mixed")
+    assert np.array_equal(got, got2)
+
+
+def test_direct_diagnostic_matches_oracle():
+    b = ics.plummer(20000, seed=21)
+    s = _solver(theta=0.5)
+    x, y, z, m = _dev(b)
+    t = ics.error_subset(b.n, 300, seed=2)
+    a = torch.stack(s.direct(x, y, z, m, t), 1).cpu().numpy()
+    ref = oracle.direct(b.x, b.y, b.z, b.m, targets=t)
+    assert _rel_dev(a, ref).max() <= 1e-14
+    a2 = torch.stack(s.direct(x, y, z, m, t), 1).cpu().numpy()
+    assert np.array_equal(a, a2)
+
+
+def test_balance_diagnostic_matches_oracle():
+    b = ics.plummer(50000, seed=22)
+    s, got = _solve(b, variant="UC")
+    x, y, z, m = _dev(b)
+    g = torch.from_numpy(got).cuda()
+    fb, tb = s.balance(x, y, z, m, g[:, 0].contiguous(), g[:, 1].contiguous(), g[:, 2].contiguous())
+    ofb, otb = oracle.balance(b.x, b.y, b.z, b.m, got)
+    assert abs(tb - otb) <= 1e-3 * otb  # UC: a clear torque imbalance, same value
+    assert fb <= 1e-13 and ofb <= 1e-13
