@@ -52,6 +52,7 @@ extern "C" {
 #define FMM_ETIMEOUT (-4)     /* a bounded device wait expired */
 #define FMM_EORDER (-5)       /* call out of sequence */
 #define FMM_EUNSUPPORTED (-6) /* option not built */
+#define FMM_ESIZE (-7)        /* input larger than a fixed capacity */
 
 /* Variants of Sec. 3. */
 #define FMM_UC 0  /* uncorrected Dehnen (2000) expansion */
@@ -160,6 +161,29 @@ int fmm_direct(fmm_ctx *ctx, const double *x, const double *y, const double *z, 
  * FP64, compensated, fixed order.  Synchronises the stream. */
 int fmm_balance(fmm_ctx *ctx, const double *x, const double *y, const double *z, const double *m,
                 const double *ax, const double *ay, const double *az, int64_t n, double *out);
+
+/* The same balance check for callers that cannot allocate device memory: no
+ * context, and no cudaMalloc, cudaFree or other allocating call.  Some callers
+ * cannot allocate at the moment they want this check: codes whose device
+ * memory is handed out by their own fixed pool or arena and may not grow it,
+ * and time-step loops that must not stall on the device synchronisation that
+ * cudaMalloc and cudaFree bring, or risk an allocation failure mid-run.  (The
+ * paper has no counterpart; this is a library convenience.)
+ *
+ * x, y, z, m, ax, ay, az: device, n doubles; out: DEVICE, 2 doubles
+ * {force, torque}, written by a kernel on `cuda_stream` (a cudaStream_t; NULL
+ * = the legacy default stream); the call returns without synchronising.
+ * Scratch is a fixed array in the library's device memory, one record per
+ * 4,096 bodies, so n is limited to 4,194,304: a larger n returns FMM_ESIZE and
+ * launches nothing.  The array (about 197 KB) stays allocated on every GPU
+ * that loads the library until the process exits.  All calls share it: two
+ * calls whose kernels overlap on the GPU race; issue them on one stream, or
+ * order them.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Returns FMM_EINVAL for n < 1 or a NULL pointer, FMM_ECUDA if a launch fails. */
+int fmm_balance_noalloc(const double *x, const double *y, const double *z, const double *m,
+                        const double *ax, const double *ay, const double *az, int64_t n, double *out,
+                        void *cuda_stream);
 
 /* Counts (and stage timings) of the last solve; synchronises the stream. */
 int fmm_get_stats(fmm_ctx *ctx, fmm_stats *out);

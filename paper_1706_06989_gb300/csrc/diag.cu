@@ -5,6 +5,8 @@
 // with A = a (force) and A = X x a (torque).  Both are FP64 with Neumaier
 // compensated sums in a fixed order of combination, so they are
 // reproducible bit for bit.
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace amfmm {
@@ -175,3 +177,100 @@ int fmm_balance(fmm_ctx *c, const double *x, const double *y, const double *z, c
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Balance check without any allocation.
+//
+// The partial sums live in a file-scope device array instead of memory the
+// library allocates: one record of 12 compensated sums (24 doubles) per tile
+// of kNoAllocTile bodies, for at most kNoAllocMaxTiles tiles.  Every GPU that
+// loads the library holds this array (about 197 KB) until the process exits.
+// Each call overwrites the records it reads, so nothing needs clearing, but all
+// calls share the one array: two calls whose kernels overlap on the GPU (for
+// example on two streams) race and can return wrong values.
+// ---------------------------------------------------------------------------
+namespace amfmm {
+namespace {
+
+constexpr int64_t kNoAllocTile = 4096;
+constexpr int64_t kNoAllocMaxTiles = 1024;  // at most 4,194,304 bodies
+static __device__ __align__(256) double g_balance_scratch[kNoAllocMaxTiles * 24];
+
+// same sums as k_balance_partial, over fixed tiles of kNoAllocTile bodies
+__global__ void __launch_bounds__(kBlock) k_balance_tiles(int64_t n, const double *__restrict__ x,
+                                                          const double *__restrict__ y,
+                                                          const double *__restrict__ z,
+                                                          const double *__restrict__ m,
+                                                          const double *__restrict__ ax,
+                                                          const double *__restrict__ ay,
+                                                          const double *__restrict__ az,
+                                                          double *__restrict__ part) {
+  Comp v[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) v[k] = Comp{0, 0};
+  const int64_t b0 = blockIdx.x * kNoAllocTile, b1 = min(n, b0 + kNoAllocTile);
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += kBlock) {
+    const double mu = m[i];
+    const double a[3] = {ax[i], ay[i], az[i]};
+    const double t[3] = {y[i] * az[i] - z[i] * ay[i], z[i] * ax[i] - x[i] * az[i], x[i] * ay[i] - y[i] * ax[i]};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      nadd(v[d], mu * a[d]);
+      nadd(v[3 + d], mu * fabs(a[d]));
+      nadd(v[6 + d], mu * t[d]);
+      nadd(v[9 + d], mu * fabs(t[d]));
+    }
+  }
+  block_reduce<12>(v);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 12; ++k) {
+      part[(blockIdx.x * 12 + k) * 2] = v[k].s;
+      part[(blockIdx.x * 12 + k) * 2 + 1] = v[k].c;
+    }
+}
+
+// Device address of g_balance_scratch for the current device, looked up once
+// per device (host code cannot use the symbol's name as a device pointer).
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+double *g_scratch_ptr[kMaxDevices] = {};
+
+int noalloc_scratch(double **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return FMM_ECUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_balance_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return FMM_ECUDA;
+    }
+    g_scratch_ptr[dev] = static_cast<double *>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return FMM_OK;
+}
+
+}  // namespace
+}  // namespace amfmm
+
+extern "C" int fmm_balance_noalloc(const double *x, const double *y, const double *z, const double *m,
+                                   const double *ax, const double *ay, const double *az, int64_t n,
+                                   double *out, void *cuda_stream) {
+  using namespace amfmm;
+  if (n < 1 || !x || !y || !z || !m || !ax || !ay || !az || !out) return FMM_EINVAL;
+  if (n > kNoAllocTile * kNoAllocMaxTiles) return FMM_ESIZE;
+  double *part = nullptr;
+  const int rc = noalloc_scratch(&part);
+  if (rc != FMM_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int nb = static_cast<int>((n + kNoAllocTile - 1) / kNoAllocTile);
+  k_balance_tiles<<<nb, kBlock, 0, st>>>(n, x, y, z, m, ax, ay, az, part);
+  if (cudaGetLastError() != cudaSuccess) return FMM_ECUDA;
+  k_balance_final<<<1, 32, 0, st>>>(nb, part, out);
+  if (cudaGetLastError() != cudaSuccess) return FMM_ECUDA;
+  return FMM_OK;
+}
