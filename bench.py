@@ -38,7 +38,7 @@ SM_MAX_MHZ = 2070.0
 FP64_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 4
 FP32_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 256
 # algorithmic flops (FMA = 2, rsqrt = 1) per unit of work; derivation in the design doc
-M2L_FLOPS = {"UC": 165, "TC": 281, "TCO": 260}
+M2L_FLOPS = {"UC": 174, "TC": 295, "TCO": 276}
 P2P_FLOPS_PER_BODY_PAIR = 25
 ORACLE_SAMPLE_N = 131072
 
@@ -57,6 +57,10 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-other", action="store_true", help="skip timing the other precision form")
+    p.add_argument("--experiment", choices=["none", "leapfrog", "ensemble"], default="none",
+                   help="leapfrog: two-Plummer binary, uniform KDK steps, momentum drift per step")
+    p.add_argument("--lf-steps", type=int, default=200)
+    p.add_argument("--lf-variants", default="TC:mixed,UC:mixed,TC:fp64")
     return p.parse_args()
 
 
@@ -349,8 +353,117 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def run_leapfrog(a):
+    """Binary of two Plummer spheres (masses 0.6 and 0.9, scale radii 0.05 and
+    0.04, separation 1 on a circular orbit), N = 4,194,304 by default, uniform
+    kick-drift-kick steps of dt = P_orb / 1000; drift of the total linear and
+    angular momentum per step for each (variant, precision)."""
+    import torch
+    from paper_1706_06989_gb300 import fmm, ics
+    n = a.n if a.n != N_DEFAULT else 4194304
+    b = ics.binary_plummer(n, seed=0)
+    p_orb = 2 * np.pi / np.sqrt(1.5)
+    dt = p_orb / 1000
+    dev = torch.device("cuda", 0)
+    v0 = np.stack([b.vx, b.vy, b.vz], 1)
+    p_scale = float(np.sum(b.m * np.linalg.norm(v0, axis=1)))
+    l_scale = float(np.sum(b.m * np.linalg.norm(np.cross(b.pos(), v0), axis=1)))
+    results = []
+    for spec in a.lf_variants.split(","):
+        variant, prec = spec.split(":")
+        st = [torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (b.x, b.y, b.z, b.vx, b.vy, b.vz, b.m)]
+        s = fmm.FMM(theta=a.theta, n_crit=a.n_crit, variant=variant, precision=prec)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, mom = s.leapfrog(*st, dt=dt, nsteps=a.lf_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        mom = mom.cpu().numpy()
+        fin = s.stats()
+        ext = (2.0 ** 21 / fin.scale) if fin.scale > 0 else 0.0
+        dP = np.abs(np.diff(mom[:, :3], axis=0)).max(axis=1) / p_scale
+        dL = np.abs(np.diff(mom[:, 3:], axis=0)).max(axis=1) / l_scale
+        Lz0 = mom[0, 5]
+        results.append({"variant": variant, "precision": prec, "steps": a.lf_steps,
+                        "ms_per_step": ms / (a.lf_steps + 1), "bodies_per_s": n * (a.lf_steps + 1) / (ms / 1e3),
+                        "dP_per_step_max": float(dP.max()), "dP_per_step_rms": float(np.sqrt(np.mean(dP ** 2))),
+                        "dL_per_step_max": float(dL.max()), "dL_per_step_rms": float(np.sqrt(np.mean(dL ** 2))),
+                        "dLz_total_rel": float((mom[-1, 5] - Lz0) / abs(Lz0)),
+                        "orbits": a.lf_steps * dt / p_orb,
+                        "final_tree": {"cube_extent": ext, "depth": fin.depth, "ncell": fin.ncell,
+                                       "n_p2p_body_pairs": fin.p2p_body_pairs}})
+        s.close()
+        del st
+    print(json.dumps({"experiment": "leapfrog", "workload": f"binary_plummer_n{n}_dt_porb_over_1000",
+                      "theta": a.theta, "n_crit": a.n_crit, "scales": {"sum_m_abs_v": p_scale,
+                                                                      "sum_m_abs_xv": l_scale},
+                      "results": results}), flush=True)
+
+
+def run_ensemble(a):
+    """512 independent Plummer systems with N log-uniform in [1024, 65536]
+    (seed per system): the forest solve of all of them in one launch sequence
+    against one solve per system, after choosing n_crit by timing."""
+    import torch
+    from paper_1706_06989_gb300 import fmm, ics
+    prec = a.precision
+    off, b = ics.ensemble(nsys=512, seed=0)
+    dev = torch.device("cuda", 0)
+    x, y, z, m = (torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (b.x, b.y, b.z, b.m))
+    n = b.n
+    s = fmm.FMM(theta=a.theta, n_crit=a.n_crit, variant=a.variant, precision=prec)
+    best, tune = s.autotune_ncrit(x, y, z, m, off, candidates=(16, 25, 32, 64), reps=3)
+    s.set_opts(n_crit=best)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = tuple(torch.empty(n, dtype=torch.float64, device=dev) for _ in range(3))
+    for _ in range(3):
+        s.solve_batch(x, y, z, m, off, out)
+    ts = []
+    for k in range(a.steps):
+        flush.fill_(k & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.solve_batch(x, y, z, m, off, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    batched_ms = statistics.mean(ts)
+    # one solve per system (the same n_crit), same timing rules
+    views = [tuple(v[int(off[k]):int(off[k + 1])] for v in (x, y, z, m)) for k in range(len(off) - 1)]
+    for v in views[:8]:
+        s.solve(*v)
+    tl = []
+    for k in range(max(1, a.steps // 3)):
+        flush.fill_(k & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for v in views:
+            s.solve(*v)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tl.append(e0.elapsed_time(e1))
+    loop_ms = statistics.mean(tl)
+    st = s.stats()
+    print(json.dumps({"experiment": "ensemble", "workload": "512 Plummer systems, N log-uniform [1024, 65536], seed per system",
+                      "n_total": n, "precision": prec, "variant": a.variant, "theta": a.theta,
+                      "autotune_ms": tune, "n_crit": best,
+                      "batched": {"ms": batched_ms, "bodies_per_s": n / (batched_ms / 1e3)},
+                      "one_solve_per_system": {"ms": loop_ms, "bodies_per_s": n / (loop_ms / 1e3)},
+                      "speedup": loop_ms / batched_ms}), flush=True)
+
+
 def main():
     a = _args()
+    if a.experiment == "leapfrog":
+        run_leapfrog(a)
+        return
+    if a.experiment == "ensemble":
+        run_ensemble(a)
+        return
     if a.impl == "reference":
         run_reference(a)
     else:

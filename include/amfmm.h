@@ -27,7 +27,7 @@
  * Errors: every int-returning call returns FMM_OK (0) or a negative code;
  * fmm_last_error gives a one-line message.  A failed call leaves the
  * context usable for a new fmm_build_tree.  Input validation: n >= 1,
- * 0 < theta <= 1 (Sec. 2), n_crit >= 1, order_P == 3; a body with a
+ * 0 < theta <= 1 (Sec. 2), n_crit >= 1, order_P in {3, 4, 5}; a body with a
  * non-finite coordinate or a mass that is not positive and finite is
  * detected on the device and reported as FMM_EINVAL by the next call that
  * synchronises (fmm_build_tree).
@@ -69,7 +69,7 @@ typedef struct fmm_ctx fmm_ctx;
 typedef struct {
   double theta;  /* opening angle, 0 < theta <= 1 (Sec. 2) */
   int n_crit;    /* a cell with at most n_crit bodies is a leaf (Sec. 2: 25) */
-  int order_P;   /* expansion order; 3 (Eqs. 2-4) */
+  int order_P;   /* expansion order: 3 (Eqs. 2-4), or 4, 5 (App. A; FP64 only) */
   int variant;   /* FMM_UC, FMM_TC or FMM_TCO */
   int precision; /* FMM_FP64 or FMM_MIXED */
   double G;      /* gravitational constant applied to the accelerations */
@@ -113,7 +113,7 @@ int fmm_build_tree(fmm_ctx *ctx, const double *x, const double *y, const double 
 
 /* a4 (Eqs. 1-3 and the octupole definition): per cell mass M, centre of
  * mass Z, R_max (the largest body distance from Z) and moments about Z to
- * order 3 (leaf P2M from bodies, then M2M shifts).  Asynchronous. */
+ * order P (leaf P2M from bodies, then M2M shifts).  Asynchronous. */
 int fmm_upward(fmm_ctx *ctx);
 
 /* a5-a8: dual-tree walk under the opening criterion
@@ -136,11 +136,45 @@ int fmm_forces(fmm_ctx *ctx, double *ax, double *ay, double *az);
 int fmm_solve(fmm_ctx *ctx, const double *x, const double *y, const double *z, const double *m,
               int64_t n, double *ax, double *ay, double *az);
 
+/* a13: one solve of nsys independent systems in one launch sequence.  The
+ * bodies are concatenated: system s owns indices [offsets[s], offsets[s+1])
+ * of x, y, z, m (device, offsets[nsys] doubles each); offsets is a HOST array
+ * of nsys + 1 increasing entries with offsets[0] = 0 and no empty system.
+ * Every system gets its own bounding cube, keys and octree (a forest with one
+ * root per system); bodies of different systems never interact.  Outputs as
+ * fmm_forces.  Synchronises the stream (like fmm_build_tree). */
+int fmm_solve_batch(fmm_ctx *ctx, const double *x, const double *y, const double *z, const double *m,
+                    const int64_t *offsets, int nsys, double *ax, double *ay, double *az);
+
+/* a13: picks the leaf size for an ensemble.  Runs fmm_solve_batch once per
+ * candidate n_crit (warm-up) and then `reps` timed times (CUDA events on the
+ * context's stream), writes the mean ms per candidate to ms_out (HOST, ncand
+ * floats, may be NULL) and the fastest candidate to *best (HOST).  The
+ * context's options are restored afterwards (set n_crit to *best with
+ * fmm_set_opts to use it).  ax, ay, az receive the last solve's accelerations.
+ * Synchronises the stream. */
+int fmm_autotune_ncrit(fmm_ctx *ctx, const double *x, const double *y, const double *z, const double *m,
+                       const int64_t *offsets, int nsys, const int *candidates, int ncand, int reps,
+                       double *ax, double *ay, double *az, int *best, float *ms_out);
+
 /* The same solve from HOST arrays (pageable or pinned): copies the bodies to
  * context-owned device buffers, solves, copies the accelerations back and
  * synchronises the stream before returning. */
 int fmm_solve_host(fmm_ctx *ctx, const double *x, const double *y, const double *z,
                    const double *m, int64_t n, double *ax, double *ay, double *az);
+
+/* a14: nsteps uniform kick-drift-kick leapfrog steps of length dt (uniform
+ * steps are what conservation needs, Sec. 4).  Each step: v += a dt/2,
+ * x += v dt, a = solve(x), v += a dt/2; the first acceleration is solved
+ * before the loop.  x, y, z, vx, vy, vz: device, n doubles, updated in place
+ * (caller order); m: device; ax, ay, az: device, n doubles, hold the
+ * accelerations of the final positions on return.  mom: device, 6 (nsteps+1)
+ * doubles or NULL: after step s (s = 0 before the first) the totals
+ * P = sum m v and L = sum m x x v (about the origin), FP64 compensated in a
+ * fixed order.  Synchronises the stream once per solve. */
+int fmm_leapfrog(fmm_ctx *ctx, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                 const double *m, int64_t n, double dt, int nsteps, double *ax, double *ay, double *az,
+                 double *mom);
 
 /* ---- a10 diagnostics (Sec. 3) ---------------------------------------------- */
 
@@ -198,18 +232,21 @@ int fmm_export_keys(fmm_ctx *ctx, uint64_t *keys, int32_t *order);
 int fmm_export_tree(fmm_ctx *ctx, int32_t *begin, int32_t *count, int32_t *level,
                     int32_t *parent, int32_t *first_child, int32_t *nchild, double *M,
                     double *Z, double *Rmax);
-/* moments about Z: ncell x 20 doubles in the order
+/* moments about Z: ncell x (P+1)(P+2)(P+3)/6 doubles (20 at P = 3), orders 0..P
+ * by exponent triple (a,b,c), a = n..0 then b = n-a..0; at P = 3:
  * [M, Mx, My, Mz, Qxx, Qxy, Qxz, Qyy, Qyz, Qzz,
  *  Oxxx, Oxxy, Oxxz, Oxyy, Oxyz, Oxzz, Oyyy, Oyyz, Oyzz, Ozzz] */
 int fmm_export_moments(fmm_ctx *ctx, double *mom);
 /* m2l: n_m2l x 2, p2p: n_p2p x 2 (each pair (min, max)), self: n_self;
  * int32, in the library's processing order (sort them to compare) */
 int fmm_export_lists(fmm_ctx *ctx, int32_t *m2l, int32_t *p2p, int32_t *self);
-/* local expansion of every cell after the downward shift: ncell x 20
+/* local expansion of every cell after the downward shift.  P = 3: ncell x 20
  * doubles [C_x, C_y, C_z, C_xx, C_xy, C_xz, C_yy, C_yz, C_zz, C_xxx, C_xxy,
  * C_xxz, C_xyy, C_xyz, C_xzz, C_yyy, C_yyz, C_yzz, C_zzz, 0]; a body at
  * offset x from Z receives a = -(C_i + C_ij x_j + C_ijk x_j x_k / 2) plus its
- * near-field sum. */
+ * near-field sum.  P = 4, 5: ncell x ((P+1)(P+2)(P+3)/6 - 1) doubles, the
+ * Taylor coefficients L^a of orders 1..P in the moments' multi-index order
+ * (a body at x receives g_k = -sum_a L^(a+e_k) x^a / a!). */
 int fmm_export_locals(fmm_ctx *ctx, double *C);
 
 #ifdef __cplusplus

@@ -88,8 +88,10 @@ int check_opts(fmm_ctx *c, const fmm_opts *o) {
   if (!(o->theta > 0.0 && o->theta <= 1.0))
     return set_error(c, FMM_EINVAL, "theta must satisfy 0 < theta <= 1 (got %g)", o->theta);
   if (o->n_crit < 1) return set_error(c, FMM_EINVAL, "n_crit must be >= 1 (got %d)", o->n_crit);
-  if (o->order_P != 3)
-    return set_error(c, FMM_EUNSUPPORTED, "order_P %d is not built (order 3 only)", o->order_P);
+  if (o->order_P < 3 || o->order_P > 5)
+    return set_error(c, FMM_EUNSUPPORTED, "order_P %d is not built (3, 4 and 5 are)", o->order_P);
+  if (o->order_P != 3 && o->precision != FMM_FP64)
+    return set_error(c, FMM_EUNSUPPORTED, "orders above 3 are built in FP64 only");
   if (o->variant < FMM_UC || o->variant > FMM_TCO)
     return set_error(c, FMM_EINVAL, "variant must be FMM_UC, FMM_TC or FMM_TCO");
   if (o->precision != FMM_FP64 && o->precision != FMM_MIXED)
@@ -148,7 +150,7 @@ void fmm_destroy(fmm_ctx *c) {
   else cudaDeviceSynchronize();
   DBuf *all[] = {&c->key[0], &c->key[1], &c->idx[0], &c->idx[1], &c->order, &c->X, &c->Y, &c->Zb, &c->Mb,
                  &c->cur, &c->flag, &c->incl, &c->lcp, &c->leaf_of, &c->cell_at, &c->near, &c->acc,
-                 &c->status, &c->bbox_part, &c->bbox, &c->begin, &c->count, &c->level, &c->parent,
+                 &c->status, &c->bbox_part, &c->bbox, &c->sys_off, &c->sysid, &c->sbox, &c->begin, &c->count, &c->level, &c->parent,
                  &c->first_child, &c->nchild, &c->S, &c->M, &c->Z, &c->invM, &c->Rmax, &c->rmax2, &c->mom,
                  &c->loc, &c->leaves, &c->front[0], &c->front[1], &c->action, &c->wcount, &c->woff,
                  &c->m2l, &c->p2p, &c->self_list, &c->ekey[0], &c->ekey[1], &c->eval[0], &c->eval[1],
@@ -180,8 +182,14 @@ int fmm_set_timing(fmm_ctx *c, int enable) {
   return FMM_OK;
 }
 
-int fmm_build_tree(fmm_ctx *c, const double *x, const double *y, const double *z, const double *m,
-                   int64_t n, double theta) {
+}  // extern "C"
+
+namespace {
+
+// Common start of a solve of nsys >= 1 independent systems; offsets (host,
+// nsys + 1 entries) or NULL for a single system of n bodies.
+int start_solve(fmm_ctx *c, const double *x, const double *y, const double *z, const double *m, int64_t n,
+                double theta, const int64_t *offsets, int nsys) {
   if (!c) return FMM_EINVAL;
   c->stage = kNone;
   c->errbuf[0] = 0;
@@ -195,18 +203,63 @@ int fmm_build_tree(fmm_ctx *c, const double *x, const double *y, const double *z
   } else {
     c->theta = c->opts.theta;
   }
+  if (nsys < 1) return set_error(c, FMM_EINVAL, "nsys must be >= 1");
   c->x = x;
   c->y = y;
   c->z = z;
   c->m = m;
   c->sz = Sizes();
   c->sz.n = n;
+  c->sz.nsys = nsys;
   c->launches = 0;
+  // system offsets on the device
+  AMFMM_TRY(ensure<int64_t>(c, c->sys_off, static_cast<size_t>(nsys) + 1));
+  if (offsets) {
+    AMFMM_CUDA(c, cudaStreamSynchronize(c->stream));  // the pinned staging buffer is reused
+    int64_t *h = static_cast<int64_t *>(c->hpin);
+    const size_t cap = 4096 / sizeof(int64_t);
+    for (size_t b = 0; b < static_cast<size_t>(nsys) + 1; b += cap) {
+      const size_t cnt = std::min(cap, static_cast<size_t>(nsys) + 1 - b);
+      for (size_t k = 0; k < cnt; ++k) h[k] = offsets[b + k];
+      AMFMM_CUDA(c, cudaMemcpyAsync(ptr<int64_t>(c->sys_off) + b, h, cnt * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, c->stream));
+      AMFMM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+  } else {
+    int64_t *h = static_cast<int64_t *>(c->hpin);
+    AMFMM_CUDA(c, cudaStreamSynchronize(c->stream));
+    h[0] = 0;
+    h[1] = n;
+    AMFMM_CUDA(c, cudaMemcpyAsync(c->sys_off.p, h, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+  }
   timer(c, kTreeBeg);
   AMFMM_TRY(build_tree(c));
   timer(c, kTreeEnd);
   c->stage = kTree;
   return FMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fmm_build_tree(fmm_ctx *c, const double *x, const double *y, const double *z, const double *m,
+                   int64_t n, double theta) {
+  return start_solve(c, x, y, z, m, n, theta, nullptr, 1);
+}
+
+int fmm_solve_batch(fmm_ctx *c, const double *x, const double *y, const double *z, const double *m,
+                    const int64_t *offsets, int nsys, double *ax, double *ay, double *az) {
+  if (!c) return FMM_EINVAL;
+  if (!offsets || nsys < 1) return set_error(c, FMM_EINVAL, "offsets must list nsys >= 1 systems");
+  if (offsets[0] != 0) return set_error(c, FMM_EINVAL, "offsets[0] must be 0");
+  for (int s = 0; s < nsys; ++s)
+    if (offsets[s + 1] <= offsets[s]) return set_error(c, FMM_EINVAL, "system %d is empty or offsets decrease", s);
+  AMFMM_TRY(start_solve(c, x, y, z, m, offsets[nsys], 0.0, offsets, nsys));
+  AMFMM_TRY(fmm_upward(c));
+  AMFMM_TRY(fmm_interact(c));
+  AMFMM_TRY(fmm_downward(c));
+  return fmm_forces(c, ax, ay, az);
 }
 
 int fmm_upward(fmm_ctx *c) {
@@ -351,7 +404,8 @@ int fmm_export_tree(fmm_ctx *c, int32_t *begin, int32_t *count, int32_t *level, 
 int fmm_export_moments(fmm_ctx *c, double *mom) {
   if (!c || !mom) return FMM_EINVAL;
   AMFMM_TRY(need_stage(c, kUp, "fmm_export_moments"));
-  AMFMM_CUDA(c, cudaMemcpyAsync(mom, c->mom.p, static_cast<size_t>(c->sz.ncell) * kMomStride * sizeof(double),
+  AMFMM_CUDA(c, cudaMemcpyAsync(mom, c->mom.p,
+                                static_cast<size_t>(c->sz.ncell) * mom_stride(c->opts.order_P) * sizeof(double),
                                 cudaMemcpyDeviceToDevice, c->stream));
   return FMM_OK;
 }
@@ -371,7 +425,8 @@ int fmm_export_lists(fmm_ctx *c, int32_t *m2l, int32_t *p2p, int32_t *self) {
 int fmm_export_locals(fmm_ctx *c, double *C) {
   if (!c || !C) return FMM_EINVAL;
   AMFMM_TRY(need_stage(c, kDown, "fmm_export_locals"));
-  AMFMM_CUDA(c, cudaMemcpyAsync(C, c->loc.p, static_cast<size_t>(c->sz.ncell) * kLocStride * sizeof(double),
+  AMFMM_CUDA(c, cudaMemcpyAsync(C, c->loc.p,
+                                static_cast<size_t>(c->sz.ncell) * loc_stride(c->opts.order_P) * sizeof(double),
                                 cudaMemcpyDeviceToDevice, c->stream));
   return FMM_OK;
 }

@@ -111,6 +111,7 @@ int downward(fmm_ctx *c) {
   cudaStream_t st = c->stream;
   const int64_t n = c->sz.n;
   AMFMM_TRY(ensure<double>(c, c->acc, 3 * n));
+  if (c->opts.order_P != 3) return downward_general(c);
   for (int lev = 1; lev <= c->sz.depth; ++lev) {
     const int64_t c0 = c->sz.lvl_off[lev], c1 = c->sz.lvl_off[lev + 1];
     if (c1 <= c0) continue;

@@ -34,6 +34,7 @@ struct Sizes {
   int64_t n = 0, ncell = 0, nleaf = 0, n_m2l = 0, n_p2p = 0, n_self = 0;
   int depth = 0;
   int key_which = 0;             // ping-pong slot holding the sorted keys
+  int nsys = 1;                  // independent systems (roots) in the forest
   double lo[3] = {0, 0, 0}, scale = 0;
   int64_t p2p_body_pairs = 0;
   std::vector<int64_t> lvl_off;  // cells of level l are [lvl_off[l], lvl_off[l+1])
@@ -71,7 +72,7 @@ struct fmm_ctx {
   // ---- device buffers ----
   // bodies
   amfmm::DBuf key[2], idx[2], order, X, Y, Zb, Mb, cur, flag, incl, lcp, leaf_of, cell_at,
-      near, acc, status, bbox_part, bbox;
+      near, acc, status, bbox_part, bbox, sys_off, sysid, sbox;
   // cells
   amfmm::DBuf begin, count, level, parent, first_child, nchild, S, M, Z, invM, Rmax,
       rmax2, mom, loc, leaves;
@@ -157,6 +158,14 @@ int p2p_run(fmm_ctx *c);            // p2p.cu: mutual near field
 int p2p_reduce(fmm_ctx *c);         // p2p.cu: per-body fixed-order sums
 int downward(fmm_ctx *c);           // down.cu (L2L, L2P into sorted order)
 int forces(fmm_ctx *c, double *ax, double *ay, double *az);  // down.cu (caller order)
+
+// general order P (expansion.cu)
+int mom_stride(int P);  // moments of order 0..P per cell
+int loc_stride(int P);  // local coefficients per cell (order 3: 20 with padding)
+int upward_general(fmm_ctx *c);
+int m2l_general(fmm_ctx *c);
+int reduce_general(fmm_ctx *c);
+int downward_general(fmm_ctx *c);
 
 void timer(fmm_ctx *c, int slot);
 

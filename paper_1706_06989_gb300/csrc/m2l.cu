@@ -14,7 +14,8 @@
 //     C^B_i = -M_A D_i - Q_A,jk D_ijk / 2, C^B_ij = M_A D_ij, C^B_ijk = -M_A D_ijk.
 // (Q is the extensive quadrupole of Eq. 3; dipoles about the centres of mass
 // vanish and are dropped, as Sec. 2 notes.)  The contraction Q_jk D_ijk is
-// taken through r:  Q_jk D_ijk = 15 r_i (r.Q.r)/R^7 - 3 (2 (Q r)_i + r_i tr Q)/R^5.
+// taken through r:  Q_jk D_ijk = 15 r_i (r.Q.r)/R^7 - 3 (2 (Q r)_i + r_i tr Q)/R^5
+// (evaluated below with the unit vector n = r/R).
 //
 // Torque correction (Eq. 7 with the coefficient of App. A at P = 3):
 //     F_i = (1/6) (M_A O_B,jkl - O_A,jkl M_B) D_ijkl,
@@ -42,92 +43,109 @@ __device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
 
 // Local layout: Cx Cy Cz | Cxx Cxy Cxz Cyy Cyz Czz | Cxxx Cxxy Cxxz Cxyy Cxyz Cxzz Cyyy Cyyz Cyzz Czzz
 // Moment layout: M | Dx Dy Dz | Qxx Qxy Qxz Qyy Qyz Qzz | Oxxx ... Ozzz (same order as locals)
+// Separations below which the FP32 form treats a pair as coincident (its
+// r^-5 terms would leave the FP32 range); FP64 only skips r = 0.
+template <class T>
+__device__ __forceinline__ T min_r2();
+template <>
+__device__ __forceinline__ double min_r2<double>() { return 0.0; }
+template <>
+__device__ __forceinline__ float min_r2<float>() { return 1e-30f; }
+
+// The pair in terms of the unit vector n = r/R: D_i = n_i R^-2,
+// D_ij = (d_ij - 3 n_i n_j) R^-3, D_ijk = (15 n_i n_j n_k - 3 (d_ij n_k + d_jk n_i
+// + d_ki n_j)) R^-4 and D_ijkl S_jkl = (-105 n_i (n.u) + 45 (u_i + n_i (n.t))
+// - 9 t_i) R^-5 with u_i = S_ikl n_k n_l, t_i = S_ijj.  Powers of 1/R are
+// applied one factor at a time to the mass- or moment-scaled terms, so no
+// large power of 1/R is formed on its own (this keeps the FP32 form in range).
 template <class T, int VARIANT>
 __device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, T iMA, T iMB, const T *QA,
                                          const T *QB, const T *OA, const T *OB, T *CA, T *CB) {
-  const T x = r[0], y = r[1], z = r[2];
-  const T xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
-  const T R2 = xx + yy + zz;
+  const T R2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  if (!(R2 > min_r2<T>())) {
+#pragma unroll
+    for (int q = 0; q < 19; ++q) CA[q] = CB[q] = T(0);
+    return;
+  }
   const T Ri = rsqrt_t(R2);
+  const T x = r[0] * Ri, y = r[1] * Ri, z = r[2] * Ri;
+  const T xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+  // unit parts of D_ij and D_ijk
+  const T U2[6] = {T(1) - T(3) * xx, T(-3) * xy, T(-3) * xz, T(1) - T(3) * yy, T(-3) * yz, T(1) - T(3) * zz};
+  const T fxx = T(15) * xx, fyy = T(15) * yy, fzz = T(15) * zz;
+  const T U3[10] = {(fxx - T(9)) * x, (fxx - T(3)) * y, (fxx - T(3)) * z, (fyy - T(3)) * x,
+                    T(15) * xy * z,   (fzz - T(3)) * x, (fyy - T(9)) * y, (fyy - T(3)) * z,
+                    (fzz - T(3)) * y, (fzz - T(9)) * z};
+  // mass-scaled powers: M R^-2, M R^-3, M R^-4
+  const T MB2 = MB * Ri * Ri, MA2 = MA * Ri * Ri;
+  const T MB3 = MB2 * Ri, MA3 = MA2 * Ri;
+  const T MB4 = MB3 * Ri, MA4 = MA3 * Ri;
   const T Ri2 = Ri * Ri;
-  const T R3 = Ri * Ri2;   // R^-3
-  const T R5 = R3 * Ri2;   // R^-5
-  const T R7 = R5 * Ri2;   // R^-7
-  const T a2 = T(-3) * R5; // coefficient of r_i r_j in D_ij, of the d-terms in D_ijk
-  const T a3 = T(15) * R7; // coefficient of r_i r_j r_k in D_ijk
-  // D_i
-  const T D1[3] = {x * R3, y * R3, z * R3};
-  // D_ij
-  const T D2[6] = {a2 * xx + R3, a2 * xy, a2 * xz, a2 * yy + R3, a2 * yz, a2 * zz + R3};
-  // D_ijk
-  const T axx = a3 * xx, ayy = a3 * yy, azz = a3 * zz;
-  const T D3[10] = {(axx + T(3) * a2) * x, (axx + a2) * y, (axx + a2) * z, (ayy + a2) * x,
-                    a3 * xy * z,         (azz + a2) * x, (ayy + T(3) * a2) * y, (ayy + a2) * z,
-                    (azz + a2) * y,      (azz + T(3) * a2) * z};
-  // h = Q_jk D_ijk / 2 = r_i (a3 r.Q.r + a2 trQ)/2 + a2 (Q r)_i
+  // h = Q_jk D_ijk / 2 = R^-4 [n_i (15 n.Q.n - 3 trQ) - 6 (Q n)_i] / 2
   T hA[3], hB[3];
   {
     const T *Q = QB;
     const T qx = Q[0] * x + Q[1] * y + Q[2] * z;
     const T qy = Q[1] * x + Q[3] * y + Q[4] * z;
     const T qz = Q[2] * x + Q[4] * y + Q[5] * z;
-    const T u = T(0.5) * (a3 * (x * qx + y * qy + z * qz) + a2 * (Q[0] + Q[3] + Q[5]));
-    hB[0] = u * x + a2 * qx;
-    hB[1] = u * y + a2 * qy;
-    hB[2] = u * z + a2 * qz;
+    const T w = (T(7.5) * (x * qx + y * qy + z * qz) - T(1.5) * (Q[0] + Q[3] + Q[5])) * Ri2 * Ri2;
+    const T v = T(-3) * Ri2 * Ri2;
+    hB[0] = w * x + v * qx;
+    hB[1] = w * y + v * qy;
+    hB[2] = w * z + v * qz;
   }
   {
     const T *Q = QA;
     const T qx = Q[0] * x + Q[1] * y + Q[2] * z;
     const T qy = Q[1] * x + Q[3] * y + Q[4] * z;
     const T qz = Q[2] * x + Q[4] * y + Q[5] * z;
-    const T u = T(0.5) * (a3 * (x * qx + y * qy + z * qz) + a2 * (Q[0] + Q[3] + Q[5]));
-    hA[0] = u * x + a2 * qx;
-    hA[1] = u * y + a2 * qy;
-    hA[2] = u * z + a2 * qz;
+    const T w = (T(7.5) * (x * qx + y * qy + z * qz) - T(1.5) * (Q[0] + Q[3] + Q[5])) * Ri2 * Ri2;
+    const T v = T(-3) * Ri2 * Ri2;
+    hA[0] = w * x + v * qx;
+    hA[1] = w * y + v * qy;
+    hA[2] = w * z + v * qz;
   }
+  const T nv[3] = {x, y, z};
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    CA[i] = MB * D1[i] + hB[i];
-    CB[i] = -(MA * D1[i] + hA[i]);
+    CA[i] = MB2 * nv[i] + hB[i];
+    CB[i] = -(MA2 * nv[i] + hA[i]);
   }
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    CA[3 + k] = MB * D2[k];
-    CB[3 + k] = MA * D2[k];
+    CA[3 + k] = MB3 * U2[k];
+    CB[3 + k] = MA3 * U2[k];
   }
 #pragma unroll
   for (int k = 0; k < 10; ++k) {
-    CA[9 + k] = MB * D3[k];
-    CB[9 + k] = -(MA * D3[k]);
+    CA[9 + k] = MB4 * U3[k];
+    CB[9 + k] = -(MA4 * U3[k]);
   }
   if (VARIANT != FMM_UC) {
     // S = M_A O_B - M_B O_A (xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)
     T S[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) S[k] = MA * OB[k] - MB * OA[k];
-    // u_i = S_ikl r_k r_l
+    // u_i = S_ikl n_k n_l, t_i = S_ijj
     const T ux = S[0] * xx + S[3] * yy + S[5] * zz + T(2) * (S[1] * xy + S[2] * xz + S[4] * yz);
     const T uy = S[1] * xx + S[6] * yy + S[8] * zz + T(2) * (S[3] * xy + S[4] * xz + S[7] * yz);
     const T uz = S[2] * xx + S[7] * yy + S[9] * zz + T(2) * (S[4] * xy + S[5] * xz + S[8] * yz);
-    // t_i = S_ijj
     const T tx = S[0] + S[3] + S[5];
     const T ty = S[1] + S[6] + S[8];
     const T tz = S[2] + S[7] + S[9];
-    // F = (1/6) D S: (a3/2) u + (a2/2) t [+ r (-105 R^-9 r.u + 45 R^-7 r.t)/6 for TC]
-    const T ha3 = T(0.5) * a3, ha2 = T(0.5) * a2;
-    T F[3] = {ha3 * ux + ha2 * tx, ha3 * uy + ha2 * ty, ha3 * uz + ha2 * tz};
+    // F = (1/6) D_ijkl S_jkl = R^-5 [7.5 u - 1.5 t (+ n (-17.5 n.u + 7.5 n.t) for TC)]
+    T F[3] = {T(7.5) * ux - T(1.5) * tx, T(7.5) * uy - T(1.5) * ty, T(7.5) * uz - T(1.5) * tz};
     if (VARIANT == FMM_TC) {
-      const T R9 = R7 * Ri2;
-      const T w = (T(-17.5) * R9) * (x * ux + y * uy + z * uz) + ha3 * (x * tx + y * ty + z * tz);
+      const T w = T(-17.5) * (x * ux + y * uy + z * uz) + T(7.5) * (x * tx + y * ty + z * tz);
       F[0] += w * x;
       F[1] += w * y;
       F[2] += w * z;
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      CA[i] -= F[i] * iMA;
-      CB[i] += F[i] * iMB;
+      const T f = F[i] * Ri2 * Ri2 * Ri;
+      CA[i] -= f * iMA;
+      CB[i] += f * iMB;
     }
   }
 }
@@ -145,17 +163,11 @@ __global__ void __launch_bounds__(kBlock) k_m2l64(int64_t K, const int2 *__restr
   if (k >= K) return;
   const int A = pairs[k].x, B = pairs[k].y;
   double CA[kLocStride], CB[kLocStride];
-  const double rx = Z[3 * A] - Z[3 * B], ry = Z[3 * A + 1] - Z[3 * B + 1], rz = Z[3 * A + 2] - Z[3 * B + 2];
-  if (rx == 0.0 && ry == 0.0 && rz == 0.0) {
-#pragma unroll
-    for (int q = 0; q < kLocStride; ++q) CA[q] = CB[q] = 0.0;
-  } else {
-    const double r[3] = {rx, ry, rz};
-    const double *mA = mom + static_cast<int64_t>(A) * kMomStride;
-    const double *mB = mom + static_cast<int64_t>(B) * kMomStride;
-    m2l_pair<double, VARIANT>(r, M[A], M[B], invM[A], invM[B], mA + 4, mB + 4, mA + 10, mB + 10, CA, CB);
-    CA[19] = CB[19] = 0.0;
-  }
+  const double r[3] = {Z[3 * A] - Z[3 * B], Z[3 * A + 1] - Z[3 * B + 1], Z[3 * A + 2] - Z[3 * B + 2]};
+  const double *mA = mom + static_cast<int64_t>(A) * kMomStride;
+  const double *mB = mom + static_cast<int64_t>(B) * kMomStride;
+  m2l_pair<double, VARIANT>(r, M[A], M[B], invM[A], invM[B], mA + 4, mB + 4, mA + 10, mB + 10, CA, CB);
+  CA[19] = CB[19] = 0.0;
   double *sa = slots + static_cast<int64_t>(pos[2 * k]) * kLocStride;
   double *sb = slots + static_cast<int64_t>(pos[2 * k + 1]) * kLocStride;
 #pragma unroll
@@ -186,13 +198,8 @@ __global__ void __launch_bounds__(kBlock) k_m2l32(int64_t K, const int2 *__restr
   }
   float CA[kLocStride], CB[kLocStride];
   const float r[3] = {(a[0] - b[0]) + (a[3] - b[3]), (a[1] - b[1]) + (a[4] - b[4]), (a[2] - b[2]) + (a[5] - b[5])};
-  if (r[0] == 0.f && r[1] == 0.f && r[2] == 0.f) {
-#pragma unroll
-    for (int q = 0; q < kLocStride; ++q) CA[q] = CB[q] = 0.f;
-  } else {
-    m2l_pair<float, VARIANT>(r, a[6], b[6], a[7], b[7], a + 8, b + 8, a + 14, b + 14, CA, CB);
-    CA[19] = CB[19] = 0.f;
-  }
+  m2l_pair<float, VARIANT>(r, a[6], b[6], a[7], b[7], a + 8, b + 8, a + 14, b + 14, CA, CB);
+  CA[19] = CB[19] = 0.f;
   float *sa = slots + static_cast<int64_t>(pos[2 * k]) * kLocStride;
   float *sb = slots + static_cast<int64_t>(pos[2 * k + 1]) * kLocStride;
 #pragma unroll
@@ -256,13 +263,23 @@ __global__ void k_m2l_reduce(int32_t ncell, const int32_t *__restrict__ off, con
   double acc = 0.0;
   int s = s0;
   if (sizeof(T) == sizeof(float)) {
-    // FP32 slots: pairwise sums of eight in FP32, accumulated in FP64
+    // FP32 slots: pairwise sums of 32 in FP32, accumulated in FP64
+    for (; s + 32 <= s1; s += 32) {
+      T g[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = slots[static_cast<int64_t>(s + 8 * h + u) * kLocStride + q];
+        g[h] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+      }
+      acc += static_cast<double>((g[0] + g[1]) + (g[2] + g[3]));
+    }
     for (; s + 8 <= s1; s += 8) {
       T v[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) v[u] = slots[static_cast<int64_t>(s + u) * kLocStride + q];
-      const T g = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
-      acc += static_cast<double>(g);
+      acc += static_cast<double>(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
     }
   } else {
     for (; s + 4 <= s1; s += 4) {
@@ -322,7 +339,7 @@ int bits_for(int64_t v) {
 int m2l_prepare(fmm_ctx *c) {
   cudaStream_t st = c->stream;
   const int64_t K = c->sz.n_m2l, nc = c->sz.ncell, E = 2 * K;
-  AMFMM_TRY(ensure<double>(c, c->loc, static_cast<size_t>(kLocStride) * nc));
+  AMFMM_TRY(ensure<double>(c, c->loc, static_cast<size_t>(loc_stride(c->opts.order_P)) * nc));
   AMFMM_TRY(ensure<int32_t>(c, c->m2l_off, nc + 1));
   if (E > 0x7fffffffLL) return set_error(c, FMM_EUNSUPPORTED, "too many M2L pairs (%lld)", (long long)K);
   int32_t *off = ptr<int32_t>(c->m2l_off);
@@ -344,7 +361,7 @@ int m2l_prepare(fmm_ctx *c) {
   AMFMM_TRY(launched(c, "m2l_inverse"));
   const bool fp32 = c->opts.precision == FMM_MIXED;
   const size_t esz = fp32 ? sizeof(float) : sizeof(double);
-  AMFMM_TRY(ensure_bytes(c, c->m2l_slots, static_cast<size_t>(E) * kLocStride * esz));
+  AMFMM_TRY(ensure_bytes(c, c->m2l_slots, static_cast<size_t>(E) * loc_stride(c->opts.order_P) * esz));
   if (fp32) {
     AMFMM_TRY(ensure<float>(c, c->cell32, static_cast<size_t>(kCell32) * nc));
     k_cell32<<<grid_for(nc, 256), 256, 0, st>>>(static_cast<int32_t>(nc), ptr<double>(c->Z), ptr<double>(c->M),
@@ -357,11 +374,13 @@ int m2l_prepare(fmm_ctx *c) {
 int m2l_run(fmm_ctx *c) {
   const int64_t K = c->sz.n_m2l;
   if (K == 0) return FMM_OK;
+  if (c->opts.order_P != 3) return m2l_general(c);
   if (c->opts.precision == FMM_MIXED) return launch_m2l32(c, K);
   return launch_m2l64(c, K);
 }
 
 int m2l_reduce(fmm_ctx *c) {
+  if (c->opts.order_P != 3) return reduce_general(c);
   cudaStream_t st = c->stream;
   const int64_t K = c->sz.n_m2l, nc = c->sz.ncell;
   if (K == 0) {

@@ -44,6 +44,15 @@ struct P2PSmem {
 
 // Coordinates a lane works with: absolute in FP64; relative to Z_A (computed
 // in FP64, rounded once) in the mixed form.
+// below this squared separation the FP32 form treats two bodies as coincident
+// (their 1/r^3 would leave the FP32 range); FP64 only skips r = 0
+template <class T>
+__device__ __forceinline__ T p2p_min_r2();
+template <>
+__device__ __forceinline__ double p2p_min_r2<double>() { return 0.0; }
+template <>
+__device__ __forceinline__ float p2p_min_r2<float>() { return 1e-30f; }
+
 template <class T>
 __device__ __forceinline__ T coord(double v, double z);
 template <>
@@ -103,7 +112,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
       for (int i = 0; i < nr; ++i) {
         const T dx = sm.row[i][0] - xj, dy = sm.row[i][1] - yj, dz = sm.row[i][2] - zj;
         const T r2 = dx * dx + dy * dy + dz * dz;
-        if (valid && r2 > T(0)) {
+        if (valid && r2 > p2p_min_r2<T>()) {
           const T ri = rsqrt_t(r2);
           const T r3 = ri * ri * ri;
           const T si = sm.row[i][3] * r3;
@@ -170,7 +179,25 @@ __global__ void k_p2p_reduce(int64_t n, const int32_t *__restrict__ leaf_of, con
   const int L = leaf_of[i];
   const int t = static_cast<int>(i - begin[L]);
   double a0 = near[i], a1 = near[n + i], a2 = near[2 * n + i];
-  for (int e = offB[L]; e < offB[L + 1]; ++e) {
+  int e = offB[L];
+  const int e1 = offB[L + 1];
+  if (sizeof(T) == sizeof(float)) {
+    // FP32 partials: sums of eight in FP32 (fixed order), accumulated in FP64
+    for (; e + 8 <= e1; e += 8) {
+      T s0 = T(0), s1 = T(0), s2 = T(0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const T *p = slots + poff[e + u] + 3 * t;
+        s0 += p[0];
+        s1 += p[1];
+        s2 += p[2];
+      }
+      a0 += static_cast<double>(s0);
+      a1 += static_cast<double>(s1);
+      a2 += static_cast<double>(s2);
+    }
+  }
+  for (; e < e1; ++e) {
     const T *p = slots + poff[e] + 3 * t;
     a0 += static_cast<double>(p[0]);
     a1 += static_cast<double>(p[1]);

@@ -13,7 +13,9 @@ constexpr int kScanTile = kScanBlock * kScanItems;
 constexpr int kSortBlock = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortBlock * kSortItems;
-constexpr int kRadix = 256;
+constexpr int kDigitBits = 9;
+constexpr int kRadix = 1 << kDigitBits;  // 512 buckets per pass
+constexpr unsigned kDigitMask = kRadix - 1;
 
 // ---- element operations for the scans ----
 __device__ __forceinline__ int32_t vadd(int32_t a, int32_t b) { return a + b; }
@@ -161,17 +163,21 @@ template <class K>
 __global__ void k_radix_hist(const K *__restrict__ key, int64_t n, int shift,
                              int32_t *__restrict__ hist, int ntiles) {
   __shared__ int cnt[kRadix];
-  cnt[threadIdx.x] = 0;
+  for (int d = threadIdx.x; d < kRadix; d += kSortBlock) cnt[d] = 0;
   __syncthreads();
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
   for (int k = 0; k < kSortItems; ++k) {
     int64_t i = base + static_cast<int64_t>(k) * kSortBlock + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[static_cast<int>((key[i] >> shift) & 0xff)], 1);
+    if (i < n) atomicAdd(&cnt[static_cast<int>((key[i] >> shift) & kDigitMask)], 1);
   }
   __syncthreads();
-  hist[static_cast<int64_t>(threadIdx.x) * ntiles + blockIdx.x] = cnt[threadIdx.x];
+  for (int d = threadIdx.x; d < kRadix; d += kSortBlock)
+    hist[static_cast<int64_t>(d) * ntiles + blockIdx.x] = cnt[d];
 }
 
+// Stable scatter of one tile: keys are taken in index order, kSortBlock at a
+// time; within a round, equal digits rank by lane (warp match) and by warp
+// (prefix over the per-warp counts), after all earlier rounds of the tile.
 template <class K>
 __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(
     const K *__restrict__ key, const uint32_t *__restrict__ val, int64_t n, int shift,
@@ -180,8 +186,10 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(
   __shared__ int wc[kSortBlock / 32][kRadix + 1];
   __shared__ int wp[kSortBlock / 32][kRadix + 1];
   const int t = threadIdx.x, w = t >> 5;
-  run[t] = 0;
-  for (int q = 0; q < kSortBlock / 32; ++q) wc[q][t] = 0;
+  for (int d = t; d < kRadix; d += kSortBlock) {
+    run[d] = 0;
+    for (int q = 0; q < kSortBlock / 32; ++q) wc[q][d] = 0;
+  }
   if (t < kSortBlock / 32) wc[t][kRadix] = 0;
   __syncthreads();
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
@@ -191,22 +199,22 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(
     const bool valid = i < n;
     K k = valid ? key[i] : K(0);
     uint32_t v = valid ? val[i] : 0u;
-    int d = valid ? static_cast<int>((k >> shift) & 0xff) : kRadix;
+    int d = valid ? static_cast<int>((k >> shift) & kDigitMask) : kRadix;
     unsigned peers = __match_any_sync(0xffffffffu, d);
     int wrank = __popc(peers & lt);
     if (wrank == 0) wc[w][d] = __popc(peers);
     __syncthreads();
-    {
-      int s = run[t];
+    for (int dd = t; dd < kRadix; dd += kSortBlock) {
+      int s = run[dd];
 #pragma unroll
       for (int q = 0; q < kSortBlock / 32; ++q) {
-        wp[q][t] = s;
-        s += wc[q][t];
-        wc[q][t] = 0;
+        wp[q][dd] = s;
+        s += wc[q][dd];
+        wc[q][dd] = 0;
       }
-      run[t] = s;
-      if (t < kSortBlock / 32) wc[t][kRadix] = 0;
+      run[dd] = s;
     }
+    if (t < kSortBlock / 32) wc[t][kRadix] = 0;
     __syncthreads();
     if (valid) {
       int64_t pos = static_cast<int64_t>(offs[static_cast<int64_t>(d) * ntiles + blockIdx.x]) + wp[w][d] + wrank;
@@ -229,7 +237,9 @@ int radix_sort(fmm_ctx *c, DBuf key[2], DBuf val[2], int64_t n, int bits, int *w
   int32_t *hist = ptr<int32_t>(c->sort_hist);
   int32_t *offs = hist + nh;
   int cur = 0;
-  for (int shift = 0; shift < bits; shift += 8) {
+  // equal digit widths of at most kDigitBits bits
+  const int passes = (bits + kDigitBits - 1) / kDigitBits;
+  for (int p = 0, shift = 0; p < passes; ++p, shift += kDigitBits) {
     k_radix_hist<K><<<ntiles, kSortBlock, 0, c->stream>>>(ptr<K>(key[cur]), n, shift, hist, ntiles);
     AMFMM_TRY(launched(c, "radix_hist"));
     AMFMM_TRY(exclusive_scan_i32(c, hist, offs, nh, nullptr));

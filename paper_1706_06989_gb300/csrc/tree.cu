@@ -10,6 +10,7 @@
 // order, other cells sum their children in octant order, Z = S / M, and R_max
 // is the exact maximum over the cell's bodies.
 #include "internal.cuh"
+#include "geom.cuh"
 
 namespace amfmm {
 namespace {
@@ -122,6 +123,106 @@ __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ 
   idx[i] = static_cast<uint32_t>(i);
 }
 
+// ---------------------------------------------------------------------------
+// a13: a forest of independent systems (concatenated, system s owns caller
+// indices [off[s], off[s+1])).  Every system gets its own bounding cube and
+// keys; a second stable sort pass groups the bodies by system, so each
+// system's bodies stay in key order and every root covers one system.
+// ---------------------------------------------------------------------------
+// one block per system: its cube (lo, scale), the system id of its bodies and
+// the bad-data flag
+__global__ void k_bbox_sys(const double *__restrict__ x, const double *__restrict__ y,
+                           const double *__restrict__ z, const double *__restrict__ m,
+                           const int64_t *__restrict__ off, double *__restrict__ sbox,
+                           int32_t *__restrict__ sysid, int *__restrict__ status) {
+  const int s = blockIdx.x;
+  const int64_t b = off[s], e = off[s + 1];
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  bool bad = false;
+  for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+    const double p[3] = {x[i], y[i], z[i]};
+    const double mi = m[i];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      bad |= !isfinite(p[d]);
+      lo[d] = fmin(lo[d], p[d]);
+      hi[d] = fmax(hi[d], p[d]);
+    }
+    bad |= !(mi > 0.0) || !isfinite(mi);
+    sysid[i] = s;
+  }
+  if (bad) atomicOr(status, 1);
+  __shared__ double sh[6][kBlock / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+      hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+    }
+    if (lane == 0) {
+      sh[d][w] = lo[d];
+      sh[3 + d][w] = hi[d];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int d = 0; d < 3; ++d)
+    for (int q = 1; q < kBlock / 32; ++q) {
+      sh[d][0] = fmin(sh[d][0], sh[d][q]);
+      sh[3 + d][0] = fmax(sh[3 + d][0], sh[3 + d][q]);
+    }
+  double ext = __dsub_rn(sh[3][0], sh[0][0]);
+  ext = fmax(ext, __dsub_rn(sh[4][0], sh[1][0]));
+  ext = fmax(ext, __dsub_rn(sh[5][0], sh[2][0]));
+  for (int d = 0; d < 3; ++d) sbox[4 * s + d] = sh[d][0];
+  sbox[4 * s + 3] = ext > 0.0 ? __ddiv_rn(2097152.0, ext) : 0.0;
+}
+
+__global__ void k_keys_sys(const double *__restrict__ x, const double *__restrict__ y,
+                           const double *__restrict__ z, int64_t n, const double *__restrict__ sbox,
+                           const int32_t *__restrict__ sysid, uint64_t *__restrict__ key,
+                           uint32_t *__restrict__ idx) {
+  int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const double *b = sbox + 4 * sysid[i];
+  uint64_t qx = quantise(x[i], b[0], b[3]), qy = quantise(y[i], b[1], b[3]), qz = quantise(z[i], b[2], b[3]);
+  key[i] = spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
+  idx[i] = static_cast<uint32_t>(i);
+}
+
+// second pass: (system of the body at sorted position s, s)
+__global__ void k_sys_keys(int64_t n, const uint32_t *__restrict__ idx, const int32_t *__restrict__ sysid,
+                           uint32_t *__restrict__ skey, uint32_t *__restrict__ sval) {
+  int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (s >= n) return;
+  skey[s] = static_cast<uint32_t>(sysid[idx[s]]);
+  sval[s] = static_cast<uint32_t>(s);
+}
+
+__global__ void k_gather_sorted(int64_t n, const uint32_t *__restrict__ perm, const uint64_t *__restrict__ k1,
+                                const uint32_t *__restrict__ i1, uint64_t *__restrict__ k2,
+                                uint32_t *__restrict__ i2) {
+  int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= n) return;
+  k2[t] = k1[perm[t]];
+  i2[t] = i1[perm[t]];
+}
+
+// level 0: one root per system
+__global__ void k_roots(int32_t nsys, const int64_t *__restrict__ off, int32_t *__restrict__ begin,
+                        int32_t *__restrict__ count, int32_t *__restrict__ level, int32_t *__restrict__ parent,
+                        int32_t *__restrict__ first_child, int32_t *__restrict__ nchild) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys) return;
+  begin[s] = static_cast<int32_t>(off[s]);
+  count[s] = static_cast<int32_t>(off[s + 1] - off[s]);
+  level[s] = 0;
+  parent[s] = -1;
+  first_child[s] = -1;
+  nchild[s] = 0;
+}
+
 // Gather the bodies into key order; lcp[s] = octal digits shared by keys s-1, s.
 __global__ void k_permute(const double *__restrict__ x, const double *__restrict__ y,
                           const double *__restrict__ z, const double *__restrict__ m,
@@ -129,7 +230,7 @@ __global__ void k_permute(const double *__restrict__ x, const double *__restrict
                           int64_t n, double *__restrict__ X, double *__restrict__ Y,
                           double *__restrict__ Zb, double *__restrict__ Mb,
                           int32_t *__restrict__ order, int32_t *__restrict__ lcp,
-                          int32_t *__restrict__ cur) {
+                          int32_t *__restrict__ cur, const int32_t *__restrict__ sysid) {
   int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (s >= n) return;
   const uint32_t o = idx[s];
@@ -144,7 +245,7 @@ __global__ void k_permute(const double *__restrict__ x, const double *__restrict
     l = d == 0 ? kMaxLevel : (__clzll(static_cast<long long>(d)) - 1) / 3;
   }
   lcp[s] = l;
-  cur[s] = 0;
+  cur[s] = sysid ? sysid[o] : 0;  // root of the body's system
 }
 
 // ---------------------------------------------------------------------------
@@ -269,23 +370,9 @@ __global__ void k_leaf_upward(int32_t nleaf, const int32_t *__restrict__ leaves,
   if (q >= nleaf) return;
   const int c = leaves[q];
   const int b = begin[c], e = b + count[c];
-  double sx = 0.0, sy = 0.0, sz = 0.0, mm = 0.0;
-  for (int i = b; i < e; ++i) {
-    const double mu = Mb[i];
-    sx = __dadd_rn(sx, __dmul_rn(mu, X[i]));
-    sy = __dadd_rn(sy, __dmul_rn(mu, Y[i]));
-    sz = __dadd_rn(sz, __dmul_rn(mu, Zb[i]));
-    mm = __dadd_rn(mm, mu);
-  }
-  const double zx = __ddiv_rn(sx, mm), zy = __ddiv_rn(sy, mm), zz = __ddiv_rn(sz, mm);
-  S[3 * c] = sx;
-  S[3 * c + 1] = sy;
-  S[3 * c + 2] = sz;
-  M[c] = mm;
-  Z[3 * c] = zx;
-  Z[3 * c + 1] = zy;
-  Z[3 * c + 2] = zz;
-  invM[c] = 1.0 / mm;
+  double zc[3];
+  leaf_com(c, b, e, X, Y, Zb, Mb, S, M, Z, invM, zc);
+  const double zx = zc[0], zy = zc[1], zz = zc[2], mm = M[c];
   double mo[kMomStride];
 #pragma unroll
   for (int k = 0; k < kMomStride; ++k) mo[k] = 0.0;
@@ -297,12 +384,13 @@ __global__ void k_leaf_upward(int32_t nleaf, const int32_t *__restrict__ leaves,
 }
 
 // One level of internal cells: S, M from the children in octant order, then
-// the moments shifted from each child centre to Z (M2M, exact algebra):
-//   with s = Z_child - Z,
-//   D_i   += D_i' + M' s_i
-//   Q_ij  += Q_ij' + D_i' s_j + D_j' s_i + M' s_i s_j
-//   O_ijk += O_ijk' + (Q_ij' s_k + Q_ik' s_j + Q_jk' s_i)
-//            + (D_i' s_j s_k + D_j' s_i s_k + D_k' s_i s_j) + M' s_i s_j s_k
+// the moments shifted from each child centre to Z (M2M, exact algebra for the
+// raw moments Sum mu x^a): with s = Z_child - Z,
+//   Q_ij  += Q_ij' + M' s_i s_j
+//   O_ijk += O_ijk' + (Q_ij' s_k + Q_ik' s_j + Q_jk' s_i) + M' s_i s_j s_k
+// The child dipoles D' (zero about a centre of mass up to rounding, Sec. 2)
+// are left out of the shift; the parent's dipole is the shift of the child
+// monopoles, D_i = Sum M' s_i.
 __global__ void k_internal_upward(int32_t c0, int32_t c1, const int32_t *__restrict__ first_child,
                                   const int32_t *__restrict__ nchild, double *__restrict__ S,
                                   double *__restrict__ M, double *__restrict__ Z,
@@ -312,22 +400,9 @@ __global__ void k_internal_upward(int32_t c0, int32_t c1, const int32_t *__restr
   const int nch = nchild[c];
   if (nch == 0) return;
   const int f = first_child[c];
-  double sx = 0.0, sy = 0.0, sz = 0.0, mm = 0.0;
-  for (int k = f; k < f + nch; ++k) {
-    sx = __dadd_rn(sx, S[3 * k]);
-    sy = __dadd_rn(sy, S[3 * k + 1]);
-    sz = __dadd_rn(sz, S[3 * k + 2]);
-    mm = __dadd_rn(mm, M[k]);
-  }
-  const double zx = __ddiv_rn(sx, mm), zy = __ddiv_rn(sy, mm), zz = __ddiv_rn(sz, mm);
-  S[3 * c] = sx;
-  S[3 * c + 1] = sy;
-  S[3 * c + 2] = sz;
-  M[c] = mm;
-  Z[3 * c] = zx;
-  Z[3 * c + 1] = zy;
-  Z[3 * c + 2] = zz;
-  invM[c] = 1.0 / mm;
+  double zc[3];
+  parent_com(c, f, nch, S, M, Z, invM, zc);
+  const double zx = zc[0], zy = zc[1], zz = zc[2], mm = M[c];
   double p[kMomStride];
 #pragma unroll
   for (int k = 0; k < kMomStride; ++k) p[k] = 0.0;
@@ -335,19 +410,15 @@ __global__ void k_internal_upward(int32_t c0, int32_t c1, const int32_t *__restr
     const double *q = mom + static_cast<int64_t>(k) * kMomStride;
     const double s[3] = {Z[3 * k] - zx, Z[3 * k + 1] - zy, Z[3 * k + 2] - zz};
     const double Mc = q[0];
-    const double D[3] = {q[1], q[2], q[3]};
+    const double Ms[3] = {Mc * s[0], Mc * s[1], Mc * s[2]};
     // symmetric Q' as a full matrix
     const double Q[3][3] = {{q[4], q[5], q[6]}, {q[5], q[7], q[8]}, {q[6], q[8], q[9]}};
-    p[0] += Mc;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) p[1 + i] += D[i] + Mc * s[i];
+    for (int i = 0; i < 3; ++i) p[1 + i] += Ms[i];
     // Q: xx xy xz yy yz zz
     const int qi[6] = {0, 0, 0, 1, 1, 2}, qj[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
-    for (int t = 0; t < 6; ++t) {
-      const int i = qi[t], j = qj[t];
-      p[4 + t] += Q[i][j] + D[i] * s[j] + D[j] * s[i] + Mc * s[i] * s[j];
-    }
+    for (int t = 0; t < 6; ++t) p[4 + t] += Q[qi[t]][qj[t]] + Ms[qi[t]] * s[qj[t]];
     // O: xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
     const int oi[10] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 2};
     const int oj[10] = {0, 0, 0, 1, 1, 2, 1, 1, 2, 2};
@@ -355,9 +426,7 @@ __global__ void k_internal_upward(int32_t c0, int32_t c1, const int32_t *__restr
 #pragma unroll
     for (int t = 0; t < 10; ++t) {
       const int i = oi[t], j = oj[t], l = ok[t];
-      p[10 + t] += q[10 + t] + (Q[i][j] * s[l] + Q[i][l] * s[j] + Q[j][l] * s[i]) +
-                   (D[i] * s[j] * s[l] + D[j] * s[i] * s[l] + D[l] * s[i] * s[j]) +
-                   Mc * s[i] * s[j] * s[l];
+      p[10 + t] += q[10 + t] + (Q[i][j] * s[l] + Q[i][l] * s[j] + Q[j][l] * s[i]) + Ms[i] * s[j] * s[l];
     }
   }
   p[0] = mm;
@@ -438,15 +507,43 @@ int build_tree(fmm_ctx *c) {
 
   int *status = ptr<int>(c->status);
   AMFMM_CUDA(c, cudaMemsetAsync(status, 0, sizeof(int) * 4, st));
-  k_bbox_partial<<<nbb, kBlock, 0, st>>>(c->x, c->y, c->z, c->m, n, ptr<double>(c->bbox_part), status);
-  AMFMM_TRY(launched(c, "bbox_partial"));
-  k_bbox_final<<<1, kBlock, 0, st>>>(ptr<double>(c->bbox_part), nbb, ptr<double>(c->bbox));
-  AMFMM_TRY(launched(c, "bbox_final"));
-  k_keys<<<grid_for(n, kBlock), kBlock, 0, st>>>(c->x, c->y, c->z, n, ptr<double>(c->bbox),
-                                                 ptr<uint64_t>(c->key[0]), ptr<uint32_t>(c->idx[0]));
-  AMFMM_TRY(launched(c, "keys"));
+  const int nsys = c->sz.nsys;
   int which = 0;
-  AMFMM_TRY(radix_sort_u64(c, c->key, c->idx, n, 63, &which));
+  if (nsys == 1) {
+    k_bbox_partial<<<nbb, kBlock, 0, st>>>(c->x, c->y, c->z, c->m, n, ptr<double>(c->bbox_part), status);
+    AMFMM_TRY(launched(c, "bbox_partial"));
+    k_bbox_final<<<1, kBlock, 0, st>>>(ptr<double>(c->bbox_part), nbb, ptr<double>(c->bbox));
+    AMFMM_TRY(launched(c, "bbox_final"));
+    k_keys<<<grid_for(n, kBlock), kBlock, 0, st>>>(c->x, c->y, c->z, n, ptr<double>(c->bbox),
+                                                   ptr<uint64_t>(c->key[0]), ptr<uint32_t>(c->idx[0]));
+    AMFMM_TRY(launched(c, "keys"));
+    AMFMM_TRY(radix_sort_u64(c, c->key, c->idx, n, 63, &which));
+  } else {
+    AMFMM_TRY(ensure<double>(c, c->sbox, 4 * static_cast<size_t>(nsys)));
+    AMFMM_TRY(ensure<int32_t>(c, c->sysid, n));
+    k_bbox_sys<<<nsys, kBlock, 0, st>>>(c->x, c->y, c->z, c->m, ptr<int64_t>(c->sys_off), ptr<double>(c->sbox),
+                                        ptr<int32_t>(c->sysid), status);
+    AMFMM_TRY(launched(c, "bbox_sys"));
+    k_keys_sys<<<grid_for(n, kBlock), kBlock, 0, st>>>(c->x, c->y, c->z, n, ptr<double>(c->sbox),
+                                                       ptr<int32_t>(c->sysid), ptr<uint64_t>(c->key[0]),
+                                                       ptr<uint32_t>(c->idx[0]));
+    AMFMM_TRY(launched(c, "keys_sys"));
+    int w1 = 0;
+    AMFMM_TRY(radix_sort_u64(c, c->key, c->idx, n, 63, &w1));
+    AMFMM_TRY(ensure<uint32_t>(c, c->ekey[0], n));
+    AMFMM_TRY(ensure<uint32_t>(c, c->eval[0], n));
+    k_sys_keys<<<grid_for(n, kBlock), kBlock, 0, st>>>(n, ptr<uint32_t>(c->idx[w1]), ptr<int32_t>(c->sysid),
+                                                       ptr<uint32_t>(c->ekey[0]), ptr<uint32_t>(c->eval[0]));
+    AMFMM_TRY(launched(c, "sys_keys"));
+    int w2 = 0, sbits = 1;
+    while ((int64_t(1) << sbits) <= nsys) ++sbits;
+    AMFMM_TRY(radix_sort_u32(c, c->ekey, c->eval, n, sbits, &w2));
+    k_gather_sorted<<<grid_for(n, kBlock), kBlock, 0, st>>>(n, ptr<uint32_t>(c->eval[w2]), ptr<uint64_t>(c->key[w1]),
+                                                            ptr<uint32_t>(c->idx[w1]), ptr<uint64_t>(c->key[w1 ^ 1]),
+                                                            ptr<uint32_t>(c->idx[w1 ^ 1]));
+    AMFMM_TRY(launched(c, "gather_sorted"));
+    which = w1 ^ 1;
+  }
   const uint64_t *skey = ptr<uint64_t>(c->key[which]);
   const uint32_t *sidx = ptr<uint32_t>(c->idx[which]);
   AMFMM_TRY(ensure<int32_t>(c, c->lcp, n));
@@ -454,23 +551,20 @@ int build_tree(fmm_ctx *c) {
   k_permute<<<grid_for(n, kBlock), kBlock, 0, st>>>(c->x, c->y, c->z, c->m, skey, sidx, n,
                                                     ptr<double>(c->X), ptr<double>(c->Y),
                                                     ptr<double>(c->Zb), ptr<double>(c->Mb),
-                                                    ptr<int32_t>(c->order), lcp, ptr<int32_t>(c->cur));
+                                                    ptr<int32_t>(c->order), lcp, ptr<int32_t>(c->cur),
+                                                    nsys == 1 ? nullptr : ptr<int32_t>(c->sysid));
   AMFMM_TRY(launched(c, "permute"));
   c->sz.key_which = which;
 
-  // octree level by level
-  int64_t cap_cells = std::max<int64_t>(1024, n / 2 + 64);
+  // octree level by level, from one root per system
+  int64_t cap_cells = std::max<int64_t>(std::max<int64_t>(1024, n / 2 + 64), 2 * static_cast<int64_t>(nsys));
   AMFMM_TRY(ensure_cells(c, cap_cells, 0));
-  {
-    // root
-    int32_t root[6] = {0, static_cast<int32_t>(n), 0, -1, -1, 0};
-    int32_t *h = static_cast<int32_t *>(c->hpin);
-    for (int k = 0; k < 6; ++k) h[k] = root[k];
-    DBuf *ib[] = {&c->begin, &c->count, &c->level, &c->parent, &c->first_child, &c->nchild};
-    for (int k = 0; k < 6; ++k)
-      AMFMM_CUDA(c, cudaMemcpyAsync(ib[k]->p, h + k, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-  }
-  c->sz.lvl_off.assign({0, 1});
+  k_roots<<<grid_for(nsys, kBlock), kBlock, 0, st>>>(nsys, ptr<int64_t>(c->sys_off), ptr<int32_t>(c->begin),
+                                                     ptr<int32_t>(c->count), ptr<int32_t>(c->level),
+                                                     ptr<int32_t>(c->parent), ptr<int32_t>(c->first_child),
+                                                     ptr<int32_t>(c->nchild));
+  AMFMM_TRY(launched(c, "roots"));
+  c->sz.lvl_off.assign({0, static_cast<int64_t>(nsys)});
   int32_t *flag = ptr<int32_t>(c->flag);
   int32_t *excl = ptr<int32_t>(c->incl);
   int32_t *total = ptr<int32_t>(c->totals);
@@ -531,7 +625,8 @@ int build_tree(fmm_ctx *c) {
     AMFMM_CUDA(c, cudaMemcpyAsync(h, total, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     AMFMM_CUDA(c, cudaMemcpyAsync(h + 1, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     double *hb = reinterpret_cast<double *>(h + 4);
-    AMFMM_CUDA(c, cudaMemcpyAsync(hb, c->bbox.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    AMFMM_CUDA(c, cudaMemcpyAsync(hb, c->sz.nsys == 1 ? c->bbox.p : c->sbox.p, 4 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, st));
     AMFMM_CUDA(c, cudaStreamSynchronize(st));
     c->sz.nleaf = h[0];
     for (int d = 0; d < 3; ++d) c->sz.lo[d] = hb[d];
@@ -551,7 +646,10 @@ int upward(fmm_ctx *c) {
   AMFMM_TRY(ensure<double>(c, c->invM, nc));
   AMFMM_TRY(ensure<double>(c, c->Rmax, nc));
   AMFMM_TRY(ensure<unsigned long long>(c, c->rmax2, nc));
-  AMFMM_TRY(ensure<double>(c, c->mom, static_cast<size_t>(kMomStride) * nc));
+  AMFMM_TRY(ensure<double>(c, c->mom, static_cast<size_t>(mom_stride(c->opts.order_P)) * nc));
+  if (c->opts.order_P != 3) {
+    AMFMM_TRY(upward_general(c));
+  } else {
   k_leaf_upward<<<grid_for(c->sz.nleaf, 128), 128, 0, st>>>(
       static_cast<int32_t>(c->sz.nleaf), ptr<int32_t>(c->leaves), ptr<int32_t>(c->begin),
       ptr<int32_t>(c->count), ptr<double>(c->X), ptr<double>(c->Y), ptr<double>(c->Zb),
@@ -565,6 +663,7 @@ int upward(fmm_ctx *c) {
         ptr<int32_t>(c->nchild), ptr<double>(c->S), ptr<double>(c->M), ptr<double>(c->Z),
         ptr<double>(c->invM), ptr<double>(c->mom));
     AMFMM_TRY(launched(c, "internal_upward"));
+  }
   }
   AMFMM_CUDA(c, cudaMemsetAsync(c->rmax2.p, 0, sizeof(unsigned long long) * nc, st));
   dim3 g(grid_for(n, kBlock), static_cast<unsigned>(c->sz.depth + 1));

@@ -121,6 +121,11 @@ __global__ void k_emit(int64_t nf, const int2 *__restrict__ front, const int32_t
   }
 }
 
+__global__ void k_roots_front(int32_t nsys, int2 *__restrict__ front) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < nsys) front[s] = make_int2(s, s);
+}
+
 }  // namespace
 
 int walk(fmm_ctx *c) {
@@ -145,13 +150,12 @@ int walk(fmm_ctx *c) {
   }
 
   int4 *total = ptr<int4>(c->totals);
-  {
-    int2 root = make_int2(0, 0);
-    int2 *h = static_cast<int2 *>(c->hpin);
-    *h = root;
-    AMFMM_CUDA(c, cudaMemcpyAsync(c->front[0].p, h, sizeof(int2), cudaMemcpyHostToDevice, st));
-  }
-  int64_t nf = 1, n_m2l = 0, n_p2p = 0, n_self = 0;
+  // one self pair per root: systems of a forest never interact
+  const int64_t nsys = c->sz.nsys;
+  if (nsys > static_cast<int64_t>(c->front[0].cap / sizeof(int2))) AMFMM_TRY(ensure<int2>(c, c->front[0], nsys));
+  k_roots_front<<<grid_for(nsys, kBlock), kBlock, 0, st>>>(static_cast<int32_t>(nsys), ptr<int2>(c->front[0]));
+  AMFMM_TRY(launched(c, "walk_roots"));
+  int64_t nf = nsys, n_m2l = 0, n_p2p = 0, n_self = 0;
   int cur = 0;
   while (nf > 0) {
     AMFMM_TRY(ensure<int32_t>(c, c->action, nf));

@@ -76,6 +76,9 @@ def load() -> ctypes.CDLL:
                 "fmm_export_locals": [P, P],
                 "fmm_direct": [P, P, P, P, P, I64, P, I64, P, P, P],
                 "fmm_balance": [P, P, P, P, P, P, P, P, I64, P],
+                "fmm_leapfrog": [P, P, P, P, P, P, P, P, I64, D, I, P, P, P, P],
+                "fmm_solve_batch": [P, P, P, P, P, P, I, P, P, P],
+                "fmm_autotune_ncrit": [P, P, P, P, P, P, I, P, I, I, P, P, P, P, P],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -230,6 +233,63 @@ class FMM:
                     "fmm_solve_host")
         return out
 
+    # ---- ensembles (a13) -------------------------------------------------------
+    @staticmethod
+    def _offsets(offsets):
+        import numpy as np
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        return off, ctypes.c_void_p(off.ctypes.data)
+
+    def solve_batch(self, x, y, z, m, offsets, out=None):
+        """Independent systems in one launch sequence: system s owns bodies
+        [offsets[s], offsets[s+1]) of the concatenated arrays."""
+        t = self._torch
+        x, y, z, m = (self._as_dev(a) for a in (x, y, z, m))
+        off, offp = self._offsets(offsets)
+        n = x.shape[0]
+        if int(off[-1]) != n:
+            raise ValueError("offsets[-1] must equal the number of bodies")
+        if out is None:
+            out = tuple(t.empty(n, dtype=t.float64, device=x.device) for _ in range(3))
+        self._bodies = (x, y, z, m)
+        self._check(self.lib.fmm_solve_batch(self._h, _dptr(x), _dptr(y), _dptr(z), _dptr(m), offp,
+                                             len(off) - 1, *(_dptr(o) for o in out)), "fmm_solve_batch")
+        return out
+
+    def autotune_ncrit(self, x, y, z, m, offsets, candidates=(16, 25, 32, 64), reps: int = 3):
+        """Times the batched solve for each leaf size; returns (best, {n_crit: ms})."""
+        import numpy as np
+        t = self._torch
+        x, y, z, m = (self._as_dev(a) for a in (x, y, z, m))
+        off, offp = self._offsets(offsets)
+        cand = np.ascontiguousarray(candidates, dtype=np.int32)
+        ms = np.zeros(len(cand), dtype=np.float32)
+        best = ctypes.c_int(0)
+        out = tuple(t.empty(x.shape[0], dtype=t.float64, device=x.device) for _ in range(3))
+        self._bodies = (x, y, z, m)
+        self._check(self.lib.fmm_autotune_ncrit(self._h, _dptr(x), _dptr(y), _dptr(z), _dptr(m), offp, len(off) - 1,
+                                                ctypes.c_void_p(cand.ctypes.data), len(cand), int(reps),
+                                                *(_dptr(o) for o in out), ctypes.byref(best),
+                                                ctypes.c_void_p(ms.ctypes.data)), "fmm_autotune_ncrit")
+        return int(best.value), {int(k): float(v) for k, v in zip(cand, ms)}
+
+    # ---- time integration (a14) ---------------------------------------------
+    def leapfrog(self, x, y, z, vx, vy, vz, m, dt: float, nsteps: int, acc=None, record=True):
+        """Uniform kick-drift-kick steps, state updated in place.  Returns
+        (ax, ay, az) and, if record, a [nsteps+1, 6] tensor of the totals
+        (P_x, P_y, P_z, L_x, L_y, L_z) after every step."""
+        t = self._torch
+        arrs = [self._as_dev(a) for a in (x, y, z, vx, vy, vz, m)]
+        n = arrs[0].shape[0]
+        if acc is None:
+            acc = tuple(t.empty(n, dtype=t.float64, device=arrs[0].device) for _ in range(3))
+        mom = t.zeros((nsteps + 1, 6), dtype=t.float64, device=arrs[0].device) if record else None
+        self._bodies = (arrs[0], arrs[1], arrs[2], arrs[6])
+        self._check(self.lib.fmm_leapfrog(self._h, *(_dptr(a) for a in arrs), n, float(dt), int(nsteps),
+                                          *(_dptr(a) for a in acc), _dptr(mom) if record else None),
+                    "fmm_leapfrog")
+        return acc, mom
+
     # ---- diagnostics (Sec. 3) ---------------------------------------------------
     def direct(self, x, y, z, m, targets):
         """Exact FP64 accelerations of the target bodies by direct summation."""
@@ -287,10 +347,14 @@ class FMM:
         out.update(M=M, Z=Z, Rmax=R)
         return out
 
+    def _mom_stride(self):
+        P = self.opts.order_P
+        return (P + 1) * (P + 2) * (P + 3) // 6
+
     def export_moments(self):
         t = self._torch
         nc = self.stats().ncell
-        mom = t.empty((nc, 20), dtype=t.float64, device=self._bodies[0].device)
+        mom = t.empty((nc, self._mom_stride()), dtype=t.float64, device=self._bodies[0].device)
         self._check(self.lib.fmm_export_moments(self._h, _dptr(mom)), "fmm_export_moments")
         return mom
 
@@ -307,6 +371,7 @@ class FMM:
     def export_locals(self):
         t = self._torch
         nc = self.stats().ncell
-        C = t.empty((nc, 20), dtype=t.float64, device=self._bodies[0].device)
+        width = 20 if self.opts.order_P == 3 else self._mom_stride() - 1
+        C = t.empty((nc, width), dtype=t.float64, device=self._bodies[0].device)
         self._check(self.lib.fmm_export_locals(self._h, _dptr(C)), "fmm_export_locals")
         return C
