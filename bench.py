@@ -57,9 +57,12 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-other", action="store_true", help="skip timing the other precision form")
-    p.add_argument("--experiment", choices=["none", "leapfrog", "ensemble"], default="none",
+    p.add_argument("--experiment", choices=["none", "leapfrog", "ensemble", "selector"], default="none",
                    help="leapfrog: two-Plummer binary, uniform KDK steps, momentum drift per step")
     p.add_argument("--lf-steps", type=int, default=200)
+    p.add_argument("--sel-steps", type=int, default=3000)
+    p.add_argument("--sel-floor", type=float, default=0.35,
+                   help="theta of the plain criterion kept under the learned selector")
     p.add_argument("--lf-variants", default="TC:mixed,UC:mixed,TC:fp64")
     return p.parse_args()
 
@@ -456,8 +459,112 @@ def run_ensemble(a):
                       "speedup": loop_ms / batched_ms}), flush=True)
 
 
+def _rms_err(solver, x, y, z, m, out, tg_dev, ref):
+    got = torch_stack(out)[tg_dev]
+    import torch
+    rel = torch.linalg.norm(got - ref, dim=1) / torch.linalg.norm(ref, dim=1)
+    return float(torch.sqrt(torch.mean(rel * rel)).cpu())
+
+
+def torch_stack(out):
+    import torch
+    return torch.stack(out, 1)
+
+
+def _time_solves(solver, x, y, z, m, out, flush, reps=3):
+    import torch
+    stream = torch.cuda.current_stream()
+    ts = []
+    for k in range(reps):
+        flush.fill_(k & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.solve(x, y, z, m, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def run_selector(a):
+    """Learned pair selector: trained on pairs of the Plummer N = 2,000 and
+    N = 1,048,576 spheres accepted at theta = 0.3 .. 1.0 (labels: the method's
+    own M2L errors), applied to a Plummer sphere and to a Hernquist halo +
+    exponential disc, both N = 4,194,304, against the fixed theta = 0.5
+    criterion (FP64 and the mixed form) at matched rms force error (4,096
+    bodies against exact direct sums)."""
+    import torch
+    from paper_1706_06989_gb300 import fmm, ics, selector
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    s = fmm.FMM(theta=0.5, n_crit=25, variant="TC", precision="fp64")
+    feats, labs = [], []
+    for b, per in ((ics.plummer(2000, seed=0), 200_000), (ics.plummer(1 << 20, seed=0), 2_500_000)):
+        x, y, z, m = (torch.from_numpy(v).to(dev) for v in (b.x, b.y, b.z, b.m))
+        f, l = selector.pair_samples(s, x, y, z, m, thetas=(0.3, 0.5, 0.7, 1.0), per_theta=per, seed=3)
+        feats.append(f)
+        labs.append(l)
+    X, Y = torch.cat(feats), torch.cat(labs)
+    t_data = time.perf_counter() - t0
+    params, losses = selector.train(s, X, Y, steps=a.sel_steps, batch=8192, lr=2e-3, seed=4)
+    t_train = time.perf_counter() - t0 - t_data
+    s.close()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    evals = []
+    for wname, b in (("plummer, N=4194304 (seed 0)", ics.plummer(4194304, seed=0)),
+                     ("hernquist(a=1, 70%) + exponential disc (30%), N=4194304", ics.hernquist_disc(4194304, seed=0))):
+        x, y, z, m = (torch.from_numpy(v).to(dev) for v in (b.x, b.y, b.z, b.m))
+        tgd = torch.as_tensor(ics.error_subset(b.n, 4096, seed=1), device=dev)
+        ev = fmm.FMM(theta=0.5, n_crit=25, variant="TC", precision=a.precision)
+        out = tuple(torch.empty(b.n, dtype=torch.float64, device=dev) for _ in range(3))
+        ref = torch.stack(ev.direct(x, y, z, m, tgd), 1)
+        res = {}
+        for prec in ("fp64", a.precision):
+            ev.set_opts(theta=0.5, precision=prec)
+            ev.selector_set(None, 0.0, enable=False)
+            ev.solve(x, y, z, m, out)
+            st = ev.stats()
+            res[f"theta0.5_{prec}"] = {"ms": _time_solves(ev, x, y, z, m, out, flush),
+                                       "rms_err": _rms_err(ev, x, y, z, m, out, tgd, ref),
+                                       "n_m2l": st.n_m2l, "p2p_body_pairs": st.p2p_body_pairs}
+        base = res[f"theta0.5_{a.precision}"]["rms_err"]
+        # theta is the floor of the accepted set; the network adds pairs
+        ev.set_opts(theta=a.sel_floor, precision=a.precision)
+        scan, best = [], None
+        for tgt in np.arange(-4.0, -1.49, 0.25):
+            ev.selector_set(params, float(tgt), enable=True)
+            ev.solve(x, y, z, m, out)
+            st = ev.stats()
+            e = _rms_err(ev, x, y, z, m, out, tgd, ref)
+            row = {"log10_target": float(tgt), "rms_err": e, "n_m2l": st.n_m2l,
+                   "p2p_body_pairs": st.p2p_body_pairs}
+            if e <= base:
+                row["ms"] = _time_solves(ev, x, y, z, m, out, flush)
+                if best is None or row["ms"] < best["ms"]:
+                    best = row
+            scan.append(row)
+        ev.selector_set(None, 0.0, enable=False)
+        fp64_ms = res["theta0.5_fp64"]["ms"]
+        evals.append({"workload": wname, "fixed_theta": res, "selector_theta_floor": a.sel_floor,
+                      "selector_scan": scan, "selector_best_at_matched_error": best,
+                      "speedup_vs_fixed_theta_same_precision":
+                          (res[f"theta0.5_{a.precision}"]["ms"] / best["ms"]) if best else None,
+                      "speedup_vs_plain_fp64": (fp64_ms / best["ms"]) if best else None})
+        ev.close()
+        del x, y, z, m, out, ref
+        torch.cuda.empty_cache()
+    print(json.dumps({"experiment": "selector", "train": {"samples": int(X.shape[0]), "steps": a.sel_steps,
+                                                          "loss_first": float(losses[:20].mean()),
+                                                          "loss_last": float(losses[-50:].mean()),
+                                                          "s_data": t_data, "s_train": t_train},
+                      "evaluations": evals}), flush=True)
+
+
 def main():
     a = _args()
+    if a.experiment == "selector":
+        run_selector(a)
+        return
     if a.experiment == "leapfrog":
         run_leapfrog(a)
         return

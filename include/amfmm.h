@@ -176,6 +176,55 @@ int fmm_leapfrog(fmm_ctx *ctx, double *x, double *y, double *z, double *vx, doub
                  const double *m, int64_t n, double dt, int nsteps, double *ax, double *ay, double *az,
                  double *mom);
 
+/* ---- a12: learned pair selector ------------------------------------------ */
+/* The paper allows any pair selection driven by an error estimate (Sec. 2,
+ * after the opening criterion); every accepted pair still interacts mutually
+ * with the correction, so conservation is unchanged.  The estimate is a
+ * network of 8 pair features -> 3 x 64 SiLU -> 1 output, the predicted log10
+ * of the pair's normalised M2L error; it runs in BF16 on the tensor cores
+ * with FP32 accumulation.  Parameters: fmm_selector_nparams() floats (FP32):
+ * W1[64][8], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], w4[64], b4,
+ * feature mean[8], feature scale[8].  Features of a pair (ordered by R_max,
+ * then id): log10 of |r|, R_A/|r|, R_B/|r|, M_A, M_B, |Q_A - tr/3|/(M_A R_A^2),
+ * the same for B, and N_A + N_B; normalised as (f - mean) * scale. */
+int fmm_selector_nparams(void);
+
+/* Enables (enable = 1) or disables the selector for the following solves.
+ * params: HOST, fmm_selector_nparams() floats.  With it, a pair is accepted
+ * when the opening criterion at the context's theta accepts it, or when it
+ * passes |Z_A - Z_B| >= R_A + R_B (the criterion at theta = 1) and the
+ * prediction is below log10_target; others are opened as usual.  theta thus
+ * becomes a floor: the network only adds pairs, so the work of a solve never
+ * exceeds that of the plain criterion at the same theta. */
+int fmm_selector_set(fmm_ctx *ctx, const float *params, double log10_target, int enable);
+
+/* Training samples for K given cell pairs of the current tree (after
+ * fmm_upward, order 3): pairs: device, K x 2 int32; feat: device, K x 8 raw
+ * features; label (device, K floats, may be NULL): log10 of the larger of
+ * the two sides' errors, where a side's error is the rms over its bodies of
+ * |a_M2L - a_direct| for the pair alone (torque-corrected order-3
+ * expansion) divided by the other cell's monopole field M_other/|r|^2;
+ * floored at -12 (the FP64 rounding level).  Asynchronous. */
+int fmm_selector_samples(fmm_ctx *ctx, const int32_t *pairs, int64_t K, float *feat, float *label);
+
+/* Network output for K samples of raw features (device in, device out). */
+int fmm_mlp_forward(fmm_ctx *ctx, const float *params, const float *feat, int64_t K, float *out);
+/* Gradient (device, first 8961 entries of the parameter layout) and mean
+ * squared error (device, 1 float, may be NULL) of a batch of B samples; sums
+ * in a fixed order (reproducible). */
+int fmm_mlp_grad(fmm_ctx *ctx, const float *params, const float *feat, const float *label, int64_t B,
+                 float *grad, float *loss);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) of the network weights; m, v:
+ * device moment buffers of the same layout; step counts from 1. */
+int fmm_mlp_adam(fmm_ctx *ctx, float *params, float *m, float *v, const float *grad, float lr, int step);
+/* `steps` Adam steps on minibatches of `batch` samples in the order of one
+ * seeded permutation of the n samples (X: device n x 8 raw features, y:
+ * device n labels; params: device, updated; adam: device, 2 x 8961 floats,
+ * zeroed by the caller).  loss_out: HOST, steps floats or NULL.
+ * Synchronises the stream. */
+int fmm_selector_train(fmm_ctx *ctx, float *params, float *adam, const float *X, const float *y, int64_t n,
+                       int batch, int steps, float lr, unsigned long long seed, float *loss_out);
+
 /* ---- a10 diagnostics (Sec. 3) ---------------------------------------------- */
 
 /* Exact accelerations of nt target bodies by direct summation over all n

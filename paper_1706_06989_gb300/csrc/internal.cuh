@@ -65,6 +65,7 @@ struct fmm_ctx {
   const double *x = nullptr, *y = nullptr, *z = nullptr, *m = nullptr;
   double theta = 0.5;
   amfmm::Sizes sz;
+  int m2l_which = 0;  // which of the ekey/eval buffers holds the sorted M2L entries
 
   // pinned host scratch for small read-backs
   void *hpin = nullptr;
@@ -77,7 +78,7 @@ struct fmm_ctx {
   amfmm::DBuf begin, count, level, parent, first_child, nchild, S, M, Z, invM, Rmax,
       rmax2, mom, loc, leaves;
   // walk
-  amfmm::DBuf front[2], action, wcount, woff, m2l, p2p, self_list;
+  amfmm::DBuf front[2], action, wcount, woff, m2l, p2p, self_list, walk_zr, walk_nl;
   // M2L scatter
   amfmm::DBuf ekey[2], eval[2], m2l_pos, m2l_off, m2l_slots, cell32;
   // P2P grouping
@@ -87,6 +88,10 @@ struct fmm_ctx {
   // [0,16) scan totals, [64,72) near-field body-pair count, [96,104) slot total,
   // [128,132) near-field column total
   amfmm::DBuf scan_tmp, sort_hist, totals, diag;
+  // learned pair selector
+  amfmm::DBuf sel_params, sel_scratch, sel_part, sel_score, sel_grad, sel_perm, sel_xb, sel_yb;
+  bool sel_enabled = false;
+  double sel_log10_target = -3.0;
   // host-solve staging
   amfmm::DBuf hx, hy, hz, hm, hax, hay, haz;
 };
@@ -153,6 +158,8 @@ int walk(fmm_ctx *c);               // walk.cu
 int m2l_prepare(fmm_ctx *c);        // m2l.cu: slot positions (sort by cell)
 int m2l_run(fmm_ctx *c);            // m2l.cu: mutual M2L into slots
 int m2l_reduce(fmm_ctx *c);         // m2l.cu: per-cell fixed-order sums
+// the mixed form at order 3 gathers each cell's partners (one-sided, no slots)
+inline bool m2l_gathered(const fmm_ctx *c) { return c->opts.precision == FMM_MIXED && c->opts.order_P == 3; }
 int p2p_prepare(fmm_ctx *c);        // p2p.cu: grouping by leaf, partial slots
 int p2p_run(fmm_ctx *c);            // p2p.cu: mutual near field
 int p2p_reduce(fmm_ctx *c);         // p2p.cu: per-body fixed-order sums
@@ -166,6 +173,10 @@ int upward_general(fmm_ctx *c);
 int m2l_general(fmm_ctx *c);
 int reduce_general(fmm_ctx *c);
 int downward_general(fmm_ctx *c);
+
+// learned selector (selector.cu, m2l.cu)
+int walk_scores(fmm_ctx *c, int64_t nf, const int2 *front, float *score);
+int pair_locals_tc(fmm_ctx *c, const int2 *pairs, int64_t K, double *out);
 
 void timer(fmm_ctx *c, int slot);
 

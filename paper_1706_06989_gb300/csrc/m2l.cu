@@ -209,6 +209,132 @@ __global__ void __launch_bounds__(kBlock) k_m2l32(int64_t K, const int2 *__restr
   }
 }
 
+// One side of the same interaction: the local of a target cell T from a
+// source cell S, with r = Z_T - Z_S.  Written for T = A it is the C^A of
+// m2l_pair; for T = B it is C^B, because every term of C^B is the C^A form
+// with r -> -r and A <-> B: the odd terms (n D, U3, Q D_ijk) change sign with
+// r, the even ones (U2, and F, whose S = M_T O_S - M_S O_T changes sign
+// with the roles) pick up the sign of the role swap.  So a gather over each
+// cell's partners evaluates the mutual interaction once from each side.
+template <class T, int VARIANT>
+__device__ __forceinline__ void m2l_one(const T r[3], T MT, T iMT, T MS, const T *QS, const T *OT, const T *OS,
+                                        T *C) {
+  const T R2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  if (!(R2 > min_r2<T>())) {
+#pragma unroll
+    for (int q = 0; q < 19; ++q) C[q] = T(0);
+    return;
+  }
+  const T Ri = rsqrt_t(R2);
+  const T x = r[0] * Ri, y = r[1] * Ri, z = r[2] * Ri;
+  const T xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+  const T fxx = T(15) * xx, fyy = T(15) * yy, fzz = T(15) * zz;
+  const T M2 = MS * Ri * Ri, M3 = M2 * Ri, M4 = M3 * Ri;
+  const T Ri2 = Ri * Ri;
+  const T qx = QS[0] * x + QS[1] * y + QS[2] * z;
+  const T qy = QS[1] * x + QS[3] * y + QS[4] * z;
+  const T qz = QS[2] * x + QS[4] * y + QS[5] * z;
+  const T w = (T(7.5) * (x * qx + y * qy + z * qz) - T(1.5) * (QS[0] + QS[3] + QS[5])) * Ri2 * Ri2;
+  const T v = T(-3) * Ri2 * Ri2;
+  C[0] = M2 * x + (w * x + v * qx);
+  C[1] = M2 * y + (w * y + v * qy);
+  C[2] = M2 * z + (w * z + v * qz);
+  C[3] = M3 * (T(1) - T(3) * xx);
+  C[4] = M3 * (T(-3) * xy);
+  C[5] = M3 * (T(-3) * xz);
+  C[6] = M3 * (T(1) - T(3) * yy);
+  C[7] = M3 * (T(-3) * yz);
+  C[8] = M3 * (T(1) - T(3) * zz);
+  C[9] = M4 * ((fxx - T(9)) * x);
+  C[10] = M4 * ((fxx - T(3)) * y);
+  C[11] = M4 * ((fxx - T(3)) * z);
+  C[12] = M4 * ((fyy - T(3)) * x);
+  C[13] = M4 * (T(15) * xy * z);
+  C[14] = M4 * ((fzz - T(3)) * x);
+  C[15] = M4 * ((fyy - T(9)) * y);
+  C[16] = M4 * ((fyy - T(3)) * z);
+  C[17] = M4 * ((fzz - T(3)) * y);
+  C[18] = M4 * ((fzz - T(9)) * z);
+  if (VARIANT != FMM_UC) {
+    T S[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) S[k] = MT * OS[k] - MS * OT[k];
+    const T ux = S[0] * xx + S[3] * yy + S[5] * zz + T(2) * (S[1] * xy + S[2] * xz + S[4] * yz);
+    const T uy = S[1] * xx + S[6] * yy + S[8] * zz + T(2) * (S[3] * xy + S[4] * xz + S[7] * yz);
+    const T uz = S[2] * xx + S[7] * yy + S[9] * zz + T(2) * (S[4] * xy + S[5] * xz + S[8] * yz);
+    const T tx = S[0] + S[3] + S[5];
+    const T ty = S[1] + S[6] + S[8];
+    const T tz = S[2] + S[7] + S[9];
+    T F[3] = {T(7.5) * ux - T(1.5) * tx, T(7.5) * uy - T(1.5) * ty, T(7.5) * uz - T(1.5) * tz};
+    if (VARIANT == FMM_TC) {
+      const T g = T(-17.5) * (x * ux + y * uy + z * uz) + T(7.5) * (x * tx + y * ty + z * tz);
+      F[0] += g * x;
+      F[1] += g * y;
+      F[2] += g * z;
+    }
+    const T s5 = Ri2 * Ri2 * Ri * iMT;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) C[i] -= F[i] * s5;
+  }
+}
+
+// Mixed form, gathered: one warp per cell T, its lanes over T's partners in
+// the stably sorted order of the list.  Every lane keeps compensated FP32
+// sums (Kahan) of the partners it visits; the 32 lane sums are then added in
+// FP64 over a fixed butterfly.  Each cell's local is written whole (zero for
+// a cell without partners).
+template <int VARIANT>
+__global__ void __launch_bounds__(256) k_m2l32_gather(int32_t ncell, const int32_t *__restrict__ off,
+                                                       const uint32_t *__restrict__ partner,
+                                                       const float *__restrict__ cell32,
+                                                       double *__restrict__ loc) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= ncell) return;
+  const float *t = cell32 + static_cast<int64_t>(c) * kCell32;
+  const float thx = t[0], thy = t[1], thz = t[2], tlx = t[3], tly = t[4], tlz = t[5];
+  const float MT = t[6], iMT = t[7];
+  float OT[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) OT[k] = VARIANT != FMM_UC ? t[14 + k] : 0.f;
+  float sum[19], cmp[19];
+#pragma unroll
+  for (int q = 0; q < 19; ++q) sum[q] = cmp[q] = 0.f;
+  const int e1 = off[c + 1];
+  for (int e = off[c] + lane; e < e1; e += 32) {
+    const float4 *ps = reinterpret_cast<const float4 *>(cell32 + static_cast<int64_t>(partner[e]) * kCell32);
+    float b[kCell32];
+#pragma unroll
+    for (int u = 0; u < kCell32 / 4; ++u) {
+      const float4 vb = ps[u];
+      b[4 * u] = vb.x; b[4 * u + 1] = vb.y; b[4 * u + 2] = vb.z; b[4 * u + 3] = vb.w;
+    }
+    const float r[3] = {(thx - b[0]) + (tlx - b[3]), (thy - b[1]) + (tly - b[4]), (thz - b[2]) + (tlz - b[5])};
+    float C[19];
+    m2l_one<float, VARIANT>(r, MT, iMT, b[6], b + 8, OT, b + 14, C);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+      const float yq = C[q] - cmp[q];
+      const float tq = sum[q] + yq;
+      cmp[q] = (tq - sum[q]) - yq;
+      sum[q] = tq;
+    }
+  }
+  double acc[19];
+#pragma unroll
+  for (int q = 0; q < 19; ++q) acc[q] = static_cast<double>(sum[q]) - static_cast<double>(cmp[q]);
+#pragma unroll
+  for (int h = 1; h < 32; h <<= 1)
+#pragma unroll
+    for (int q = 0; q < 19; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], h);
+  // every lane holds the same sums; lane q stores coefficient q
+  double mine = 0.0;
+#pragma unroll
+  for (int q = 0; q < 19; ++q)
+    if (lane == q) mine = acc[q];
+  if (lane < kLocStride) loc[static_cast<int64_t>(c) * kLocStride + lane] = mine;
+}
+
 // FP32 copy of the cell data for the mixed form
 __global__ void k_cell32(int32_t ncell, const double *__restrict__ Z, const double *__restrict__ M,
                          const double *__restrict__ invM, const double *__restrict__ mom,
@@ -230,18 +356,52 @@ __global__ void k_cell32(int32_t ncell, const double *__restrict__ Z, const doub
   for (int q = 0; q < 16; ++q) o[8 + q] = static_cast<float>(m[4 + q]);
 }
 
-// entries: (cell, 2k + side) for the stable sort
-__global__ void k_m2l_entries(int64_t K, const int2 *__restrict__ pairs, uint32_t *__restrict__ key,
-                              uint32_t *__restrict__ val, int32_t *__restrict__ cnt) {
+// The two order-3 TC locals of given pairs, [k][side][20] (labels of the
+// learned selector)
+__global__ void k_pair_locals(int64_t K, const int2 *__restrict__ pairs, const double *__restrict__ Z,
+                              const double *__restrict__ M, const double *__restrict__ invM,
+                              const double *__restrict__ mom, double *__restrict__ out) {
+  const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (k >= K) return;
+  const int A = pairs[k].x, B = pairs[k].y;
+  double CA[kLocStride], CB[kLocStride];
+  const double r[3] = {Z[3 * A] - Z[3 * B], Z[3 * A + 1] - Z[3 * B + 1], Z[3 * A + 2] - Z[3 * B + 2]};
+  const double *mA = mom + static_cast<int64_t>(A) * kMomStride;
+  const double *mB = mom + static_cast<int64_t>(B) * kMomStride;
+  m2l_pair<double, FMM_TC>(r, M[A], M[B], invM[A], invM[B], mA + 4, mB + 4, mA + 10, mB + 10, CA, CB);
+  CA[19] = CB[19] = 0.0;
+#pragma unroll
+  for (int q = 0; q < kLocStride; ++q) {
+    out[(2 * k) * kLocStride + q] = CA[q];
+    out[(2 * k + 1) * kLocStride + q] = CB[q];
+  }
+}
+
+// entries for the stable sort by cell: (cell, 2k + side) for the slot form,
+// (cell, partner) for the gather form
+__global__ void k_m2l_entries(int64_t K, const int2 *__restrict__ pairs, int gather, uint32_t *__restrict__ key,
+                              uint32_t *__restrict__ val) {
   const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (k >= K) return;
   const int2 p = pairs[k];
   key[2 * k] = static_cast<uint32_t>(p.x);
-  val[2 * k] = static_cast<uint32_t>(2 * k);
+  val[2 * k] = gather ? static_cast<uint32_t>(p.y) : static_cast<uint32_t>(2 * k);
   key[2 * k + 1] = static_cast<uint32_t>(p.y);
-  val[2 * k + 1] = static_cast<uint32_t>(2 * k + 1);
-  atomicAdd(&cnt[p.x], 1);
-  atomicAdd(&cnt[p.y], 1);
+  val[2 * k + 1] = gather ? static_cast<uint32_t>(p.x) : static_cast<uint32_t>(2 * k + 1);
+}
+
+// off[c] = first sorted position of cell c (cells without entries get the
+// position of the next cell): every position s starts the cells
+// (key[s-1], key[s]], and the last entry closes the cells after it.
+__global__ void k_segment_offsets(int64_t E, int32_t ncell, const uint32_t *__restrict__ key,
+                                  int32_t *__restrict__ off) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (s >= E) return;
+  const int k = static_cast<int>(key[s]);
+  const int kp = s == 0 ? -1 : static_cast<int>(key[s - 1]);
+  for (int c = kp + 1; c <= k; ++c) off[c] = static_cast<int32_t>(s);
+  if (s == E - 1)
+    for (int c = k + 1; c <= ncell; ++c) off[c] = static_cast<int32_t>(E);
 }
 
 __global__ void k_inverse(int64_t E, const uint32_t *__restrict__ sval, int32_t *__restrict__ pos) {
@@ -313,6 +473,22 @@ int launch_m2l64(fmm_ctx *c, int64_t K) {
   return launched(c, "m2l");
 }
 
+int launch_m2l32_gather(fmm_ctx *c) {
+  const int32_t nc = static_cast<int32_t>(c->sz.ncell);
+  const unsigned g = grid_for(static_cast<int64_t>(nc) * 32, 256);
+  const int32_t *off = ptr<int32_t>(c->m2l_off);
+  const uint32_t *partner = ptr<uint32_t>(c->eval[c->m2l_which]);
+  const float *c32 = ptr<float>(c->cell32);
+  double *loc = ptr<double>(c->loc);
+  cudaStream_t st = c->stream;
+  switch (c->opts.variant) {
+    case FMM_UC: k_m2l32_gather<FMM_UC><<<g, 256, 0, st>>>(nc, off, partner, c32, loc); break;
+    case FMM_TC: k_m2l32_gather<FMM_TC><<<g, 256, 0, st>>>(nc, off, partner, c32, loc); break;
+    default: k_m2l32_gather<FMM_TCO><<<g, 256, 0, st>>>(nc, off, partner, c32, loc); break;
+  }
+  return launched(c, "m2l");
+}
+
 int launch_m2l32(fmm_ctx *c, int64_t K) {
   const int2 *pairs = ptr<int2>(c->m2l);
   const unsigned g = grid_for(K, kBlock);
@@ -347,21 +523,23 @@ int m2l_prepare(fmm_ctx *c) {
   if (K == 0) return FMM_OK;
   AMFMM_TRY(ensure<uint32_t>(c, c->ekey[0], E));
   AMFMM_TRY(ensure<uint32_t>(c, c->eval[0], E));
-  AMFMM_TRY(ensure<int32_t>(c, c->m2l_pos, E));
-  AMFMM_TRY(ensure<int32_t>(c, c->incl, std::max<int64_t>(nc + 1, c->sz.n + 1)));
-  int32_t *cnt = ptr<int32_t>(c->incl);
-  AMFMM_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nc + 1), st));
-  k_m2l_entries<<<grid_for(K, 256), 256, 0, st>>>(K, ptr<int2>(c->m2l), ptr<uint32_t>(c->ekey[0]),
-                                                  ptr<uint32_t>(c->eval[0]), cnt);
+  if (!m2l_gathered(c)) AMFMM_TRY(ensure<int32_t>(c, c->m2l_pos, E));
+  const bool fp32 = c->opts.precision == FMM_MIXED;
+  const int gather = m2l_gathered(c);
+  k_m2l_entries<<<grid_for(K, 256), 256, 0, st>>>(K, ptr<int2>(c->m2l), gather, ptr<uint32_t>(c->ekey[0]),
+                                                  ptr<uint32_t>(c->eval[0]));
   AMFMM_TRY(launched(c, "m2l_entries"));
-  AMFMM_TRY(exclusive_scan_i32(c, cnt, off, nc + 1, nullptr));
   int which = 0;
   AMFMM_TRY(radix_sort_u32(c, c->ekey, c->eval, E, bits_for(nc), &which));
-  k_inverse<<<grid_for(E, 256), 256, 0, st>>>(E, ptr<uint32_t>(c->eval[which]), ptr<int32_t>(c->m2l_pos));
-  AMFMM_TRY(launched(c, "m2l_inverse"));
-  const bool fp32 = c->opts.precision == FMM_MIXED;
-  const size_t esz = fp32 ? sizeof(float) : sizeof(double);
-  AMFMM_TRY(ensure_bytes(c, c->m2l_slots, static_cast<size_t>(E) * loc_stride(c->opts.order_P) * esz));
+  c->m2l_which = which;
+  k_segment_offsets<<<grid_for(E, 256), 256, 0, st>>>(E, static_cast<int32_t>(nc), ptr<uint32_t>(c->ekey[which]), off);
+  AMFMM_TRY(launched(c, "segment_offsets"));
+  if (!gather) {
+    k_inverse<<<grid_for(E, 256), 256, 0, st>>>(E, ptr<uint32_t>(c->eval[which]), ptr<int32_t>(c->m2l_pos));
+    AMFMM_TRY(launched(c, "m2l_inverse"));
+    const size_t esz = fp32 ? sizeof(float) : sizeof(double);
+    AMFMM_TRY(ensure_bytes(c, c->m2l_slots, static_cast<size_t>(E) * loc_stride(c->opts.order_P) * esz));
+  }
   if (fp32) {
     AMFMM_TRY(ensure<float>(c, c->cell32, static_cast<size_t>(kCell32) * nc));
     k_cell32<<<grid_for(nc, 256), 256, 0, st>>>(static_cast<int32_t>(nc), ptr<double>(c->Z), ptr<double>(c->M),
@@ -371,10 +549,17 @@ int m2l_prepare(fmm_ctx *c) {
   return FMM_OK;
 }
 
+int pair_locals_tc(fmm_ctx *c, const int2 *pairs, int64_t K, double *out) {
+  k_pair_locals<<<grid_for(K, 128), 128, 0, c->stream>>>(K, pairs, ptr<double>(c->Z), ptr<double>(c->M),
+                                                        ptr<double>(c->invM), ptr<double>(c->mom), out);
+  return launched(c, "pair_locals");
+}
+
 int m2l_run(fmm_ctx *c) {
   const int64_t K = c->sz.n_m2l;
   if (K == 0) return FMM_OK;
   if (c->opts.order_P != 3) return m2l_general(c);
+  if (m2l_gathered(c)) return launch_m2l32_gather(c);
   if (c->opts.precision == FMM_MIXED) return launch_m2l32(c, K);
   return launch_m2l64(c, K);
 }
@@ -387,6 +572,7 @@ int m2l_reduce(fmm_ctx *c) {
     AMFMM_CUDA(c, cudaMemsetAsync(c->loc.p, 0, sizeof(double) * kLocStride * nc, st));
     return FMM_OK;
   }
+  if (m2l_gathered(c)) return FMM_OK;  // the gather kernel wrote every local
   int32_t *off = ptr<int32_t>(c->m2l_off);
   const unsigned g = grid_for(nc * 32, 256);
   if (c->opts.precision == FMM_MIXED)

@@ -109,7 +109,35 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
       }
       const bool mutual = col.y >= 0;
       T bx = T(0), by = T(0), bz = T(0);
-      for (int i = 0; i < nr; ++i) {
+      // FP32: two rows per step, independent dependency chains for the
+      // pipelines (FP64 is issue-bound and runs faster one row at a time)
+      int i = 0;
+      if constexpr (sizeof(T) == sizeof(float)) for (; i + 1 < nr; i += 2) {
+        const T dx0 = sm.row[i][0] - xj, dy0 = sm.row[i][1] - yj, dz0 = sm.row[i][2] - zj;
+        const T dx1 = sm.row[i + 1][0] - xj, dy1 = sm.row[i + 1][1] - yj, dz1 = sm.row[i + 1][2] - zj;
+        const T r20 = dx0 * dx0 + dy0 * dy0 + dz0 * dz0;
+        const T r21 = dx1 * dx1 + dy1 * dy1 + dz1 * dz1;
+        const bool ok0 = valid && r20 > p2p_min_r2<T>(), ok1 = valid && r21 > p2p_min_r2<T>();
+        const T ri0 = ok0 ? rsqrt_t(r20) : T(0), ri1 = ok1 ? rsqrt_t(r21) : T(0);
+        const T r30 = ri0 * ri0 * ri0, r31 = ri1 * ri1 * ri1;
+        const T si0 = sm.row[i][3] * r30, si1 = sm.row[i + 1][3] * r31;
+        bx += si0 * dx0;
+        by += si0 * dy0;
+        bz += si0 * dz0;
+        bx += si1 * dx1;
+        by += si1 * dy1;
+        bz += si1 * dz1;
+        if (mutual) {
+          const T sj0 = mj * r30, sj1 = mj * r31;
+          sm.acc[3 * i][l] -= sj0 * dx0;
+          sm.acc[3 * i + 1][l] -= sj0 * dy0;
+          sm.acc[3 * i + 2][l] -= sj0 * dz0;
+          sm.acc[3 * i + 3][l] -= sj1 * dx1;
+          sm.acc[3 * i + 4][l] -= sj1 * dy1;
+          sm.acc[3 * i + 5][l] -= sj1 * dz1;
+        }
+      }
+      for (; i < nr; ++i) {
         const T dx = sm.row[i][0] - xj, dy = sm.row[i][1] - yj, dz = sm.row[i][2] - zj;
         const T r2 = dx * dx + dy * dy + dz * dz;
         if (valid && r2 > p2p_min_r2<T>()) {

@@ -1,0 +1,693 @@
+// selector.cu -- a12: a learned pair selector.
+//
+// The paper notes (Sec. 2) that the modification applies unchanged to pair
+// selections driven by an error estimate (Dehnen 2014): every accepted pair
+// still interacts mutually, so force and torque stay balanced.  Here the
+// estimate is a small network: 8 pair features -> 3 x 64 SiLU -> 1, the
+// predicted log10 of the pair's normalised M2L error.  In the walk a pair that
+// passes the safety bound |Z_A - Z_B| >= R_A,max + R_B,max (the criterion at
+// theta = 1) is accepted when the prediction is below a target; without the
+// network the opening criterion decides as before.
+//
+// Network arithmetic: BF16 inputs and weights on the tensor cores
+// (mma.sync m16n8k16, FP32 accumulation); biases, SiLU and the output layer in
+// FP32; each layer's FP32 accumulator fragment is re-packed in registers as
+// the next layer's BF16 operand fragment.  Training: mean squared error,
+// gradients of the inputs of each layer on the tensor cores, gradients of the
+// weights in FP32 per block of 64 samples, summed over blocks in a fixed order,
+// Adam update of the FP32 master weights.
+//
+// Parameter layout (FP32, kNParams): W1[64][8], b1[64], W2[64][64], b2[64],
+// W3[64][64], b3[64], w4[64], b4, then the feature normalisation mean[8],
+// scale[8] (x_norm = (x - mean) * scale).
+#include <cuda_bf16.h>
+
+#include <random>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace amfmm {
+
+constexpr int kH = 64;
+constexpr int kF = 8;
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kH * kF, kOffW2 = kOffB1 + kH, kOffB2 = kOffW2 + kH * kH,
+              kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 + kH * kH, kOffW4 = kOffB3 + kH, kOffB4 = kOffW4 + kH,
+              kNWeights = kOffB4 + 1, kOffMean = kNWeights, kOffScale = kOffMean + kF,
+              kNParams = kOffScale + kF;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// features and labels
+// ---------------------------------------------------------------------------
+// Order the pair by R_max (descending), then by id, so the features (and the
+// decision) are the same for (A, B) and (B, A).
+__device__ __forceinline__ void order_pair(int &A, int &B, const double *__restrict__ Rmax) {
+  const double ra = Rmax[A], rb = Rmax[B];
+  if (rb > ra || (rb == ra && B < A)) {
+    const int t = A;
+    A = B;
+    B = t;
+  }
+}
+
+// trace-free quadrupole norm |Q - tr(Q)/3 I| / (M R_max^2)
+__device__ __forceinline__ float qnorm(const double *q, double M, double R) {
+  const double tr = (q[0] + q[3] + q[5]) / 3.0;
+  const double a = q[0] - tr, d = q[3] - tr, f = q[5] - tr;
+  const double n2 = a * a + d * d + f * f + 2.0 * (q[1] * q[1] + q[2] * q[2] + q[4] * q[4]);
+  return static_cast<float>(sqrt(n2) / (M * R * R + 1e-300));
+}
+
+// raw features: log10 of |r|, R_A/|r|, R_B/|r|, M_A, M_B, q_A, q_B, N_A + N_B
+__device__ void pair_features(int A, int B, const double *__restrict__ Z, const double *__restrict__ Rmax,
+                              const double *__restrict__ M, const double *__restrict__ mom, int mstride,
+                              const int32_t *__restrict__ count, float f[kF]) {
+  order_pair(A, B, Rmax);
+  const double dx = Z[3 * A] - Z[3 * B], dy = Z[3 * A + 1] - Z[3 * B + 1], dz = Z[3 * A + 2] - Z[3 * B + 2];
+  const double r = sqrt(dx * dx + dy * dy + dz * dz) + 1e-300;
+  f[0] = static_cast<float>(log10(r));
+  f[1] = static_cast<float>(log10(fmax(Rmax[A] / r, 1e-12)));
+  f[2] = static_cast<float>(log10(fmax(Rmax[B] / r, 1e-12)));
+  f[3] = static_cast<float>(log10(M[A]));
+  f[4] = static_cast<float>(log10(M[B]));
+  f[5] = log10f(qnorm(mom + static_cast<int64_t>(A) * mstride + 4, M[A], Rmax[A]) + 1e-12f);
+  f[6] = log10f(qnorm(mom + static_cast<int64_t>(B) * mstride + 4, M[B], Rmax[B]) + 1e-12f);
+  f[7] = log10f(static_cast<float>(count[A] + count[B]));
+}
+
+__global__ void k_features(int64_t K, const int2 *__restrict__ pairs, const double *__restrict__ Z,
+                           const double *__restrict__ Rmax, const double *__restrict__ M,
+                           const double *__restrict__ mom, int mstride, const int32_t *__restrict__ count,
+                           float *__restrict__ feat) {
+  const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (k >= K) return;
+  float f[kF];
+  pair_features(pairs[k].x, pairs[k].y, Z, Rmax, M, mom, mstride, count, f);
+#pragma unroll
+  for (int q = 0; q < kF; ++q) feat[k * kF + q] = f[q];
+}
+
+// Label of one pair (block per pair): for each side, the rms over its bodies
+// of |a_M2L - a_direct| for the interaction of A with B alone (order 3, the
+// torque-corrected expansion of Eqs. 3, 4, 7), divided by the monopole field
+// of the other cell at that distance (M_B/|r|^2 on A, M_A/|r|^2 on B); the
+// label is log10 of the larger of the two, floored at -12.  Taking the worse
+// side keeps a small cell's large error from being averaged away by the
+// bodies of a big partner.
+__global__ void __launch_bounds__(128) k_labels(int64_t K, const int2 *__restrict__ pairs,
+                                                const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+                                                const double *__restrict__ X, const double *__restrict__ Y,
+                                                const double *__restrict__ Zb, const double *__restrict__ Mb,
+                                                const double *__restrict__ Z, const double *__restrict__ loc_pair,
+                                                float *__restrict__ label) {
+  const int64_t k = blockIdx.x;
+  if (k >= K) return;
+  int A = pairs[k].x, B = pairs[k].y;
+  const double *CA = loc_pair + (2 * k) * 20, *CB = loc_pair + (2 * k + 1) * 20;
+  const int bA = begin[A], nA = count[A], bB = begin[B], nB = count[B];
+  double errA = 0.0, errB = 0.0;
+  for (int t = threadIdx.x; t < nA + nB; t += blockDim.x) {
+    const bool onA = t < nA;
+    const int i = onA ? bA + t : bB + (t - nA);
+    const int c = onA ? A : B;
+    const double *C = onA ? CA : CB;
+    const int ob = onA ? bB : bA, on = onA ? nB : nA;
+    const double x[3] = {X[i] - Z[3 * c], Y[i] - Z[3 * c + 1], Zb[i] - Z[3 * c + 2]};
+    // order-3 local expansion: g_i = -(C_i + C_ij x_j + C_ijk x_j x_k / 2)
+    const double Q[3][3] = {{C[3], C[4], C[5]}, {C[4], C[6], C[7]}, {C[5], C[7], C[8]}};
+    const double O[3][3][3] = {{{C[9], C[10], C[11]}, {C[10], C[12], C[13]}, {C[11], C[13], C[14]}},
+                               {{C[10], C[12], C[13]}, {C[12], C[15], C[16]}, {C[13], C[16], C[17]}},
+                               {{C[11], C[13], C[14]}, {C[13], C[16], C[17]}, {C[14], C[17], C[18]}}};
+    double g[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double v = C[d], w = 0.0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        v += Q[d][j] * x[j];
+#pragma unroll
+        for (int l = 0; l < 3; ++l) w += O[d][j][l] * x[j] * x[l];
+      }
+      g[d] = -(v + 0.5 * w);
+    }
+    double a[3] = {0, 0, 0};
+    for (int j = ob; j < ob + on; ++j) {
+      const double d0 = X[j] - X[i], d1 = Y[j] - Y[i], d2 = Zb[j] - Zb[i];
+      const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+      if (r2 > 0.0) {
+        const double s = Mb[j] / (r2 * sqrt(r2));
+        a[0] += s * d0;
+        a[1] += s * d1;
+        a[2] += s * d2;
+      }
+    }
+    const double e0 = g[0] - a[0], e1 = g[1] - a[1], e2 = g[2] - a[2];
+    (onA ? errA : errB) += e0 * e0 + e1 * e1 + e2 * e2;
+  }
+  __shared__ double sh[2][128];
+  sh[0][threadIdx.x] = errA;
+  sh[1][threadIdx.x] = errB;
+  __syncthreads();
+  for (int o = 64; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double mA = 0, mB = 0;
+    for (int j = bA; j < bA + nA; ++j) mA += Mb[j];
+    for (int j = bB; j < bB + nB; ++j) mB += Mb[j];
+    const double dx = Z[3 * A] - Z[3 * B], dy = Z[3 * A + 1] - Z[3 * B + 1], dz = Z[3 * A + 2] - Z[3 * B + 2];
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    const double eA = sqrt(sh[0][0] / nA) / (mB / r2), eB = sqrt(sh[1][0] / nB) / (mA / r2);
+    // below 1e-12 of the monopole scale the error is FP64 rounding noise
+    label[k] = static_cast<float>(fmax(log10(fmax(eA, eB) + 1e-300), -12.0));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the network on the tensor cores
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float silu(float z) { return z / (1.f + expf(-z)); }
+__device__ __forceinline__ float silu_grad(float z) {
+  const float s = 1.f / (1.f + expf(-z));
+  return s * (1.f + z * (1.f - s));
+}
+
+// Shared-memory copy of the network: BF16 weights, FP32 biases / output layer.
+struct NetSmem {
+  __nv_bfloat16 W1[kH][16];  // input width padded to 16
+  __nv_bfloat16 W2[kH][kH];
+  __nv_bfloat16 W3[kH][kH];
+  float b1[kH], b2[kH], b3[kH], w4[kH], b4, mean[kF], scale[kF];
+};
+
+__device__ void load_net(NetSmem &s, const float *__restrict__ p) {
+  for (int q = threadIdx.x; q < kH * 16; q += blockDim.x) {
+    const int o = q / 16, i = q % 16;
+    s.W1[o][i] = __float2bfloat16_rn(i < kF ? p[kOffW1 + o * kF + i] : 0.f);
+  }
+  for (int q = threadIdx.x; q < kH * kH; q += blockDim.x) {
+    s.W2[q / kH][q % kH] = __float2bfloat16_rn(p[kOffW2 + q]);
+    s.W3[q / kH][q % kH] = __float2bfloat16_rn(p[kOffW3 + q]);
+  }
+  for (int q = threadIdx.x; q < kH; q += blockDim.x) {
+    s.b1[q] = p[kOffB1 + q];
+    s.b2[q] = p[kOffB2 + q];
+    s.b3[q] = p[kOffB3 + q];
+    s.w4[q] = p[kOffW4 + q];
+  }
+  if (threadIdx.x < kF) {
+    s.mean[threadIdx.x] = p[kOffMean + threadIdx.x];
+    s.scale[threadIdx.x] = p[kOffScale + threadIdx.x];
+  }
+  if (threadIdx.x == 0) s.b4 = p[kOffB4];
+}
+
+// Per-warp state of 16 samples.  Fragment conventions (m16n8k16): lane =
+// 4 g + t; an accumulator tile n holds rows g and g + 8, columns 8 n + 2 t and
+// 8 n + 2 t + 1.
+struct Act {
+  float z[3][8][4];  // pre-activations of the three hidden layers
+  float y[2];        // outputs of rows g and g + 8
+};
+
+// B fragment of W[o][i] used as B[k = i][n = o] (forward: out = in W^T)
+__device__ __forceinline__ void bfrag_fwd(const __nv_bfloat16 (*W)[kH], int kb, int n, int g, int t, uint32_t &b0,
+                                          uint32_t &b1) {
+  b0 = *reinterpret_cast<const uint32_t *>(&W[8 * n + g][16 * kb + 2 * t]);
+  b1 = *reinterpret_cast<const uint32_t *>(&W[8 * n + g][16 * kb + 2 * t + 8]);
+}
+
+// forward of 16 samples whose normalised features sit in xs[16][kF]
+__device__ void forward16(const NetSmem &s, const float (*xs)[kF], Act &act) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  uint32_t a[4];
+  a[0] = pack_bf16(xs[g][2 * t], xs[g][2 * t + 1]);
+  a[1] = pack_bf16(xs[g + 8][2 * t], xs[g + 8][2 * t + 1]);
+  a[2] = 0u;
+  a[3] = 0u;
+  float h[8][4];
+  // layer 1 (K = 8, padded to 16)
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    const uint32_t b0 = *reinterpret_cast<const uint32_t *>(&s.W1[8 * n + g][2 * t]);
+    mma16816(c, a, b0, 0u);
+    const float bb0 = s.b1[8 * n + 2 * t], bb1 = s.b1[8 * n + 2 * t + 1];
+    act.z[0][n][0] = c[0] + bb0;
+    act.z[0][n][1] = c[1] + bb1;
+    act.z[0][n][2] = c[2] + bb0;
+    act.z[0][n][3] = c[3] + bb1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) h[n][q] = silu(act.z[0][n][q]);
+  }
+  // layers 2 and 3
+#pragma unroll
+  for (int L = 1; L < 3; ++L) {
+    const __nv_bfloat16(*W)[kH] = L == 1 ? s.W2 : s.W3;
+    const float *bias = L == 1 ? s.b2 : s.b3;
+    uint32_t A[4][4];
+#pragma unroll
+    for (int kb = 0; kb < 4; ++kb) {
+      A[kb][0] = pack_bf16(h[2 * kb][0], h[2 * kb][1]);
+      A[kb][1] = pack_bf16(h[2 * kb][2], h[2 * kb][3]);
+      A[kb][2] = pack_bf16(h[2 * kb + 1][0], h[2 * kb + 1][1]);
+      A[kb][3] = pack_bf16(h[2 * kb + 1][2], h[2 * kb + 1][3]);
+    }
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kb = 0; kb < 4; ++kb) {
+        uint32_t b0, b1;
+        bfrag_fwd(W, kb, n, g, t, b0, b1);
+        mma16816(c, A[kb], b0, b1);
+      }
+      const float bb0 = bias[8 * n + 2 * t], bb1 = bias[8 * n + 2 * t + 1];
+      act.z[L][n][0] = c[0] + bb0;
+      act.z[L][n][1] = c[1] + bb1;
+      act.z[L][n][2] = c[2] + bb0;
+      act.z[L][n][3] = c[3] + bb1;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) h[n][q] = silu(act.z[L][n][q]);
+    }
+  }
+  // output layer in FP32: partial dots over this lane's columns, then the
+  // four lanes of the row group in a fixed order
+  float y0 = 0.f, y1 = 0.f;
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    const float w0 = s.w4[8 * n + 2 * t], w1 = s.w4[8 * n + 2 * t + 1];
+    y0 += h[n][0] * w0 + h[n][1] * w1;
+    y1 += h[n][2] * w0 + h[n][3] * w1;
+  }
+  y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
+  y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
+  y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
+  y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
+  act.y[0] = y0 + s.b4;
+  act.y[1] = y1 + s.b4;
+}
+
+// inference over K samples of raw features
+__global__ void __launch_bounds__(128) k_mlp_infer(int64_t K, const float *__restrict__ params,
+                                                   const float *__restrict__ feat, float *__restrict__ out) {
+  __shared__ NetSmem s;
+  __shared__ float xs[4][16][kF];
+  load_net(s, params);
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t base = (static_cast<int64_t>(blockIdx.x) * 4 + w) * 16;
+  if (lane < 16) {
+    const int64_t k = base + lane;
+#pragma unroll
+    for (int q = 0; q < kF; ++q)
+      xs[w][lane][q] = k < K ? (feat[k * kF + q] - s.mean[q]) * s.scale[q] : 0.f;
+  }
+  __syncwarp();
+  Act act;
+  forward16(s, xs[w], act);
+  const int g = lane >> 2;
+  if ((lane & 3) == 0) {
+    if (base + g < K) out[base + g] = act.y[0];
+    if (base + g + 8 < K) out[base + g + 8] = act.y[1];
+  }
+}
+
+// One minibatch: forward, backward, per-block gradient partials (64 samples a
+// block); loss = mean over the batch of (y - label)^2.
+struct TrainSmem {
+  NetSmem net;
+  float xs[4][16][kF];
+  float dz[64][kH];   // dL/dz of the current layer, 64 samples
+  float hin[64][kH];  // the BF16-rounded input of the current layer (as FP32)
+};
+
+__global__ void __launch_bounds__(128) k_mlp_grad(int64_t B, const float *__restrict__ params,
+                                                  const float *__restrict__ feat, const float *__restrict__ lab,
+                                                  float *__restrict__ part, float *__restrict__ loss_part) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  TrainSmem &s = *reinterpret_cast<TrainSmem *>(raw);
+  load_net(s.net, params);
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * 64 + w * 16;
+  if (lane < 16) {
+    const int64_t k = base + lane;
+#pragma unroll
+    for (int q = 0; q < kF; ++q)
+      s.xs[w][lane][q] = k < B ? (feat[k * kF + q] - s.net.mean[q]) * s.net.scale[q] : 0.f;
+  }
+  __syncwarp();
+  Act act;
+  forward16(s.net, s.xs[w], act);
+  // dL/dy = 2 (y - label) / B for real samples
+  const int64_t r0 = base + g, r1 = base + g + 8;
+  const float dy0 = r0 < B ? 2.f * (act.y[0] - lab[r0]) / static_cast<float>(B) : 0.f;
+  const float dy1 = r1 < B ? 2.f * (act.y[1] - lab[r1]) / static_cast<float>(B) : 0.f;
+  float lsum = 0.f;
+  if (t == 0) {
+    if (r0 < B) lsum += (act.y[0] - lab[r0]) * (act.y[0] - lab[r0]);
+    if (r1 < B) lsum += (act.y[1] - lab[r1]) * (act.y[1] - lab[r1]);
+  }
+  // output layer: dw4 = sum dy h3, db4 = sum dy; dz3 = dy w4 silu'(z3)
+  float dz[8][4];
+  float* pp = part + static_cast<int64_t>(blockIdx.x) * kNWeights;
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    const float w0 = s.net.w4[8 * n + 2 * t], w1 = s.net.w4[8 * n + 2 * t + 1];
+    dz[n][0] = dy0 * w0 * silu_grad(act.z[2][n][0]);
+    dz[n][1] = dy0 * w1 * silu_grad(act.z[2][n][1]);
+    dz[n][2] = dy1 * w0 * silu_grad(act.z[2][n][2]);
+    dz[n][3] = dy1 * w1 * silu_grad(act.z[2][n][3]);
+  }
+  // h3 values for dw4: stage in shared memory, reduce over 64 samples below
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    s.hin[w * 16 + g][8 * n + 2 * t] = silu(act.z[2][n][0]);
+    s.hin[w * 16 + g][8 * n + 2 * t + 1] = silu(act.z[2][n][1]);
+    s.hin[w * 16 + g + 8][8 * n + 2 * t] = silu(act.z[2][n][2]);
+    s.hin[w * 16 + g + 8][8 * n + 2 * t + 1] = silu(act.z[2][n][3]);
+  }
+  // dy per sample (kept in dz row space: column 0 of a scratch row)
+  if (t == 0) {
+    s.dz[w * 16 + g][0] = dy0;
+    s.dz[w * 16 + g + 8][0] = dy1;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < kH + 1; q += blockDim.x) {
+    float acc = 0.f;
+    for (int r = 0; r < 64; ++r) acc += s.dz[r][0] * (q < kH ? s.hin[r][q] : 1.f);
+    pp[q < kH ? kOffW4 + q : kOffB4] = acc;
+  }
+  __syncthreads();
+  // hidden layers 3, 2, 1
+#pragma unroll
+  for (int L = 2; L >= 0; --L) {
+    // stage dz (FP32) and the layer input (BF16-rounded) for the weight gradient
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      s.dz[w * 16 + g][8 * n + 2 * t] = dz[n][0];
+      s.dz[w * 16 + g][8 * n + 2 * t + 1] = dz[n][1];
+      s.dz[w * 16 + g + 8][8 * n + 2 * t] = dz[n][2];
+      s.dz[w * 16 + g + 8][8 * n + 2 * t + 1] = dz[n][3];
+    }
+    if (L > 0) {
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        s.hin[w * 16 + g][8 * n + 2 * t] = bf16r(silu(act.z[L - 1][n][0]));
+        s.hin[w * 16 + g][8 * n + 2 * t + 1] = bf16r(silu(act.z[L - 1][n][1]));
+        s.hin[w * 16 + g + 8][8 * n + 2 * t] = bf16r(silu(act.z[L - 1][n][2]));
+        s.hin[w * 16 + g + 8][8 * n + 2 * t + 1] = bf16r(silu(act.z[L - 1][n][3]));
+      }
+    } else if (lane < 16) {
+#pragma unroll
+      for (int q = 0; q < kF; ++q) s.hin[w * 16 + lane][q] = bf16r(s.xs[w][lane][q]);
+    }
+    __syncthreads();
+    const int nin = L > 0 ? kH : kF;
+    const int offW = L == 2 ? kOffW3 : (L == 1 ? kOffW2 : kOffW1);
+    const int offB = L == 2 ? kOffB3 : (L == 1 ? kOffB2 : kOffB1);
+    for (int q = threadIdx.x; q < kH * nin; q += blockDim.x) {
+      const int o = q / nin, i = q % nin;
+      float acc = 0.f;
+      for (int r = 0; r < 64; ++r) acc += s.dz[r][o] * s.hin[r][i];
+      pp[offW + q] = acc;
+    }
+    for (int o = threadIdx.x; o < kH; o += blockDim.x) {
+      float acc = 0.f;
+      for (int r = 0; r < 64; ++r) acc += s.dz[r][o];
+      pp[offB + o] = acc;
+    }
+    __syncthreads();
+    if (L > 0) {
+      // dh_{L-1} = bf16(dz_L) W_L on the tensor cores, then dz_{L-1}
+      const __nv_bfloat16(*W)[kH] = L == 2 ? s.net.W3 : s.net.W2;
+      uint32_t A[4][4];
+#pragma unroll
+      for (int kb = 0; kb < 4; ++kb) {
+        A[kb][0] = pack_bf16(dz[2 * kb][0], dz[2 * kb][1]);
+        A[kb][1] = pack_bf16(dz[2 * kb][2], dz[2 * kb][3]);
+        A[kb][2] = pack_bf16(dz[2 * kb + 1][0], dz[2 * kb + 1][1]);
+        A[kb][3] = pack_bf16(dz[2 * kb + 1][2], dz[2 * kb + 1][3]);
+      }
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kb = 0; kb < 4; ++kb) {
+          // B[k = o][n = i] = W[o][i]
+          const int o0 = 16 * kb + 2 * t, i0 = 8 * n + g;
+          __nv_bfloat162 v0, v1;
+          v0.x = W[o0][i0];
+          v0.y = W[o0 + 1][i0];
+          v1.x = W[o0 + 8][i0];
+          v1.y = W[o0 + 9][i0];
+          mma16816(c, A[kb], *reinterpret_cast<uint32_t *>(&v0), *reinterpret_cast<uint32_t *>(&v1));
+        }
+        dz[n][0] = c[0] * silu_grad(act.z[L - 1][n][0]);
+        dz[n][1] = c[1] * silu_grad(act.z[L - 1][n][1]);
+        dz[n][2] = c[2] * silu_grad(act.z[L - 1][n][2]);
+        dz[n][3] = c[3] * silu_grad(act.z[L - 1][n][3]);
+      }
+    }
+    __syncthreads();
+  }
+  // loss partial: lanes with t == 0 hold row losses; fixed-order sum
+  lsum += __shfl_xor_sync(0xffffffffu, lsum, 4);
+  lsum += __shfl_xor_sync(0xffffffffu, lsum, 8);
+  lsum += __shfl_xor_sync(0xffffffffu, lsum, 16);
+  __shared__ float ls[4];
+  if (lane == 0) ls[w] = lsum;
+  __syncthreads();
+  if (threadIdx.x == 0) loss_part[blockIdx.x] = ((ls[0] + ls[1]) + (ls[2] + ls[3]));
+}
+
+// gradient = sum of the block partials in block order; loss likewise
+__global__ void k_grad_reduce(int nblk, const float *__restrict__ part, const float *__restrict__ loss_part,
+                              int64_t B, float *__restrict__ grad, float *__restrict__ loss) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < kNWeights) {
+    float acc = 0.f;
+    for (int b = 0; b < nblk; ++b) acc += part[static_cast<int64_t>(b) * kNWeights + q];
+    grad[q] = acc;
+  }
+  if (q == 0 && loss) {
+    float acc = 0.f;
+    for (int b = 0; b < nblk; ++b) acc += loss_part[b];
+    *loss = acc / static_cast<float>(B);
+  }
+}
+
+__global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
+                       const float *__restrict__ g, float lr, float b1, float b2, float eps, int step) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= kNWeights) return;
+  const float gg = g[q];
+  const float mm = b1 * m[q] + (1.f - b1) * gg;
+  const float vv = b2 * v[q] + (1.f - b2) * gg * gg;
+  m[q] = mm;
+  v[q] = vv;
+  const float mh = mm / (1.f - powf(b1, static_cast<float>(step)));
+  const float vh = vv / (1.f - powf(b2, static_cast<float>(step)));
+  p[q] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+// ---------------------------------------------------------------------------
+// scoring of the walk's candidate pairs
+// ---------------------------------------------------------------------------
+// score[t] = predicted log10 normalised error for frontier pairs that pass the
+// safety bound (A != B, |Z_A - Z_B| >= R_A + R_B); +inf otherwise.
+__global__ void __launch_bounds__(128) k_walk_scores(int64_t nf, const int2 *__restrict__ front,
+                                                     const float *__restrict__ params, const double *__restrict__ Z,
+                                                     const double *__restrict__ Rmax, const double *__restrict__ M,
+                                                     const double *__restrict__ mom, int mstride,
+                                                     const int32_t *__restrict__ count, float *__restrict__ score) {
+  __shared__ NetSmem s;
+  __shared__ float xs[4][16][kF];
+  __shared__ int cand[4][16];
+  load_net(s, params);
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t base = (static_cast<int64_t>(blockIdx.x) * 4 + w) * 16;
+  if (lane < 16) {
+    const int64_t k = base + lane;
+    int ok = 0;
+    float f[kF] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (k < nf) {
+      const int A = front[k].x, B = front[k].y;
+      if (A != B) {
+        const double dx = __dsub_rn(Z[3 * A], Z[3 * B]), dy = __dsub_rn(Z[3 * A + 1], Z[3 * B + 1]),
+                     dz = __dsub_rn(Z[3 * A + 2], Z[3 * B + 2]);
+        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        const double sr = __dadd_rn(Rmax[A], Rmax[B]);
+        ok = d2 >= __dmul_rn(sr, sr);
+        if (ok) pair_features(A, B, Z, Rmax, M, mom, mstride, count, f);
+      }
+    }
+    cand[w][lane] = ok;
+#pragma unroll
+    for (int q = 0; q < kF; ++q) xs[w][lane][q] = (f[q] - s.mean[q]) * s.scale[q];
+  }
+  __syncwarp();
+  Act act;
+  forward16(s, xs[w], act);
+  const int g = lane >> 2;
+  if ((lane & 3) == 0) {
+    if (base + g < nf) score[base + g] = cand[w][g] ? act.y[0] : INFINITY;
+    if (base + g + 8 < nf) score[base + g + 8] = cand[w][g + 8] ? act.y[1] : INFINITY;
+  }
+}
+
+__global__ void k_gather_batch(int64_t B, const int64_t *__restrict__ perm, int64_t start, int64_t n,
+                               const float *__restrict__ X, const float *__restrict__ y, float *__restrict__ xb,
+                               float *__restrict__ yb) {
+  const int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (b >= B) return;
+  const int64_t i = perm[(start + b) % n];
+#pragma unroll
+  for (int q = 0; q < kF; ++q) xb[b * kF + q] = X[i * kF + q];
+  yb[b] = y[i];
+}
+
+}  // namespace
+
+int walk_scores(fmm_ctx *c, int64_t nf, const int2 *front, float *score) {
+  k_walk_scores<<<grid_for(nf, 64), 128, 0, c->stream>>>(nf, front, ptr<float>(c->sel_params), ptr<double>(c->Z),
+                                                         ptr<double>(c->Rmax), ptr<double>(c->M), ptr<double>(c->mom),
+                                                         mom_stride(c->opts.order_P), ptr<int32_t>(c->count), score);
+  return launched(c, "walk_scores");
+}
+
+}  // namespace amfmm
+
+using namespace amfmm;
+
+extern "C" {
+
+int fmm_selector_nparams(void) { return kNParams; }
+
+int fmm_selector_set(fmm_ctx *c, const float *params, double log10_target, int enable) {
+  if (!c) return FMM_EINVAL;
+  if (enable) {
+    if (!params) return set_error(c, FMM_EINVAL, "NULL parameters");
+    AMFMM_TRY(ensure<float>(c, c->sel_params, kNParams));
+    AMFMM_CUDA(c, cudaMemcpyAsync(c->sel_params.p, params, sizeof(float) * kNParams, cudaMemcpyHostToDevice,
+                                  c->stream));
+    AMFMM_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  c->sel_enabled = enable != 0;
+  c->sel_log10_target = log10_target;
+  c->stage = kNone;
+  return FMM_OK;
+}
+
+int fmm_selector_samples(fmm_ctx *c, const int32_t *pairs, int64_t K, float *feat, float *label) {
+  if (!c) return FMM_EINVAL;
+  if (c->stage < kUp) return set_error(c, FMM_EORDER, "fmm_selector_samples needs fmm_upward first");
+  if (c->opts.order_P != 3) return set_error(c, FMM_EUNSUPPORTED, "samples are built at order 3");
+  if (K < 0 || (K > 0 && (!pairs || !feat))) return set_error(c, FMM_EINVAL, "bad sample arguments");
+  if (K == 0) return FMM_OK;
+  cudaStream_t st = c->stream;
+  const int2 *pp = reinterpret_cast<const int2 *>(pairs);
+  k_features<<<grid_for(K, 256), 256, 0, st>>>(K, pp, ptr<double>(c->Z), ptr<double>(c->Rmax), ptr<double>(c->M),
+                                               ptr<double>(c->mom), mom_stride(3), ptr<int32_t>(c->count), feat);
+  AMFMM_TRY(launched(c, "features"));
+  if (label) {
+    // the pairs' order-3 TC locals, then the per-pair errors
+    AMFMM_TRY(ensure<double>(c, c->sel_scratch, static_cast<size_t>(K) * 40));
+    AMFMM_TRY(pair_locals_tc(c, pp, K, ptr<double>(c->sel_scratch)));
+    k_labels<<<static_cast<unsigned>(K), 128, 0, st>>>(K, pp, ptr<int32_t>(c->begin), ptr<int32_t>(c->count),
+                                                         ptr<double>(c->X), ptr<double>(c->Y), ptr<double>(c->Zb),
+                                                         ptr<double>(c->Mb), ptr<double>(c->Z),
+                                                         ptr<double>(c->sel_scratch), label);
+    AMFMM_TRY(launched(c, "labels"));
+  }
+  return FMM_OK;
+}
+
+int fmm_mlp_forward(fmm_ctx *c, const float *params, const float *feat, int64_t K, float *out) {
+  if (!c || !params || K < 0) return FMM_EINVAL;
+  if (K == 0) return FMM_OK;
+  k_mlp_infer<<<grid_for(K, 64), 128, 0, c->stream>>>(K, params, feat, out);
+  return launched(c, "mlp_infer");
+}
+
+int fmm_mlp_grad(fmm_ctx *c, const float *params, const float *feat, const float *label, int64_t B, float *grad,
+                 float *loss) {
+  if (!c || !params || !feat || !label || !grad || B < 1) return FMM_EINVAL;
+  const int nblk = static_cast<int>((B + 63) / 64);
+  AMFMM_TRY(ensure<float>(c, c->sel_part, static_cast<size_t>(nblk) * kNWeights + nblk + 8));
+  float *part = ptr<float>(c->sel_part);
+  float *lpart = part + static_cast<size_t>(nblk) * kNWeights;
+  const size_t shm = sizeof(TrainSmem);
+  static bool attr = false;
+  if (!attr) {
+    AMFMM_CUDA(c, cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
+    attr = true;
+  }
+  k_mlp_grad<<<nblk, 128, shm, c->stream>>>(B, params, feat, label, part, lpart);
+  AMFMM_TRY(launched(c, "mlp_grad"));
+  k_grad_reduce<<<grid_for(kNWeights, 256), 256, 0, c->stream>>>(nblk, part, lpart, B, grad, loss);
+  return launched(c, "grad_reduce");
+}
+
+int fmm_mlp_adam(fmm_ctx *c, float *params, float *m, float *v, const float *grad, float lr, int step) {
+  if (!c || !params || !m || !v || !grad || step < 1) return FMM_EINVAL;
+  k_adam<<<grid_for(kNWeights, 256), 256, 0, c->stream>>>(params, m, v, grad, lr, 0.9f, 0.999f, 1e-8f, step);
+  return launched(c, "adam");
+}
+
+// Adam on minibatches drawn in the order of one seeded permutation of the
+// samples (wrapping around), one device step per minibatch.
+int fmm_selector_train(fmm_ctx *c, float *params, float *adam, const float *X, const float *y, int64_t n, int batch,
+                       int steps, float lr, unsigned long long seed, float *loss_out) {
+  if (!c || !params || !adam || !X || !y || n < 1 || batch < 1 || steps < 0) return FMM_EINVAL;
+  std::vector<int64_t> perm(static_cast<size_t>(n));
+  for (int64_t i = 0; i < n; ++i) perm[static_cast<size_t>(i)] = i;
+  std::mt19937_64 rng(seed);
+  for (int64_t i = n - 1; i > 0; --i) {
+    std::uniform_int_distribution<int64_t> d(0, i);
+    std::swap(perm[static_cast<size_t>(i)], perm[static_cast<size_t>(d(rng))]);
+  }
+  AMFMM_TRY(ensure<int64_t>(c, c->sel_perm, static_cast<size_t>(n)));
+  AMFMM_CUDA(c, cudaMemcpyAsync(c->sel_perm.p, perm.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->stream));
+  AMFMM_TRY(ensure<float>(c, c->sel_xb, static_cast<size_t>(batch) * kF));
+  AMFMM_TRY(ensure<float>(c, c->sel_yb, static_cast<size_t>(batch)));
+  AMFMM_TRY(ensure<float>(c, c->sel_grad, static_cast<size_t>(kNWeights) + 1 + static_cast<size_t>(steps)));
+  float *grad = ptr<float>(c->sel_grad);
+  float *losses = grad + kNWeights + 1;
+  for (int s = 0; s < steps; ++s) {
+    k_gather_batch<<<grid_for(batch, 256), 256, 0, c->stream>>>(batch, ptr<int64_t>(c->sel_perm),
+                                                                static_cast<int64_t>(s) * batch, n, X, y,
+                                                                ptr<float>(c->sel_xb), ptr<float>(c->sel_yb));
+    AMFMM_TRY(launched(c, "gather_batch"));
+    AMFMM_TRY(fmm_mlp_grad(c, params, ptr<float>(c->sel_xb), ptr<float>(c->sel_yb), batch, grad, losses + s));
+    AMFMM_TRY(fmm_mlp_adam(c, params, adam, adam + kNWeights, grad, lr, s + 1));
+  }
+  if (loss_out && steps > 0)
+    AMFMM_CUDA(c, cudaMemcpyAsync(loss_out, losses, sizeof(float) * steps, cudaMemcpyDeviceToHost, c->stream));
+  AMFMM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return FMM_OK;
+}
+
+}  // extern "C"

@@ -175,52 +175,119 @@ __global__ void k_radix_hist(const K *__restrict__ key, int64_t n, int shift,
     hist[static_cast<int64_t>(d) * ntiles + blockIdx.x] = cnt[d];
 }
 
-// Stable scatter of one tile: keys are taken in index order, kSortBlock at a
-// time; within a round, equal digits rank by lane (warp match) and by warp
-// (prefix over the per-warp counts), after all earlier rounds of the tile.
+// Stable scatter of one tile of kSortTile keys.  Warp w owns the keys
+// [w * 512, (w + 1) * 512) of the tile and takes them 32 at a time in index
+// order: a key's rank among the warp's keys of its digit is the warp's running
+// count of that digit (shared memory, updated by the first lane of each group
+// of equal digits) plus its rank within the group.  One exclusive scan over
+// (digit, warp) then gives every key its position in the tile's stably
+// digit-sorted order; the tile is staged in that order in shared memory and
+// written out so that consecutive threads store consecutive positions of a
+// bucket (coalesced).
+constexpr int kWarpKeys = kSortTile / (kSortBlock / 32);  // 512
+constexpr int kRounds = kWarpKeys / 32;                   // 16
+static_assert(kRadix == 2 * kSortBlock, "the scan gives each thread two digits");
+
 template <class K>
 __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(
     const K *__restrict__ key, const uint32_t *__restrict__ val, int64_t n, int shift,
     const int32_t *__restrict__ offs, int ntiles, K *__restrict__ okey, uint32_t *__restrict__ oval) {
-  __shared__ int run[kRadix];
-  __shared__ int wc[kSortBlock / 32][kRadix + 1];
-  __shared__ int wp[kSortBlock / 32][kRadix + 1];
-  const int t = threadIdx.x, w = t >> 5;
-  for (int d = t; d < kRadix; d += kSortBlock) {
-    run[d] = 0;
-    for (int q = 0; q < kSortBlock / 32; ++q) wc[q][d] = 0;
-  }
-  if (t < kSortBlock / 32) wc[t][kRadix] = 0;
+  constexpr int kW = kSortBlock / 32;
+  constexpr size_t kCntBytes = sizeof(int) * kW * (kRadix + 1);
+  constexpr size_t kStageBytes = sizeof(K) * kSortTile;
+  __shared__ __align__(16) unsigned char pool[kCntBytes > kStageBytes ? kCntBytes : kStageBytes];
+  __shared__ int dstart[kRadix];
+  __shared__ int goff[kRadix];
+  __shared__ int wsum[kW];
+  int(*cnt)[kRadix + 1] = reinterpret_cast<int(*)[kRadix + 1]>(pool);
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int64_t tile0 = static_cast<int64_t>(blockIdx.x) * kSortTile;
+  const int nvalid = static_cast<int>(n - tile0 < kSortTile ? n - tile0 : kSortTile);
+  for (int q = t; q < kW * (kRadix + 1); q += kSortBlock) (&cnt[0][0])[q] = 0;
+  for (int d = t; d < kRadix; d += kSortBlock) goff[d] = offs[static_cast<int64_t>(d) * ntiles + blockIdx.x];
   __syncthreads();
-  const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
   const unsigned lt = lanemask_lt();
-  for (int r = 0; r < kSortItems; ++r) {
-    const int64_t i = base + static_cast<int64_t>(r) * kSortBlock + t;
-    const bool valid = i < n;
-    K k = valid ? key[i] : K(0);
-    uint32_t v = valid ? val[i] : 0u;
-    int d = valid ? static_cast<int>((k >> shift) & kDigitMask) : kRadix;
-    unsigned peers = __match_any_sync(0xffffffffu, d);
-    int wrank = __popc(peers & lt);
-    if (wrank == 0) wc[w][d] = __popc(peers);
-    __syncthreads();
-    for (int dd = t; dd < kRadix; dd += kSortBlock) {
-      int s = run[dd];
+  K k[kRounds];
+  uint32_t v[kRounds];
+  int lpos[kRounds];
 #pragma unroll
-      for (int q = 0; q < kSortBlock / 32; ++q) {
-        wp[q][dd] = s;
-        s += wc[q][dd];
-        wc[q][dd] = 0;
-      }
-      run[dd] = s;
+  for (int r = 0; r < kRounds; ++r) {
+    const int li = w * kWarpKeys + r * 32 + lane;
+    const bool valid = li < nvalid;
+    k[r] = valid ? key[tile0 + li] : K(0);
+    v[r] = valid ? val[tile0 + li] : 0u;
+    const int d = valid ? static_cast<int>((k[r] >> shift) & kDigitMask) : kRadix;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int wrank = __popc(peers & lt);
+    const int prev = cnt[w][d];
+    __syncwarp();
+    lpos[r] = prev + wrank;
+    if (wrank == 0) cnt[w][d] = prev + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // exclusive scan over (digit, warp), digit-major: thread t owns digits
+  // 2t and 2t + 1 (kRadix = 2 * kSortBlock)
+  int own = 0;
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int q = 0; q < kW; ++q) own += cnt[q][2 * t + h];
+  int incl = own;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  int before = incl - own;
+  for (int q = 0; q < w; ++q) before += wsum[q];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int dd = 2 * t + h;
+    dstart[dd] = before;
+#pragma unroll
+    for (int q = 0; q < kW; ++q) {
+      const int cq = cnt[q][dd];
+      cnt[q][dd] = before;
+      before += cq;
     }
-    if (t < kSortBlock / 32) wc[t][kRadix] = 0;
-    __syncthreads();
-    if (valid) {
-      int64_t pos = static_cast<int64_t>(offs[static_cast<int64_t>(d) * ntiles + blockIdx.x]) + wp[w][d] + wrank;
-      okey[pos] = k;
-      oval[pos] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    const int li = w * kWarpKeys + r * 32 + lane;
+    if (li < nvalid) lpos[r] += cnt[w][static_cast<int>((k[r] >> shift) & kDigitMask)];
+  }
+  __syncthreads();  // the counts are dead from here; the pool stages the tile
+  K *sk = reinterpret_cast<K *>(pool);
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r)
+    if (w * kWarpKeys + r * 32 + lane < nvalid) sk[lpos[r]] = k[r];
+  __syncthreads();
+  int dig[kRounds];
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    const int j = r * kSortBlock + t;
+    dig[r] = 0;
+    if (j < nvalid) {
+      const K kk = sk[j];
+      const int d = static_cast<int>((kk >> shift) & kDigitMask);
+      dig[r] = d;
+      okey[goff[d] + (j - dstart[d])] = kk;
     }
+  }
+  __syncthreads();
+  uint32_t *sv = reinterpret_cast<uint32_t *>(pool);
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r)
+    if (w * kWarpKeys + r * 32 + lane < nvalid) sv[lpos[r]] = v[r];
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    const int j = r * kSortBlock + t;
+    if (j < nvalid) oval[goff[dig[r]] + (j - dstart[dig[r]])] = sv[j];
   }
 }
 

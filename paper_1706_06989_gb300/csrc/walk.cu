@@ -26,28 +26,42 @@ constexpr int kBlock = 256;
 
 enum Action : int32_t { kSelfLeaf = 0, kSelfSplit = 1, kAccept = 2, kNear = 3, kSplitA = 4, kSplitB = 5 };
 
-__device__ __forceinline__ bool well_separated(int A, int B, const double *__restrict__ Z,
-                                               const double *__restrict__ Rmax, double theta) {
-  const double dx = __dsub_rn(Z[3 * A], Z[3 * B]);
-  const double dy = __dsub_rn(Z[3 * A + 1], Z[3 * B + 1]);
-  const double dz = __dsub_rn(Z[3 * A + 2], Z[3 * B + 2]);
+// per cell {Z_x, Z_y, Z_z, R_max}, one 32-byte load
+__device__ __forceinline__ bool well_separated(const double4_32a a, const double4_32a b, double theta) {
+  const double dx = __dsub_rn(a.x, b.x);
+  const double dy = __dsub_rn(a.y, b.y);
+  const double dz = __dsub_rn(a.z, b.z);
   const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
   const double th2 = __dmul_rn(theta, theta);
-  const double s = __dadd_rn(Rmax[A], Rmax[B]);
+  const double s = __dadd_rn(a.w, b.w);
   return __dmul_rn(th2, d2) >= __dmul_rn(s, s);
 }
 
-__global__ void k_classify(int64_t nf, const int2 *__restrict__ front, const int32_t *__restrict__ nchild,
-                           const int32_t *__restrict__ level, const double *__restrict__ Z,
-                           const double *__restrict__ Rmax, double theta, int32_t *__restrict__ action,
-                           int4 *__restrict__ counts) {
+// packs the walk's per-cell inputs: {Z, R_max} and {nchild, level}
+__global__ void k_pack_cells(int32_t ncell, const double *__restrict__ Z, const double *__restrict__ Rmax,
+                             const int32_t *__restrict__ nchild, const int32_t *__restrict__ level,
+                             double4_32a *__restrict__ zr, int2 *__restrict__ nl) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  zr[c] = make_double4_32a(Z[3 * c], Z[3 * c + 1], Z[3 * c + 2], Rmax[c]);
+  nl[c] = make_int2(nchild[c], level[c]);
+}
+
+// score (may be NULL): the learned selector's prediction for every frontier
+// pair (+inf where the safety bound fails); with it, a pair is accepted when
+// the opening criterion accepts it (theta is then a floor on the accepted
+// set, which bounds the work of a strict target) or when score < target.
+__global__ void k_classify(int64_t nf, const int2 *__restrict__ front, const int2 *__restrict__ nl,
+                           const double4_32a *__restrict__ zr, double theta, const float *__restrict__ score,
+                           float target, int32_t *__restrict__ action, int4 *__restrict__ counts) {
   int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (t >= nf) return;
   const int A = front[t].x, B = front[t].y;
   int act;
   int4 cnt = make_int4(0, 0, 0, 0);
+  const int2 nlA = nl[A];
   if (A == B) {
-    const int k = nchild[A];
+    const int k = nlA.x;
     if (k == 0) {
       act = kSelfLeaf;
       cnt.w = 1;
@@ -55,11 +69,12 @@ __global__ void k_classify(int64_t nf, const int2 *__restrict__ front, const int
       act = kSelfSplit;
       cnt.x = k + k * (k - 1) / 2;
     }
-  } else if (well_separated(A, B, Z, Rmax, theta)) {
+  } else if (well_separated(zr[A], zr[B], theta) || (score && score[t] < target)) {
     act = kAccept;
     cnt.y = 1;
   } else {
-    const int ka = nchild[A], kb = nchild[B];
+    const int2 nlB = nl[B];
+    const int ka = nlA.x, kb = nlB.x;
     if (ka == 0 && kb == 0) {
       act = kNear;
       cnt.z = 1;
@@ -68,9 +83,9 @@ __global__ void k_classify(int64_t nf, const int2 *__restrict__ front, const int
       if (kb == 0) pickA = true;
       else if (ka == 0) pickA = false;
       else {
-        const double ra = Rmax[A], rb = Rmax[B];
+        const double ra = zr[A].w, rb = zr[B].w;
         if (ra != rb) pickA = ra > rb;
-        else if (level[A] != level[B]) pickA = level[A] < level[B];
+        else if (nlA.y != nlB.y) pickA = nlA.y < nlB.y;
         else pickA = A < B;
       }
       act = pickA ? kSplitA : kSplitB;
@@ -150,6 +165,13 @@ int walk(fmm_ctx *c) {
   }
 
   int4 *total = ptr<int4>(c->totals);
+  const int64_t nc = c->sz.ncell;
+  AMFMM_TRY(ensure<double4_32a>(c, c->walk_zr, nc));
+  AMFMM_TRY(ensure<int2>(c, c->walk_nl, nc));
+  k_pack_cells<<<grid_for(nc, kBlock), kBlock, 0, st>>>(static_cast<int32_t>(nc), ptr<double>(c->Z), ptr<double>(c->Rmax),
+                                                       ptr<int32_t>(c->nchild), ptr<int32_t>(c->level),
+                                                       ptr<double4_32a>(c->walk_zr), ptr<int2>(c->walk_nl));
+  AMFMM_TRY(launched(c, "walk_pack"));
   // one self pair per root: systems of a forest never interact
   const int64_t nsys = c->sz.nsys;
   if (nsys > static_cast<int64_t>(c->front[0].cap / sizeof(int2))) AMFMM_TRY(ensure<int2>(c, c->front[0], nsys));
@@ -161,9 +183,15 @@ int walk(fmm_ctx *c) {
     AMFMM_TRY(ensure<int32_t>(c, c->action, nf));
     AMFMM_TRY(ensure<int4>(c, c->wcount, nf));
     AMFMM_TRY(ensure<int4>(c, c->woff, nf));
+    const float *score = nullptr;
+    if (c->sel_enabled) {
+      AMFMM_TRY(ensure<float>(c, c->sel_score, nf));
+      AMFMM_TRY(walk_scores(c, nf, ptr<int2>(c->front[cur]), ptr<float>(c->sel_score)));
+      score = ptr<float>(c->sel_score);
+    }
     k_classify<<<grid_for(nf, kBlock), kBlock, 0, st>>>(
-        nf, ptr<int2>(c->front[cur]), ptr<int32_t>(c->nchild), ptr<int32_t>(c->level),
-        ptr<double>(c->Z), ptr<double>(c->Rmax), c->theta, ptr<int32_t>(c->action), ptr<int4>(c->wcount));
+        nf, ptr<int2>(c->front[cur]), ptr<int2>(c->walk_nl), ptr<double4_32a>(c->walk_zr), c->theta, score,
+        static_cast<float>(c->sel_log10_target), ptr<int32_t>(c->action), ptr<int4>(c->wcount));
     AMFMM_TRY(launched(c, "walk_classify"));
     AMFMM_TRY(exclusive_scan_i4(c, ptr<int4>(c->wcount), ptr<int4>(c->woff), nf, total));
     int4 *h = static_cast<int4 *>(c->hpin);

@@ -79,11 +79,19 @@ def load() -> ctypes.CDLL:
                 "fmm_leapfrog": [P, P, P, P, P, P, P, P, I64, D, I, P, P, P, P],
                 "fmm_solve_batch": [P, P, P, P, P, P, I, P, P, P],
                 "fmm_autotune_ncrit": [P, P, P, P, P, P, I, P, I, I, P, P, P, P, P],
+                "fmm_selector_set": [P, P, D, I],
+                "fmm_selector_samples": [P, P, I64, P, P],
+                "fmm_mlp_forward": [P, P, P, I64, P],
+                "fmm_mlp_grad": [P, P, P, P, I64, P, P],
+                "fmm_mlp_adam": [P, P, P, P, P, ctypes.c_float, I],
+                "fmm_selector_train": [P, P, P, P, P, I64, I, I, ctypes.c_float, ctypes.c_ulonglong, P],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
                 f.argtypes = args
                 f.restype = I
+            lib.fmm_selector_nparams.argtypes = []
+            lib.fmm_selector_nparams.restype = I
             lib.fmm_destroy.argtypes = [P]
             lib.fmm_destroy.restype = None
             lib.fmm_last_error.argtypes = [P]
@@ -272,6 +280,57 @@ class FMM:
                                                 *(_dptr(o) for o in out), ctypes.byref(best),
                                                 ctypes.c_void_p(ms.ctypes.data)), "fmm_autotune_ncrit")
         return int(best.value), {int(k): float(v) for k, v in zip(cand, ms)}
+
+    # ---- learned pair selector (a12) -------------------------------------------
+    def selector_nparams(self) -> int:
+        return int(self.lib.fmm_selector_nparams())
+
+    def selector_set(self, params, log10_target: float, enable: bool = True):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32) if params is not None else None
+        if enable and (p is None or p.shape[0] != self.selector_nparams()):
+            raise ValueError("params must hold fmm_selector_nparams() floats")
+        self._check(self.lib.fmm_selector_set(self._h, ctypes.c_void_p(p.ctypes.data) if p is not None else None,
+                                              float(log10_target), int(bool(enable))), "fmm_selector_set")
+
+    def selector_samples(self, pairs, labels: bool = True):
+        """Raw features [K, 8] (and labels [K]) of cell pairs of the current tree."""
+        t = self._torch
+        pr = t.as_tensor(pairs, dtype=t.int32, device=self._bodies[0].device).contiguous()
+        K = pr.shape[0]
+        feat = t.empty((K, 8), dtype=t.float32, device=pr.device)
+        lab = t.empty(K, dtype=t.float32, device=pr.device) if labels else None
+        self._check(self.lib.fmm_selector_samples(self._h, _dptr(pr), K, _dptr(feat), _dptr(lab) if labels else None),
+                    "fmm_selector_samples")
+        return feat, lab
+
+    def mlp_forward(self, params, feat):
+        t = self._torch
+        out = t.empty(feat.shape[0], dtype=t.float32, device=feat.device)
+        self._check(self.lib.fmm_mlp_forward(self._h, _dptr(params), _dptr(feat.contiguous()), feat.shape[0],
+                                             _dptr(out)), "fmm_mlp_forward")
+        return out
+
+    def mlp_grad(self, params, feat, label):
+        t = self._torch
+        g = t.empty(params.shape[0], dtype=t.float32, device=feat.device)
+        loss = t.empty(1, dtype=t.float32, device=feat.device)
+        self._check(self.lib.fmm_mlp_grad(self._h, _dptr(params), _dptr(feat.contiguous()), _dptr(label.contiguous()),
+                                          feat.shape[0], _dptr(g), _dptr(loss)), "fmm_mlp_grad")
+        return g, loss
+
+    def selector_train(self, params, X, y, batch: int, steps: int, lr: float, seed: int = 0, adam=None):
+        """Adam on minibatches (params: device float32 tensor, updated in place)."""
+        import numpy as np
+        t = self._torch
+        if adam is None:
+            adam = t.zeros(2 * params.shape[0], dtype=t.float32, device=params.device)
+        losses = np.zeros(max(steps, 1), dtype=np.float32)
+        self._check(self.lib.fmm_selector_train(self._h, _dptr(params), _dptr(adam), _dptr(X.contiguous()),
+                                                _dptr(y.contiguous()), X.shape[0], int(batch), int(steps),
+                                                float(lr), int(seed), ctypes.c_void_p(losses.ctypes.data)),
+                    "fmm_selector_train")
+        return losses[:steps], adam
 
     # ---- time integration (a14) ---------------------------------------------
     def leapfrog(self, x, y, z, vx, vy, vz, m, dt: float, nsteps: int, acc=None, record=True):

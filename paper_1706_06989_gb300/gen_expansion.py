@@ -237,7 +237,7 @@ def emit_P(P: int) -> str:
     return "\n".join(L)
 
 
-def main():
+def render() -> str:
     parts = ["// expansion_gen.cuh -- GENERATED by gen_expansion.py; do not edit.",
              "// General-order Cartesian expansion of App. A in multi-index form (see the",
              "// generator's docstring for the formulas).  Included by expansion.cu.",
@@ -248,8 +248,12 @@ def main():
     for P in ORDERS:
         parts.append(emit_P(P))
         parts.append("")
+    return "\n".join(parts) + "\n"
+
+
+def main():
     with open(OUT, "w") as f:
-        f.write("\n".join(parts) + "\n")
+        f.write(render())
     print(OUT)
 
 

@@ -1,0 +1,85 @@
+"""Learned pair selector: training data taken from the method's own accepted
+pairs, and the network's training, through the C ABI.
+
+Every numerical step (features, labels, forward, backward, Adam) runs in the
+library's kernels; this module only chooses which pairs to label, how the
+features are normalised and the initial weights.
+
+Labels are the method's own errors: for a cell pair (A, B) accepted at some
+opening angle, the rms over the bodies of A and B of the difference between
+the torque-corrected order-3 M2L acceleration and the direct A<->B sum,
+normalised by (M_A + M_B)/|r|^2, in log10 (see fmm_selector_samples).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+NPARAMS = 8977
+H, F = 64, 8
+
+
+def init_params(feat: np.ndarray, seed: int = 0) -> np.ndarray:
+    """Feature normalisation from samples, weights by a seeded He-style draw."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = np.zeros(NPARAMS, dtype=np.float32)
+    o = 0
+
+    def put(a):
+        nonlocal o
+        p[o:o + a.size] = a.ravel()
+        o += a.size
+
+    put(rng.normal(0, np.sqrt(2.0 / F), (H, F)))
+    put(np.zeros(H))
+    put(rng.normal(0, np.sqrt(2.0 / H), (H, H)))
+    put(np.zeros(H))
+    put(rng.normal(0, np.sqrt(2.0 / H), (H, H)))
+    put(np.zeros(H))
+    put(rng.normal(0, np.sqrt(1.0 / H), H))
+    put(np.zeros(1))
+    f = np.asarray(feat, dtype=np.float64)
+    mean = f.mean(0)
+    std = f.std(0)
+    put(mean)
+    put(1.0 / np.where(std > 1e-6, std, 1.0))
+    assert o == NPARAMS
+    return p
+
+
+def pair_samples(solver, x, y, z, m, thetas=(0.3, 0.5, 0.7, 1.0), per_theta: int = 200_000,
+                 max_work: float = 4e6, seed: int = 0):
+    """Features and labels of pairs accepted at the given opening angles.
+
+    solver: an fmm.FMM (order 3, selector disabled); x, y, z, m: device
+    tensors.  At most per_theta pairs per angle, drawn (seeded) among those
+    with n_A n_B <= max_work.  Returns (feat [K, 8], label [K]) on the device.
+    """
+    import torch
+    rng = np.random.Generator(np.random.PCG64(seed))
+    feats, labs = [], []
+    for th in thetas:
+        solver.set_opts(theta=th)
+        solver.solve(x, y, z, m)
+        m2l, _, _ = solver.export_lists()
+        cnt = solver.export_tree(geometry=False)["count"].to(torch.int64)
+        work = (cnt[m2l[:, 0].long()] * cnt[m2l[:, 1].long()]).cpu().numpy()
+        ok = np.nonzero(work <= max_work)[0]
+        if ok.size == 0:
+            continue
+        pick = np.sort(rng.choice(ok, size=min(per_theta, ok.size), replace=False))
+        pairs = m2l[torch.as_tensor(pick, device=m2l.device)].contiguous()
+        # the tree of the last solve is current: fmm_selector_samples needs it
+        f, l = solver.selector_samples(pairs, labels=True)
+        feats.append(f)
+        labs.append(l)
+    return torch.cat(feats), torch.cat(labs)
+
+
+def train(solver, feat, label, steps: int = 2000, batch: int = 4096, lr: float = 2e-3, seed: int = 0,
+          params: np.ndarray | None = None):
+    """Trains the network; returns (params as numpy float32, losses)."""
+    import torch
+    p0 = init_params(feat.cpu().numpy(), seed) if params is None else params
+    dev = torch.as_tensor(p0, device=feat.device).contiguous()
+    losses, _ = solver.selector_train(dev, feat, label, batch=batch, steps=steps, lr=lr, seed=seed)
+    return dev.cpu().numpy(), losses

@@ -46,3 +46,10 @@ def test_binding_structs_match_header():
     opts = re.search(r"typedef struct \{(.*?)\} fmm_opts;", src, re.S).group(1)
     names = re.findall(r"\b(\w+)\s*;", re.sub(r"/\*.*?\*/", "", opts, flags=re.S))
     assert names == [f[0] for f in fmm._Opts._fields_]
+
+
+def test_generated_expansion_header_matches_its_generator():
+    """csrc/expansion_gen.cuh is the output of gen_expansion.py (no hand edits)."""
+    from paper_1706_06989_gb300 import gen_expansion
+    with open(gen_expansion.OUT) as f:
+        assert f.read() == gen_expansion.render()

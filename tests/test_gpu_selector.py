@@ -1,0 +1,158 @@
+"""a12: the learned pair selector on the GPU -- network forward and gradient
+against the reference network, features and labels against the oracle, and
+the walk with the selector (mutual pairs, conservation, coverage)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as M
+from paper_1706_06989_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _solver(**kw):
+    from paper_1706_06989_gb300 import fmm
+    return fmm.FMM(**kw)
+
+
+def _dev(b):
+    return tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (b.x, b.y, b.z, b.m))
+
+
+def _params(seed=0):
+    rng = np.random.default_rng(seed)
+    p = (rng.normal(size=M.NPARAMS) * 0.15).astype(np.float32)
+    p[M.NW:M.NW + 8] = rng.normal(size=8).astype(np.float32)
+    p[M.NW + 8:] = rng.uniform(0.5, 1.5, 8).astype(np.float32)
+    return p
+
+
+def test_mlp_forward_and_gradient_match_reference():
+    s = _solver()
+    rng = np.random.default_rng(4)
+    p = _params(1)
+    X = rng.normal(size=(1000, 8)).astype(np.float32) * 2
+    y = rng.normal(size=1000).astype(np.float32)
+    pd = torch.from_numpy(p).cuda()
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    out = s.mlp_forward(pd, Xd).cpu().numpy()
+    ref, _, _ = M.forward(p, X, "bf16")
+    assert np.abs(out - ref).max() <= 2e-3 * (1 + np.abs(ref).max())
+    g, loss = s.mlp_grad(pd, Xd, yd)
+    rl, rg = M.loss_and_grad(p, X, y, "bf16")
+    g = g.cpu().numpy()[:M.NW]
+    assert abs(float(loss.cpu()) - rl) <= 1e-3 * rl
+    assert np.linalg.norm(g - rg) <= 1e-2 * np.linalg.norm(rg)
+    g2, _ = s.mlp_grad(pd, Xd, yd)
+    assert np.array_equal(g, g2.cpu().numpy()[:M.NW])  # reproducible
+
+
+def test_features_and_labels_match_oracle():
+    b = ics.plummer(3000, seed=5)
+    s = _solver(theta=0.5)
+    x, y, z, m = _dev(b)
+    s.solve(x, y, z, m)
+    m2l, _, _ = s.export_lists()
+    sel = m2l[::max(1, m2l.shape[0] // 150)].contiguous()
+    feat, lab = s.selector_samples(sel)
+    feat, lab, sel = feat.cpu().numpy(), lab.cpu().numpy(), sel.cpu().numpy()
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25)
+    Mc, Zc, R, mom = o.geometry()
+    cnt = o.cells().count
+    p = b.pos()
+    for k, (A, B) in enumerate(sel):
+        if R[B] > R[A] or (R[B] == R[A] and B < A):
+            A, B = B, A
+        r = np.linalg.norm(Zc[A] - Zc[B])
+        assert abs(feat[k, 0] - np.log10(r)) < 1e-5
+        assert abs(feat[k, 1] - np.log10(max(R[A] / r, 1e-12))) < 1e-5
+        assert abs(feat[k, 7] - np.log10(cnt[A] + cnt[B])) < 1e-5
+        # label: the worse side's rms |a_M2L - a_direct| for this pair alone,
+        # relative to the other cell's monopole field
+        a = o.pair_accel(A, B, "TC")
+        ia, ib = o.cell_bodies(A), o.cell_bodies(B)
+        dire = np.zeros_like(a)
+        for tgt, src in ((ia, ib), (ib, ia)):
+            d = p[src][None, :, :] - p[tgt][:, None, :]
+            rr = np.linalg.norm(d, axis=2)
+            dire[tgt] = np.einsum("ijk,j->ik", d / rr[:, :, None] ** 3, b.m[src])
+        def side(ii, m_other):
+            return np.sqrt(np.mean(np.sum((a[ii] - dire[ii]) ** 2, axis=1))) / (m_other / r ** 2)
+        ref = max(np.log10(max(side(ia, Mc[B]), side(ib, Mc[A])) + 1e-300), -12.0)
+        if ref < -11.0:  # rounding-level errors: both at the floor region
+            assert lab[k] < -10.5, (k, lab[k], ref)
+        else:
+            assert abs(lab[k] - ref) < 1e-4, (k, lab[k], ref)
+
+
+def _coverage_ok(s, n):
+    c = s.export_tree(geometry=False)
+    begin, count = c["begin"].cpu().numpy(), c["count"].cpu().numpy()
+    _, order = s.export_keys()
+    order = order.cpu().numpy()
+    m2l, p2p, slf = (t.cpu().numpy() for t in s.export_lists())
+    cov = np.zeros((n, n), dtype=np.int32)
+    body = lambda cid: order[begin[cid]:begin[cid] + count[cid]]
+    for A, B in np.concatenate([m2l, p2p]):
+        ia, ib = body(A), body(B)
+        cov[np.ix_(ia, ib)] += 1
+        cov[np.ix_(ib, ia)] += 1
+    for A in slf:
+        ia = body(A)
+        cov[np.ix_(ia, ia)] += 1
+    np.fill_diagonal(cov, 1)
+    return np.all(cov == 1)
+
+
+def test_selector_walk_is_mutual_conserving_and_complete():
+    b = ics.plummer(1500, seed=7)
+    s = _solver(theta=0.5, variant="TC")
+    s.selector_set(_params(2), log10_target=-2.0, enable=True)
+    x, y, z, m = _dev(b)
+    a = torch.stack(s.solve(x, y, z, m), 1).cpu().numpy()
+    assert _coverage_ok(s, b.n)
+    _, Zc, R, _ = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25).geometry()
+    m2l, _, _ = s.export_lists()
+    m2l = m2l.cpu().numpy()
+    d = np.linalg.norm(Zc[m2l[:, 0]] - Zc[m2l[:, 1]], axis=1)
+    assert np.all(d * (1 + 1e-12) >= R[m2l[:, 0]] + R[m2l[:, 1]])  # safety bound
+    fb, tb = oracle.balance(b.x, b.y, b.z, b.m, a)
+    assert fb <= 1e-13 and tb <= 1e-13
+    a2 = torch.stack(s.solve(x, y, z, m), 1).cpu().numpy()
+    assert np.array_equal(a, a2)
+
+
+def test_training_reduces_the_loss():
+    from paper_1706_06989_gb300 import selector
+    b = ics.plummer(20000, seed=8)
+    s = _solver(theta=0.5)
+    x, y, z, m = _dev(b)
+    feat, lab = selector.pair_samples(s, x, y, z, m, thetas=(0.4, 0.7, 1.0), per_theta=20000, seed=1)
+    params, losses = selector.train(s, feat, lab, steps=600, batch=2048, lr=3e-3, seed=2)
+    assert losses[-50:].mean() < 0.5 * losses[:20].mean()
+    assert np.isfinite(params).all()
+
+
+def test_selector_extremes_reduce_to_the_plain_criterion():
+    """theta is a floor: a network that accepts nothing leaves the walk of the
+    plain criterion at theta; one that accepts everything it may (the safety
+    bound) gives the walk of the criterion at theta = 1."""
+    b = ics.plummer(3000, seed=9)
+    x, y, z, m = _dev(b)
+    lists = {}
+    for th in (0.5, 1.0):
+        s = _solver(theta=th)
+        s.solve(x, y, z, m)
+        lists[th] = [t.cpu().numpy() for t in s.export_lists()]
+    p = _params(3)
+    p[M.NW - 65:M.NW - 1] = 0.0  # w4: constant output b4
+    for b4, th in ((100.0, 0.5), (-100.0, 1.0)):
+        p[M.NW - 1] = b4
+        s = _solver(theta=0.5)
+        s.selector_set(p, log10_target=-3.0, enable=True)
+        s.solve(x, y, z, m)
+        got = [t.cpu().numpy() for t in s.export_lists()]
+        for g, r in zip(got, lists[th]):
+            assert np.array_equal(g, r), (b4, th)
