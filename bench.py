@@ -61,8 +61,10 @@ def _args():
                    help="leapfrog: two-Plummer binary, uniform KDK steps, momentum drift per step")
     p.add_argument("--lf-steps", type=int, default=200)
     p.add_argument("--sel-steps", type=int, default=3000)
-    p.add_argument("--sel-floor", type=float, default=0.35,
-                   help="theta of the plain criterion kept under the learned selector")
+    p.add_argument("--sel-floor", type=float, default=0.4,
+                   help="theta of the plain criterion kept under the learned selector (band floor)")
+    p.add_argument("--sel-theta-max", type=float, default=0.7,
+                   help="upper edge of the band the learned selector decides")
     p.add_argument("--lf-variants", default="TC:mixed,UC:mixed,TC:fp64")
     return p.parse_args()
 
@@ -486,22 +488,37 @@ def _time_solves(solver, x, y, z, m, out, flush, reps=3):
     return statistics.median(ts)
 
 
+def _interp_time_at_error(curve, err):
+    """Time of the fixed-theta form at a given rms error, interpolated
+    linearly in (log error, log time) between neighbouring thetas."""
+    pts = sorted((c["rms_err"], c["ms"]) for c in curve)
+    for (e0, t0), (e1, t1) in zip(pts, pts[1:]):
+        if e0 <= err <= e1 and e1 > e0:
+            u = (np.log(err) - np.log(e0)) / (np.log(e1) - np.log(e0))
+            return float(np.exp(np.log(t0) + u * (np.log(t1) - np.log(t0))))
+    return None
+
+
 def run_selector(a):
-    """Learned pair selector: trained on pairs of the Plummer N = 2,000 and
-    N = 1,048,576 spheres accepted at theta = 0.3 .. 1.0 (labels: the method's
-    own M2L errors), applied to a Plummer sphere and to a Hernquist halo +
-    exponential disc, both N = 4,194,304, against the fixed theta = 0.5
-    criterion (FP64 and the mixed form) at matched rms force error (4,096
-    bodies against exact direct sums)."""
+    """Learned pair selector.  Trained on pairs of the Plummer N = 2,000 and
+    N = 1,048,576 spheres accepted by the plain walk at theta in the band and
+    around it (labels: the method's own M2L errors against direct sums).
+    Applied, with theta_lo as the floor and theta_hi as the ceiling of the band
+    the network decides, to a Plummer sphere and to a Hernquist halo +
+    exponential disc, both N = 4,194,304.  The fixed-theta form is swept over
+    theta to give its time-error curve; the selector is compared with it at
+    equal rms force error (4,096 bodies against exact direct sums)."""
     import torch
     from paper_1706_06989_gb300 import fmm, ics, selector
     dev = torch.device("cuda", 0)
+    lo, hi = a.sel_floor, a.sel_theta_max
     t0 = time.perf_counter()
     s = fmm.FMM(theta=0.5, n_crit=25, variant="TC", precision="fp64")
+    thetas = tuple(float(t) for t in np.round(np.linspace(lo, min(1.0, hi + 0.1), 5), 3))
     feats, labs = [], []
-    for b, per in ((ics.plummer(2000, seed=0), 200_000), (ics.plummer(1 << 20, seed=0), 2_500_000)):
+    for b, per in ((ics.plummer(2000, seed=0), 200_000), (ics.plummer(1 << 20, seed=0), 2_000_000)):
         x, y, z, m = (torch.from_numpy(v).to(dev) for v in (b.x, b.y, b.z, b.m))
-        f, l = selector.pair_samples(s, x, y, z, m, thetas=(0.3, 0.5, 0.7, 1.0), per_theta=per, seed=3)
+        f, l = selector.pair_samples(s, x, y, z, m, thetas=thetas, per_theta=per, seed=3)
         feats.append(f)
         labs.append(l)
     X, Y = torch.cat(feats), torch.cat(labs)
@@ -518,42 +535,46 @@ def run_selector(a):
         ev = fmm.FMM(theta=0.5, n_crit=25, variant="TC", precision=a.precision)
         out = tuple(torch.empty(b.n, dtype=torch.float64, device=dev) for _ in range(3))
         ref = torch.stack(ev.direct(x, y, z, m, tgd), 1)
-        res = {}
-        for prec in ("fp64", a.precision):
-            ev.set_opts(theta=0.5, precision=prec)
-            ev.selector_set(None, 0.0, enable=False)
+
+        def measure(theta, prec, tgt=None):
+            ev.set_opts(theta=theta, precision=prec)
+            if tgt is None:
+                ev.selector_set(None, 0.0, enable=False)
+            else:
+                ev.selector_set(params, float(tgt), enable=True, theta_max=hi)
             ev.solve(x, y, z, m, out)
             st = ev.stats()
-            res[f"theta0.5_{prec}"] = {"ms": _time_solves(ev, x, y, z, m, out, flush),
-                                       "rms_err": _rms_err(ev, x, y, z, m, out, tgd, ref),
-                                       "n_m2l": st.n_m2l, "p2p_body_pairs": st.p2p_body_pairs}
-        base = res[f"theta0.5_{a.precision}"]["rms_err"]
-        # theta is the floor of the accepted set; the network adds pairs
-        ev.set_opts(theta=a.sel_floor, precision=a.precision)
+            return {"ms": _time_solves(ev, x, y, z, m, out, flush), "rms_err": _rms_err(ev, x, y, z, m, out, tgd, ref),
+                    "n_m2l": st.n_m2l, "p2p_body_pairs": st.p2p_body_pairs}
+
+        fp64 = measure(0.5, "fp64")
+        curve = []
+        for th in np.round(np.arange(0.35, 0.751, 0.05), 3):
+            r = measure(float(th), a.precision)
+            r["theta"] = float(th)
+            curve.append(r)
+        base = next(c for c in curve if abs(c["theta"] - 0.5) < 1e-9)
         scan, best = [], None
-        for tgt in np.arange(-4.0, -1.49, 0.25):
-            ev.selector_set(params, float(tgt), enable=True)
-            ev.solve(x, y, z, m, out)
-            st = ev.stats()
-            e = _rms_err(ev, x, y, z, m, out, tgd, ref)
-            row = {"log10_target": float(tgt), "rms_err": e, "n_m2l": st.n_m2l,
-                   "p2p_body_pairs": st.p2p_body_pairs}
-            if e <= base:
-                row["ms"] = _time_solves(ev, x, y, z, m, out, flush)
-                if best is None or row["ms"] < best["ms"]:
-                    best = row
-            scan.append(row)
+        for tgt in np.arange(-3.5, -0.99, 0.25):
+            r = measure(lo, a.precision, tgt)
+            r["log10_target"] = float(tgt)
+            r["theta_curve_ms_at_same_error"] = _interp_time_at_error(curve, r["rms_err"])
+            if r["theta_curve_ms_at_same_error"]:
+                r["gain_vs_theta_curve"] = r["theta_curve_ms_at_same_error"] / r["ms"]
+            if r["rms_err"] <= base["rms_err"] and (best is None or r["ms"] < best["ms"]):
+                best = r
+            scan.append(r)
         ev.selector_set(None, 0.0, enable=False)
-        fp64_ms = res["theta0.5_fp64"]["ms"]
-        evals.append({"workload": wname, "fixed_theta": res, "selector_theta_floor": a.sel_floor,
-                      "selector_scan": scan, "selector_best_at_matched_error": best,
-                      "speedup_vs_fixed_theta_same_precision":
-                          (res[f"theta0.5_{a.precision}"]["ms"] / best["ms"]) if best else None,
-                      "speedup_vs_plain_fp64": (fp64_ms / best["ms"]) if best else None})
+        evals.append({"workload": wname, "fp64_theta0.5": fp64, "theta_curve": curve,
+                      "selector_band": [lo, hi], "selector_scan": scan,
+                      "selector_best_at_error_of_theta0.5": best,
+                      "speedup_vs_theta0.5_same_precision": (base["ms"] / best["ms"]) if best else None,
+                      "speedup_vs_plain_fp64_theta0.5": (fp64["ms"] / best["ms"]) if best else None})
         ev.close()
         del x, y, z, m, out, ref
         torch.cuda.empty_cache()
     print(json.dumps({"experiment": "selector", "train": {"samples": int(X.shape[0]), "steps": a.sel_steps,
+                                                          "thetas": thetas,
                                                           "loss_first": float(losses[:20].mean()),
                                                           "loss_last": float(losses[-50:].mean()),
                                                           "s_data": t_data, "s_train": t_train},

@@ -184,19 +184,21 @@ int fmm_leapfrog(fmm_ctx *ctx, double *x, double *y, double *z, double *vx, doub
  * of the pair's normalised M2L error; it runs in BF16 on the tensor cores
  * with FP32 accumulation.  Parameters: fmm_selector_nparams() floats (FP32):
  * W1[64][8], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], w4[64], b4,
- * feature mean[8], feature scale[8].  Features of a pair (ordered by R_max,
+ * feature mean[8], feature scale[8].  Features of a pair (ordered by R_max in FP32,
  * then id): log10 of |r|, R_A/|r|, R_B/|r|, M_A, M_B, |Q_A - tr/3|/(M_A R_A^2),
  * the same for B, and N_A + N_B; normalised as (f - mean) * scale. */
 int fmm_selector_nparams(void);
 
 /* Enables (enable = 1) or disables the selector for the following solves.
- * params: HOST, fmm_selector_nparams() floats.  With it, a pair is accepted
- * when the opening criterion at the context's theta accepts it, or when it
- * passes |Z_A - Z_B| >= R_A + R_B (the criterion at theta = 1) and the
- * prediction is below log10_target; others are opened as usual.  theta thus
- * becomes a floor: the network only adds pairs, so the work of a solve never
- * exceeds that of the plain criterion at the same theta. */
-int fmm_selector_set(fmm_ctx *ctx, const float *params, double log10_target, int enable);
+ * params: HOST, fmm_selector_nparams() floats.  With it, the opening
+ * criterion at the context's theta still accepts what it accepts; a pair it
+ * rejects but that the criterion at theta_max (theta < theta_max <= 1;
+ * theta_max = 1 is the safety bound |Z_A - Z_B| >= R_A + R_B) accepts is
+ * accepted when the prediction is below log10_target.  Every other pair is
+ * opened as usual.  The network only adds pairs, so the interaction lists
+ * never grow beyond those of the plain criterion at theta.  FMM_EINVAL if
+ * theta_max is outside (0, 1]. */
+int fmm_selector_set(fmm_ctx *ctx, const float *params, double log10_target, double theta_max, int enable);
 
 /* Training samples for K given cell pairs of the current tree (after
  * fmm_upward, order 3): pairs: device, K x 2 int32; feat: device, K x 8 raw

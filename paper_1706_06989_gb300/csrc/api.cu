@@ -152,11 +152,11 @@ void fmm_destroy(fmm_ctx *c) {
                  &c->cur, &c->flag, &c->incl, &c->lcp, &c->leaf_of, &c->cell_at, &c->near, &c->acc,
                  &c->status, &c->bbox_part, &c->bbox, &c->sys_off, &c->sysid, &c->sbox, &c->begin, &c->count, &c->level, &c->parent,
                  &c->first_child, &c->nchild, &c->S, &c->M, &c->Z, &c->invM, &c->Rmax, &c->rmax2, &c->mom,
-                 &c->loc, &c->leaves, &c->front[0], &c->front[1], &c->action, &c->wcount, &c->woff,
-                 &c->m2l, &c->p2p, &c->self_list, &c->walk_zr, &c->walk_nl, &c->ekey[0], &c->ekey[1], &c->eval[0], &c->eval[1],
+                 &c->loc, &c->leaves, &c->front[0], &c->front[1],
+                 &c->m2l, &c->p2p, &c->self_list, &c->walk_zr, &c->walk_zf, &c->walk_nl, &c->walk_state, &c->walk_lb, &c->ekey[0], &c->ekey[1], &c->eval[0], &c->eval[1],
                  &c->m2l_pos, &c->m2l_off, &c->m2l_slots, &c->cell32, &c->pkey[0], &c->pkey[1], &c->pval[0],
                  &c->pval[1], &c->p2p_A, &c->p2p_offA, &c->p2p_offB, &c->p2p_pos, &c->p2p_poff,
-                 &c->p2p_len, &c->p2p_slots, &c->p2p_colOff, &c->p2p_cols, &c->p2p_nb, &c->p2p_pre, &c->scan_tmp, &c->sort_hist, &c->totals, &c->diag, &c->sel_params, &c->sel_scratch, &c->sel_part, &c->sel_score, &c->sel_grad, &c->sel_perm, &c->sel_xb, &c->sel_yb, &c->hx, &c->hy,
+                 &c->p2p_len, &c->p2p_slots, &c->p2p_colOff, &c->p2p_cols, &c->p2p_nb, &c->p2p_pre, &c->p2p_bodyf, &c->scan_tmp, &c->sort_hist, &c->totals, &c->diag, &c->sel_params, &c->sel_cellfeat, &c->sel_scratch, &c->sel_part, &c->sel_score, &c->sel_grad, &c->sel_perm, &c->sel_xb, &c->sel_yb, &c->hx, &c->hy,
                  &c->hz, &c->hm, &c->hax, &c->hay, &c->haz};
   for (DBuf *b : all) free_buf(*b);
   for (int k = 0; k < kNumTimers; ++k)

@@ -78,20 +78,22 @@ struct fmm_ctx {
   amfmm::DBuf begin, count, level, parent, first_child, nchild, S, M, Z, invM, Rmax,
       rmax2, mom, loc, leaves;
   // walk
-  amfmm::DBuf front[2], action, wcount, woff, m2l, p2p, self_list, walk_zr, walk_nl;
+  amfmm::DBuf front[2], m2l, p2p, self_list, walk_zr, walk_zf, walk_nl, walk_state, walk_lb;
+  unsigned walk_ticket = 0, walk_epoch = 0;  // single-pass walk generations
   // M2L scatter
   amfmm::DBuf ekey[2], eval[2], m2l_pos, m2l_off, m2l_slots, cell32;
   // P2P grouping
   amfmm::DBuf pkey[2], pval[2], p2p_A, p2p_offA, p2p_offB, p2p_pos, p2p_poff, p2p_len,
-      p2p_slots, p2p_colOff, p2p_cols, p2p_nb, p2p_pre;
+      p2p_slots, p2p_colOff, p2p_cols, p2p_nb, p2p_pre, p2p_bodyf;
   // scan / sort scratch; `totals` holds small device results (1 KiB):
   // [0,16) scan totals, [64,72) near-field body-pair count, [96,104) slot total,
   // [128,132) near-field column total
   amfmm::DBuf scan_tmp, sort_hist, totals, diag;
   // learned pair selector
-  amfmm::DBuf sel_params, sel_scratch, sel_part, sel_score, sel_grad, sel_perm, sel_xb, sel_yb;
+  amfmm::DBuf sel_params, sel_cellfeat, sel_scratch, sel_part, sel_score, sel_grad, sel_perm, sel_xb, sel_yb;
   bool sel_enabled = false;
   double sel_log10_target = -3.0;
+  double sel_theta_max = 1.0;  // upper edge of the band the network decides
   // host-solve staging
   amfmm::DBuf hx, hy, hz, hm, hax, hay, haz;
 };
@@ -155,6 +157,7 @@ int radix_sort_u32(fmm_ctx *c, DBuf key[2], DBuf val[2], int64_t n, int bits, in
 int build_tree(fmm_ctx *c);         // tree.cu
 int upward(fmm_ctx *c);             // tree.cu
 int walk(fmm_ctx *c);               // walk.cu
+int pack_walk_cells(fmm_ctx *c);    // walk.cu: per-cell records of the criterion
 int m2l_prepare(fmm_ctx *c);        // m2l.cu: slot positions (sort by cell)
 int m2l_run(fmm_ctx *c);            // m2l.cu: mutual M2L into slots
 int m2l_reduce(fmm_ctx *c);         // m2l.cu: per-cell fixed-order sums
@@ -175,6 +178,7 @@ int reduce_general(fmm_ctx *c);
 int downward_general(fmm_ctx *c);
 
 // learned selector (selector.cu, m2l.cu)
+int cell_features(fmm_ctx *c);  // per-cell parts of the selector's features
 int walk_scores(fmm_ctx *c, int64_t nf, const int2 *front, float *score);
 int pair_locals_tc(fmm_ctx *c, const int2 *pairs, int64_t K, double *out);
 

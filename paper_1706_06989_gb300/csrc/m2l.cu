@@ -280,15 +280,29 @@ __device__ __forceinline__ void m2l_one(const T r[3], T MT, T iMT, T MS, const T
 
 // Mixed form, gathered: one warp per cell T, its lanes over T's partners in
 // the stably sorted order of the list.  Every lane keeps compensated FP32
-// sums (Kahan) of the partners it visits; the 32 lane sums are then added in
-// FP64 over a fixed butterfly.  Each cell's local is written whole (zero for
-// a cell without partners).
+// sums (Kahan) of the partners it visits.  The 32 lane sums of a coefficient
+// are then combined by one lane, in lane order, with error-free FP32
+// additions (TwoSum), and widened to FP64 once: the FP64 pipe, 1/64 of the
+// FP32 rate on this GPU, sees three operations per coefficient and cell.
+// Each cell's local is written whole (zero for a cell without partners).
+constexpr int kGatherWarps = 8;
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
 template <int VARIANT>
-__global__ void __launch_bounds__(256) k_m2l32_gather(int32_t ncell, const int32_t *__restrict__ off,
-                                                       const uint32_t *__restrict__ partner,
-                                                       const float *__restrict__ cell32,
-                                                       double *__restrict__ loc) {
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__global__ void __launch_bounds__(kGatherWarps * 32) k_m2l32_gather(int32_t ncell, const int32_t *__restrict__ off,
+                                                                    const uint32_t *__restrict__ partner,
+                                                                    const float *__restrict__ cell32,
+                                                                    double *__restrict__ loc) {
+  // per warp, per coefficient, per lane: the lane's sum and (negated) error
+  __shared__ float sh[kGatherWarps][19][33];
+  __shared__ float sl[kGatherWarps][19][33];
+  const int w = threadIdx.x >> 5;
+  const int c = blockIdx.x * kGatherWarps + w;
   const int lane = threadIdx.x & 31;
   if (c >= ncell) return;
   const float *t = cell32 + static_cast<int64_t>(c) * kCell32;
@@ -320,19 +334,24 @@ __global__ void __launch_bounds__(256) k_m2l32_gather(int32_t ncell, const int32
       sum[q] = tq;
     }
   }
-  double acc[19];
 #pragma unroll
-  for (int q = 0; q < 19; ++q) acc[q] = static_cast<double>(sum[q]) - static_cast<double>(cmp[q]);
-#pragma unroll
-  for (int h = 1; h < 32; h <<= 1)
-#pragma unroll
-    for (int q = 0; q < 19; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], h);
-  // every lane holds the same sums; lane q stores coefficient q
-  double mine = 0.0;
-#pragma unroll
-  for (int q = 0; q < 19; ++q)
-    if (lane == q) mine = acc[q];
-  if (lane < kLocStride) loc[static_cast<int64_t>(c) * kLocStride + lane] = mine;
+  for (int q = 0; q < 19; ++q) {
+    sh[w][q][lane] = sum[q];
+    sl[w][q][lane] = -cmp[q];
+  }
+  __syncwarp();
+  if (lane < 19) {
+    float hi = sh[w][lane][0], lo = sl[w][lane][0];
+    for (int j = 1; j < 32; ++j) {
+      float s2, e2;
+      two_sum(hi, sh[w][lane][j], s2, e2);
+      hi = s2;
+      lo += e2 + sl[w][lane][j];
+    }
+    loc[static_cast<int64_t>(c) * kLocStride + lane] = static_cast<double>(hi) + static_cast<double>(lo);
+  } else if (lane == 19) {
+    loc[static_cast<int64_t>(c) * kLocStride + 19] = 0.0;
+  }
 }
 
 // FP32 copy of the cell data for the mixed form
@@ -475,16 +494,16 @@ int launch_m2l64(fmm_ctx *c, int64_t K) {
 
 int launch_m2l32_gather(fmm_ctx *c) {
   const int32_t nc = static_cast<int32_t>(c->sz.ncell);
-  const unsigned g = grid_for(static_cast<int64_t>(nc) * 32, 256);
+  const unsigned g = grid_for(static_cast<int64_t>(nc) * 32, kGatherWarps * 32);
   const int32_t *off = ptr<int32_t>(c->m2l_off);
   const uint32_t *partner = ptr<uint32_t>(c->eval[c->m2l_which]);
   const float *c32 = ptr<float>(c->cell32);
   double *loc = ptr<double>(c->loc);
   cudaStream_t st = c->stream;
   switch (c->opts.variant) {
-    case FMM_UC: k_m2l32_gather<FMM_UC><<<g, 256, 0, st>>>(nc, off, partner, c32, loc); break;
-    case FMM_TC: k_m2l32_gather<FMM_TC><<<g, 256, 0, st>>>(nc, off, partner, c32, loc); break;
-    default: k_m2l32_gather<FMM_TCO><<<g, 256, 0, st>>>(nc, off, partner, c32, loc); break;
+    case FMM_UC: k_m2l32_gather<FMM_UC><<<g, kGatherWarps * 32, 0, st>>>(nc, off, partner, c32, loc); break;
+    case FMM_TC: k_m2l32_gather<FMM_TC><<<g, kGatherWarps * 32, 0, st>>>(nc, off, partner, c32, loc); break;
+    default: k_m2l32_gather<FMM_TCO><<<g, kGatherWarps * 32, 0, st>>>(nc, off, partner, c32, loc); break;
   }
   return launched(c, "m2l");
 }

@@ -60,13 +60,38 @@ __device__ __forceinline__ double coord<double>(double v, double) { return v; }
 template <>
 __device__ __forceinline__ float coord<float>(double v, double z) { return static_cast<float>(v - z); }
 
+// Mixed form: bodies and the leaf centre as hi + lo floats, so an offset
+// (x_hi - z_hi) + (x_lo - z_lo) is formed with FP32 operations only (FP64
+// costs 64 FP32 operations on this GPU) and keeps FP32 relative accuracy.
+struct BodyF {
+  float4 h;  // x, y, z hi; mass
+  float4 l;  // x, y, z lo
+};
+
+__global__ void k_body32(int64_t n, const double *__restrict__ X, const double *__restrict__ Y,
+                         const double *__restrict__ Zb, const double *__restrict__ Mb, BodyF *__restrict__ out) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const double x = X[i], y = Y[i], z = Zb[i];
+  const float hx = static_cast<float>(x), hy = static_cast<float>(y), hz = static_cast<float>(z);
+  BodyF b;
+  b.h = make_float4(hx, hy, hz, static_cast<float>(Mb[i]));
+  b.l = make_float4(static_cast<float>(x - hx), static_cast<float>(y - hy), static_cast<float>(z - hz), 0.f);
+  out[i] = b;
+}
+
+__device__ __forceinline__ float3 offset32(const BodyF &b, const float4 zh, const float4 zl) {
+  return make_float3((b.h.x - zh.x) + (b.l.x - zl.x), (b.h.y - zh.y) + (b.l.y - zl.y),
+                     (b.h.z - zh.z) + (b.l.z - zl.z));
+}
+
 template <class T>
 __global__ void __launch_bounds__(kWarps * 32) k_p2p(
     int32_t nleaf, int64_t n, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin,
     const int32_t *__restrict__ count, const double *__restrict__ Zc, const double *__restrict__ X,
     const double *__restrict__ Y, const double *__restrict__ Zb, const double *__restrict__ Mb,
     const int32_t *__restrict__ colOff, const int2 *__restrict__ cols, double *__restrict__ near,
-    T *__restrict__ slots) {
+    T *__restrict__ slots, const BodyF *__restrict__ bodyf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   P2PSmem<T> &sm = reinterpret_cast<P2PSmem<T> *>(smem_raw)[w];
@@ -75,6 +100,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
   const int L = leaves[q];
   const int bA = begin[L], nA = count[L];
   const double zx = Zc[3 * L], zy = Zc[3 * L + 1], zz = Zc[3 * L + 2];
+  float4 zh = make_float4(0.f, 0.f, 0.f, 0.f), zl = zh;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    zh = make_float4(static_cast<float>(zx), static_cast<float>(zy), static_cast<float>(zz), 0.f);
+    zl = make_float4(static_cast<float>(zx - zh.x), static_cast<float>(zy - zh.y), static_cast<float>(zz - zh.z), 0.f);
+  }
   const int cb = colOff[L], ce = colOff[L + 1];
   for (int t = l; t < nA; t += 32) {
     near[bA + t] = 0.0;
@@ -86,10 +116,19 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
     const int nr = min(kRows, nA - r0);
     if (l < nr) {
       const int i = bA + r0 + l;
-      sm.row[l][0] = coord<T>(X[i], zx);
-      sm.row[l][1] = coord<T>(Y[i], zy);
-      sm.row[l][2] = coord<T>(Zb[i], zz);
-      sm.row[l][3] = T(Mb[i]);
+      if constexpr (sizeof(T) == sizeof(float)) {
+        const BodyF b = bodyf[i];
+        const float3 o = offset32(b, zh, zl);
+        sm.row[l][0] = o.x;
+        sm.row[l][1] = o.y;
+        sm.row[l][2] = o.z;
+        sm.row[l][3] = b.h.w;
+      } else {
+        sm.row[l][0] = coord<T>(X[i], zx);
+        sm.row[l][1] = coord<T>(Y[i], zy);
+        sm.row[l][2] = coord<T>(Zb[i], zz);
+        sm.row[l][3] = T(Mb[i]);
+      }
     }
     for (int v = 0; v < 3 * nr; ++v) sm.acc[v][l] = T(0);
     __syncwarp();
@@ -102,10 +141,19 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
       T xj = T(0), yj = T(0), zj = T(0), mj = T(0);
       if (valid) {
         col = cols[c];
-        xj = coord<T>(X[col.x], zx);
-        yj = coord<T>(Y[col.x], zy);
-        zj = coord<T>(Zb[col.x], zz);
-        mj = T(Mb[col.x]);
+        if constexpr (sizeof(T) == sizeof(float)) {
+          const BodyF b = bodyf[col.x];
+          const float3 o = offset32(b, zh, zl);
+          xj = o.x;
+          yj = o.y;
+          zj = o.z;
+          mj = b.h.w;
+        } else {
+          xj = coord<T>(X[col.x], zx);
+          yj = coord<T>(Y[col.x], zy);
+          zj = coord<T>(Zb[col.x], zz);
+          mj = T(Mb[col.x]);
+        }
       }
       const bool mutual = col.y >= 0;
       T bx = T(0), by = T(0), bz = T(0);
@@ -176,16 +224,18 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
     }
     __syncwarp();
     // A-side: every row's partials summed over the lanes in a fixed order
-    // (FP64: sequential; mixed: pairwise in FP32 over groups of eight lanes,
-    // the four group sums in FP64)
+    // (FP64: sequential; mixed: pairwise in FP32 over the 32 lanes, then one
+    // FP64 addition)
     for (int v = l; v < 3 * nr; v += 32) {
       double s = 0.0;
-      if (sizeof(T) == sizeof(float)) {
+      if constexpr (sizeof(T) == sizeof(float)) {
+        float g[4];
 #pragma unroll
-        for (int g0 = 0; g0 < 32; g0 += 8) {
-          const T *a = &sm.acc[v][g0];
-          s += static_cast<double>(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
+        for (int h = 0; h < 4; ++h) {
+          const T *a = &sm.acc[v][8 * h];
+          g[h] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
         }
+        s = static_cast<double>((g[0] + g[1]) + (g[2] + g[3]));
       } else {
 #pragma unroll 8
         for (int t = 0; t < 32; ++t) s += static_cast<double>(sm.acc[v][t]);
@@ -341,7 +391,7 @@ int launch_p2p(fmm_ctx *c) {
       nleaf, n, ptr<int32_t>(c->leaves), ptr<int32_t>(c->begin), ptr<int32_t>(c->count),
       ptr<double>(c->Z), ptr<double>(c->X), ptr<double>(c->Y), ptr<double>(c->Zb), ptr<double>(c->Mb),
       ptr<int32_t>(c->p2p_colOff), ptr<int2>(c->p2p_cols), ptr<double>(c->near),
-      static_cast<T *>(c->p2p_slots.p));
+      static_cast<T *>(c->p2p_slots.p), sizeof(T) == sizeof(float) ? ptr<BodyF>(c->p2p_bodyf) : nullptr);
   return launched(c, "p2p");
 }
 
@@ -375,6 +425,12 @@ int p2p_prepare(fmm_ctx *c) {
   unsigned long long *stat = ptr<unsigned long long>(c->totals) + 8;
   int32_t *ctot = ptr<int32_t>(c->totals) + 32;
   AMFMM_CUDA(c, cudaMemsetAsync(stat, 0, sizeof(unsigned long long), st));
+  if (fp32) {
+    AMFMM_TRY(ensure<BodyF>(c, c->p2p_bodyf, n));
+    k_body32<<<grid_for(n, 256), 256, 0, st>>>(n, ptr<double>(c->X), ptr<double>(c->Y), ptr<double>(c->Zb),
+                                               ptr<double>(c->Mb), ptr<BodyF>(c->p2p_bodyf));
+    AMFMM_TRY(launched(c, "p2p_body32"));
+  }
   int64_t *h = static_cast<int64_t *>(c->hpin);
   h[0] = 0;
   if (K > 0) {

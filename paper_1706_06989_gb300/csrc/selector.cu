@@ -4,10 +4,11 @@
 // selections driven by an error estimate (Dehnen 2014): every accepted pair
 // still interacts mutually, so force and torque stay balanced.  Here the
 // estimate is a small network: 8 pair features -> 3 x 64 SiLU -> 1, the
-// predicted log10 of the pair's normalised M2L error.  In the walk a pair that
-// passes the safety bound |Z_A - Z_B| >= R_A,max + R_B,max (the criterion at
-// theta = 1) is accepted when the prediction is below a target; without the
-// network the opening criterion decides as before.
+// predicted log10 of the pair's normalised M2L error.  In the walk the
+// opening criterion at theta keeps deciding, except in a band: a pair that the
+// criterion rejects at theta but accepts at theta_max <= 1 (theta_max = 1 is
+// the safety bound |Z_A - Z_B| >= R_A,max + R_B,max) is accepted when the
+// prediction is below a target.
 //
 // Network arithmetic: BF16 inputs and weights on the tensor cores
 // (mma.sync m16n8k16, FP32 accumulation); biases, SiLU and the output layer in
@@ -25,6 +26,7 @@
 #include <random>
 #include <vector>
 
+#include "geom.cuh"
 #include "internal.cuh"
 
 namespace amfmm {
@@ -41,50 +43,63 @@ namespace {
 // ---------------------------------------------------------------------------
 // features and labels
 // ---------------------------------------------------------------------------
-// Order the pair by R_max (descending), then by id, so the features (and the
-// decision) are the same for (A, B) and (B, A).
-__device__ __forceinline__ void order_pair(int &A, int &B, const double *__restrict__ Rmax) {
-  const double ra = Rmax[A], rb = Rmax[B];
-  if (rb > ra || (rb == ra && B < A)) {
-    const int t = A;
-    A = B;
-    B = t;
-  }
-}
+// Per-cell parts of the features, once per tree: log10 R_max, log10 M,
+// log10 of the trace-free quadrupole norm |Q - tr(Q)/3 I| / (M R_max^2), and
+// the body count.  The squared norm is formed in FP64 (the trace removal
+// cancels); everything per pair is FP32 (FP64 costs 64 FP32 operations on
+// this GPU, and the features only need BF16 accuracy).
+__device__ __forceinline__ float lg(float v) { return __log2f(v) * 0.30102999566f; }
 
-// trace-free quadrupole norm |Q - tr(Q)/3 I| / (M R_max^2)
-__device__ __forceinline__ float qnorm(const double *q, double M, double R) {
+__global__ void k_cell_features(int32_t ncell, const double *__restrict__ Rmax, const double *__restrict__ M,
+                                const double *__restrict__ mom, int mstride, const int32_t *__restrict__ count,
+                                float4 *__restrict__ cf) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const double *q = mom + static_cast<int64_t>(c) * mstride + 4;
   const double tr = (q[0] + q[3] + q[5]) / 3.0;
   const double a = q[0] - tr, d = q[3] - tr, f = q[5] - tr;
   const double n2 = a * a + d * d + f * f + 2.0 * (q[1] * q[1] + q[2] * q[2] + q[4] * q[4]);
-  return static_cast<float>(sqrt(n2) / (M * R * R + 1e-300));
+  const float R = static_cast<float>(Rmax[c]), m = static_cast<float>(M[c]);
+  const float qn = sqrtf(static_cast<float>(n2)) / (m * R * R + 1e-30f);
+  cf[c] = make_float4(lg(R), lg(m), lg(qn + 1e-12f), static_cast<float>(count[c]));
 }
 
-// raw features: log10 of |r|, R_A/|r|, R_B/|r|, M_A, M_B, q_A, q_B, N_A + N_B
-__device__ void pair_features(int A, int B, const double *__restrict__ Z, const double *__restrict__ Rmax,
-                              const double *__restrict__ M, const double *__restrict__ mom, int mstride,
-                              const int32_t *__restrict__ count, float f[kF]) {
-  order_pair(A, B, Rmax);
-  const double dx = Z[3 * A] - Z[3 * B], dy = Z[3 * A + 1] - Z[3 * B + 1], dz = Z[3 * A + 2] - Z[3 * B + 2];
-  const double r = sqrt(dx * dx + dy * dy + dz * dz) + 1e-300;
-  f[0] = static_cast<float>(log10(r));
-  f[1] = static_cast<float>(log10(fmax(Rmax[A] / r, 1e-12)));
-  f[2] = static_cast<float>(log10(fmax(Rmax[B] / r, 1e-12)));
-  f[3] = static_cast<float>(log10(M[A]));
-  f[4] = static_cast<float>(log10(M[B]));
-  f[5] = log10f(qnorm(mom + static_cast<int64_t>(A) * mstride + 4, M[A], Rmax[A]) + 1e-12f);
-  f[6] = log10f(qnorm(mom + static_cast<int64_t>(B) * mstride + 4, M[B], Rmax[B]) + 1e-12f);
-  f[7] = log10f(static_cast<float>(count[A] + count[B]));
+// raw features of a pair: log10 of |r|, R_A/|r|, R_B/|r|, M_A, M_B, q_A, q_B,
+// N_A + N_B, with the pair ordered by R_max (FP32, descending), then by id,
+// so that (A, B) and (B, A) give the same features and decision.  |r| comes
+// from the hi + lo float centres.
+__device__ __forceinline__ void pair_features(int A, int B, const CellF *__restrict__ zf,
+                                              const float4 *__restrict__ cf, float f[kF]) {
+  CellF a = zf[A], b = zf[B];
+  if (b.h.w > a.h.w || (b.h.w == a.h.w && B < A)) {
+    const int t = A;
+    A = B;
+    B = t;
+    const CellF u = a;
+    a = b;
+    b = u;
+  }
+  const float4 fa = cf[A], fb = cf[B];
+  const float dx = (a.h.x - b.h.x) + (a.l.x - b.l.x);
+  const float dy = (a.h.y - b.h.y) + (a.l.y - b.l.y);
+  const float dz = (a.h.z - b.h.z) + (a.l.z - b.l.z);
+  const float lr = 0.5f * lg(dx * dx + dy * dy + dz * dz + 1e-37f);
+  f[0] = lr;
+  f[1] = fmaxf(fa.x - lr, -12.f);
+  f[2] = fmaxf(fb.x - lr, -12.f);
+  f[3] = fa.y;
+  f[4] = fb.y;
+  f[5] = fa.z;
+  f[6] = fb.z;
+  f[7] = lg(fa.w + fb.w);
 }
 
-__global__ void k_features(int64_t K, const int2 *__restrict__ pairs, const double *__restrict__ Z,
-                           const double *__restrict__ Rmax, const double *__restrict__ M,
-                           const double *__restrict__ mom, int mstride, const int32_t *__restrict__ count,
-                           float *__restrict__ feat) {
+__global__ void k_features(int64_t K, const int2 *__restrict__ pairs, const CellF *__restrict__ zf,
+                           const float4 *__restrict__ cf, float *__restrict__ feat) {
   const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (k >= K) return;
   float f[kF];
-  pair_features(pairs[k].x, pairs[k].y, Z, Rmax, M, mom, mstride, count, f);
+  pair_features(pairs[k].x, pairs[k].y, zf, cf, f);
 #pragma unroll
   for (int q = 0; q < kF; ++q) feat[k * kF + q] = f[q];
 }
@@ -186,9 +201,17 @@ __device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], uint32
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float silu(float z) { return z / (1.f + expf(-z)); }
+// SiLU z sigmoid(z) with sigmoid(z) = (1 + tanh(z/2))/2 on the hardware tanh
+// (one special-function operation per activation)
+__device__ __forceinline__ float tanh_hw(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sigm(float z) { return fmaf(0.5f, tanh_hw(0.5f * z), 0.5f); }
+__device__ __forceinline__ float silu(float z) { return z * sigm(z); }
 __device__ __forceinline__ float silu_grad(float z) {
-  const float s = 1.f / (1.f + expf(-z));
+  const float s = sigm(z);
   return s * (1.f + z * (1.f - s));
 }
 
@@ -515,46 +538,68 @@ __global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__re
 // ---------------------------------------------------------------------------
 // scoring of the walk's candidate pairs
 // ---------------------------------------------------------------------------
-// score[t] = predicted log10 normalised error for frontier pairs that pass the
-// safety bound (A != B, |Z_A - Z_B| >= R_A + R_B); +inf otherwise.
+// score[t] = predicted log10 normalised error for the frontier pairs in the
+// band the network decides: A != B, not accepted by the criterion at the
+// floor theta_lo, and accepted by it at theta_hi <= 1 (theta_hi = 1 is the
+// safety bound |Z_A - Z_B| >= R_A + R_B); +inf for every other pair.  The
+// criteria are the walk's own exactly rounded FP64 expressions.  Persistent
+// blocks: the network is staged in shared memory once per block, then each
+// warp scores groups of 16 pairs, skipping the network for groups without a
+// pair in the band.
 __global__ void __launch_bounds__(128) k_walk_scores(int64_t nf, const int2 *__restrict__ front,
-                                                     const float *__restrict__ params, const double *__restrict__ Z,
-                                                     const double *__restrict__ Rmax, const double *__restrict__ M,
-                                                     const double *__restrict__ mom, int mstride,
-                                                     const int32_t *__restrict__ count, float *__restrict__ score) {
+                                                     const float *__restrict__ params,
+                                                     const double4_32a *__restrict__ zr, const CellF *__restrict__ zf,
+                                                     const float4 *__restrict__ cf, double th_lo, double th_hi,
+                                                     float *__restrict__ score) {
+  const float th2f_lo = static_cast<float>(th_lo) * static_cast<float>(th_lo);
+  const float th2f_hi = static_cast<float>(th_hi) * static_cast<float>(th_hi);
   __shared__ NetSmem s;
   __shared__ float xs[4][16][kF];
   __shared__ int cand[4][16];
   load_net(s, params);
   __syncthreads();
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t base = (static_cast<int64_t>(blockIdx.x) * 4 + w) * 16;
-  if (lane < 16) {
-    const int64_t k = base + lane;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2;
+  for (int64_t grp = static_cast<int64_t>(blockIdx.x) * 4 + w; grp * 16 < nf;
+       grp += static_cast<int64_t>(gridDim.x) * 4) {
+    const int64_t base = grp * 16;
     int ok = 0;
-    float f[kF] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (k < nf) {
-      const int A = front[k].x, B = front[k].y;
-      if (A != B) {
-        const double dx = __dsub_rn(Z[3 * A], Z[3 * B]), dy = __dsub_rn(Z[3 * A + 1], Z[3 * B + 1]),
-                     dz = __dsub_rn(Z[3 * A + 2], Z[3 * B + 2]);
-        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-        const double sr = __dadd_rn(Rmax[A], Rmax[B]);
-        ok = d2 >= __dmul_rn(sr, sr);
-        if (ok) pair_features(A, B, Z, Rmax, M, mom, mstride, count, f);
+    if (lane < 16) {
+      const int64_t k = base + lane;
+      float f[kF] = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (k < nf) {
+        const int A = front[k].x, B = front[k].y;
+        if (A != B) {
+          // the walk's criterion at theta_hi and theta_lo (FP32 filter, FP64
+          // for close calls)
+          const CellF fa = zf[A], fb = zf[B];
+          int hi = separated_fast(fa, fb, th2f_hi);
+          if (hi < 0) hi = well_separated(zr[A], zr[B], th_hi);
+          if (hi) {
+            int lo = separated_fast(fa, fb, th2f_lo);
+            if (lo < 0) lo = well_separated(zr[A], zr[B], th_lo);
+            ok = !lo;
+          }
+          if (ok) pair_features(A, B, zf, cf, f);
+        }
       }
-    }
-    cand[w][lane] = ok;
+      cand[w][lane] = ok;
 #pragma unroll
-    for (int q = 0; q < kF; ++q) xs[w][lane][q] = (f[q] - s.mean[q]) * s.scale[q];
-  }
-  __syncwarp();
-  Act act;
-  forward16(s, xs[w], act);
-  const int g = lane >> 2;
-  if ((lane & 3) == 0) {
-    if (base + g < nf) score[base + g] = cand[w][g] ? act.y[0] : INFINITY;
-    if (base + g + 8 < nf) score[base + g + 8] = cand[w][g + 8] ? act.y[1] : INFINITY;
+      for (int q = 0; q < kF; ++q) xs[w][lane][q] = (f[q] - s.mean[q]) * s.scale[q];
+    }
+    const bool any = __any_sync(0xffffffffu, ok);
+    __syncwarp();
+    float y0 = INFINITY, y1 = INFINITY;
+    if (any) {
+      Act act;
+      forward16(s, xs[w], act);
+      y0 = act.y[0];
+      y1 = act.y[1];
+    }
+    if ((lane & 3) == 0) {
+      if (base + g < nf) score[base + g] = cand[w][g] ? y0 : INFINITY;
+      if (base + g + 8 < nf) score[base + g + 8] = cand[w][g + 8] ? y1 : INFINITY;
+    }
+    __syncwarp();
   }
 }
 
@@ -571,10 +616,23 @@ __global__ void k_gather_batch(int64_t B, const int64_t *__restrict__ perm, int6
 
 }  // namespace
 
+int cell_features(fmm_ctx *c) {
+  const int64_t nc = c->sz.ncell;
+  AMFMM_TRY(ensure<float4>(c, c->sel_cellfeat, nc));
+  k_cell_features<<<grid_for(nc, 256), 256, 0, c->stream>>>(static_cast<int32_t>(nc), ptr<double>(c->Rmax),
+                                                           ptr<double>(c->M), ptr<double>(c->mom),
+                                                           mom_stride(c->opts.order_P), ptr<int32_t>(c->count),
+                                                           ptr<float4>(c->sel_cellfeat));
+  return launched(c, "cell_features");
+}
+
 int walk_scores(fmm_ctx *c, int64_t nf, const int2 *front, float *score) {
-  k_walk_scores<<<grid_for(nf, 64), 128, 0, c->stream>>>(nf, front, ptr<float>(c->sel_params), ptr<double>(c->Z),
-                                                         ptr<double>(c->Rmax), ptr<double>(c->M), ptr<double>(c->mom),
-                                                         mom_stride(c->opts.order_P), ptr<int32_t>(c->count), score);
+  // persistent: at most 8 blocks of 4 warps per SM
+  const int64_t need = (nf + 63) / 64;
+  const unsigned g = static_cast<unsigned>(std::min<int64_t>(need, static_cast<int64_t>(c->num_sms) * 8));
+  const double lo = c->opts.theta, hi = c->sel_theta_max;
+  k_walk_scores<<<g, 128, 0, c->stream>>>(nf, front, ptr<float>(c->sel_params), ptr<double4_32a>(c->walk_zr),
+                                          ptr<CellF>(c->walk_zf), ptr<float4>(c->sel_cellfeat), lo, hi, score);
   return launched(c, "walk_scores");
 }
 
@@ -586,10 +644,12 @@ extern "C" {
 
 int fmm_selector_nparams(void) { return kNParams; }
 
-int fmm_selector_set(fmm_ctx *c, const float *params, double log10_target, int enable) {
+int fmm_selector_set(fmm_ctx *c, const float *params, double log10_target, double theta_max, int enable) {
   if (!c) return FMM_EINVAL;
   if (enable) {
     if (!params) return set_error(c, FMM_EINVAL, "NULL parameters");
+    if (!(theta_max > 0.0 && theta_max <= 1.0))
+      return set_error(c, FMM_EINVAL, "theta_max must lie in (0, 1] (got %g)", theta_max);
     AMFMM_TRY(ensure<float>(c, c->sel_params, kNParams));
     AMFMM_CUDA(c, cudaMemcpyAsync(c->sel_params.p, params, sizeof(float) * kNParams, cudaMemcpyHostToDevice,
                                   c->stream));
@@ -597,6 +657,7 @@ int fmm_selector_set(fmm_ctx *c, const float *params, double log10_target, int e
   }
   c->sel_enabled = enable != 0;
   c->sel_log10_target = log10_target;
+  if (enable) c->sel_theta_max = theta_max;
   c->stage = kNone;
   return FMM_OK;
 }
@@ -609,8 +670,9 @@ int fmm_selector_samples(fmm_ctx *c, const int32_t *pairs, int64_t K, float *fea
   if (K == 0) return FMM_OK;
   cudaStream_t st = c->stream;
   const int2 *pp = reinterpret_cast<const int2 *>(pairs);
-  k_features<<<grid_for(K, 256), 256, 0, st>>>(K, pp, ptr<double>(c->Z), ptr<double>(c->Rmax), ptr<double>(c->M),
-                                               ptr<double>(c->mom), mom_stride(3), ptr<int32_t>(c->count), feat);
+  AMFMM_TRY(pack_walk_cells(c));
+  AMFMM_TRY(cell_features(c));
+  k_features<<<grid_for(K, 256), 256, 0, st>>>(K, pp, ptr<CellF>(c->walk_zf), ptr<float4>(c->sel_cellfeat), feat);
   AMFMM_TRY(launched(c, "features"));
   if (label) {
     // the pairs' order-3 TC locals, then the per-pair errors

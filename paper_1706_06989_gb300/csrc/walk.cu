@@ -17,6 +17,7 @@
 // independent of the traversal order.  The walk proceeds one generation of
 // pairs at a time; an exclusive scan of the per-pair output counts places
 // every output, which makes the list order deterministic.
+#include "geom.cuh"
 #include "internal.cuh"
 
 namespace amfmm {
@@ -26,24 +27,20 @@ constexpr int kBlock = 256;
 
 enum Action : int32_t { kSelfLeaf = 0, kSelfSplit = 1, kAccept = 2, kNear = 3, kSplitA = 4, kSplitB = 5 };
 
-// per cell {Z_x, Z_y, Z_z, R_max}, one 32-byte load
-__device__ __forceinline__ bool well_separated(const double4_32a a, const double4_32a b, double theta) {
-  const double dx = __dsub_rn(a.x, b.x);
-  const double dy = __dsub_rn(a.y, b.y);
-  const double dz = __dsub_rn(a.z, b.z);
-  const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-  const double th2 = __dmul_rn(theta, theta);
-  const double s = __dadd_rn(a.w, b.w);
-  return __dmul_rn(th2, d2) >= __dmul_rn(s, s);
-}
-
-// packs the walk's per-cell inputs: {Z, R_max} and {nchild, level}
+// packs the walk's per-cell inputs: {Z, R_max} (FP64 and the FP32 filter's
+// copy) and {nchild, level}
 __global__ void k_pack_cells(int32_t ncell, const double *__restrict__ Z, const double *__restrict__ Rmax,
                              const int32_t *__restrict__ nchild, const int32_t *__restrict__ level,
-                             double4_32a *__restrict__ zr, int2 *__restrict__ nl) {
+                             double4_32a *__restrict__ zr, CellF *__restrict__ zf, int2 *__restrict__ nl) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncell) return;
-  zr[c] = make_double4_32a(Z[3 * c], Z[3 * c + 1], Z[3 * c + 2], Rmax[c]);
+  const double x = Z[3 * c], y = Z[3 * c + 1], z = Z[3 * c + 2], R = Rmax[c];
+  zr[c] = make_double4_32a(x, y, z, R);
+  const float hx = static_cast<float>(x), hy = static_cast<float>(y), hz = static_cast<float>(z);
+  CellF f;
+  f.h = make_float4(hx, hy, hz, static_cast<float>(R));
+  f.l = make_float4(static_cast<float>(x - hx), static_cast<float>(y - hy), static_cast<float>(z - hz), 0.f);
+  zf[c] = f;
   nl[c] = make_int2(nchild[c], level[c]);
 }
 
@@ -51,89 +48,253 @@ __global__ void k_pack_cells(int32_t ncell, const double *__restrict__ Z, const 
 // pair (+inf where the safety bound fails); with it, a pair is accepted when
 // the opening criterion accepts it (theta is then a floor on the accepted
 // set, which bounds the work of a strict target) or when score < target.
-__global__ void k_classify(int64_t nf, const int2 *__restrict__ front, const int2 *__restrict__ nl,
-                           const double4_32a *__restrict__ zr, double theta, const float *__restrict__ score,
-                           float target, int32_t *__restrict__ action, int4 *__restrict__ counts) {
-  int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (t >= nf) return;
-  const int A = front[t].x, B = front[t].y;
-  int act;
-  int4 cnt = make_int4(0, 0, 0, 0);
+// Output counts: x = next-generation pairs, y = M2L, z = P2P, w = leaf self.
+__device__ __forceinline__ int classify(int A, int B, const int2 *__restrict__ nl,
+                                        const double4_32a *__restrict__ zr, const CellF *__restrict__ zf,
+                                        double theta, float th2f, bool accept_hint, int4 &cnt) {
+  cnt = make_int4(0, 0, 0, 0);
   const int2 nlA = nl[A];
   if (A == B) {
     const int k = nlA.x;
     if (k == 0) {
-      act = kSelfLeaf;
       cnt.w = 1;
-    } else {
-      act = kSelfSplit;
-      cnt.x = k + k * (k - 1) / 2;
+      return kSelfLeaf;
     }
-  } else if (well_separated(zr[A], zr[B], theta) || (score && score[t] < target)) {
-    act = kAccept;
-    cnt.y = 1;
-  } else {
-    const int2 nlB = nl[B];
-    const int ka = nlA.x, kb = nlB.x;
-    if (ka == 0 && kb == 0) {
-      act = kNear;
-      cnt.z = 1;
-    } else {
-      bool pickA;
-      if (kb == 0) pickA = true;
-      else if (ka == 0) pickA = false;
-      else {
-        const double ra = zr[A].w, rb = zr[B].w;
-        if (ra != rb) pickA = ra > rb;
-        else if (nlA.y != nlB.y) pickA = nlA.y < nlB.y;
-        else pickA = A < B;
-      }
-      act = pickA ? kSplitA : kSplitB;
-      cnt.x = pickA ? ka : kb;
-    }
+    cnt.x = k + k * (k - 1) / 2;
+    return kSelfSplit;
   }
-  action[t] = act;
-  counts[t] = cnt;
+  int sep = accept_hint ? 1 : separated_fast(zf[A], zf[B], th2f);
+  if (sep < 0) sep = well_separated(zr[A], zr[B], theta);
+  if (sep) {
+    cnt.y = 1;
+    return kAccept;
+  }
+  const int2 nlB = nl[B];
+  const int ka = nlA.x, kb = nlB.x;
+  if (ka == 0 && kb == 0) {
+    cnt.z = 1;
+    return kNear;
+  }
+  bool pickA;
+  if (kb == 0) pickA = true;
+  else if (ka == 0) pickA = false;
+  else {
+    const double ra = zr[A].w, rb = zr[B].w;
+    if (ra != rb) pickA = ra > rb;
+    else if (nlA.y != nlB.y) pickA = nlA.y < nlB.y;
+    else pickA = A < B;
+  }
+  cnt.x = pickA ? ka : kb;
+  return pickA ? kSplitA : kSplitB;
 }
 
-__global__ void k_emit(int64_t nf, const int2 *__restrict__ front, const int32_t *__restrict__ action,
-                       const int4 *__restrict__ offs, const int32_t *__restrict__ first_child,
-                       const int32_t *__restrict__ nchild, int2 *__restrict__ next,
-                       int2 *__restrict__ m2l, int64_t m2l_base, int2 *__restrict__ p2p,
-                       int64_t p2p_base, int32_t *__restrict__ self, int64_t self_base) {
-  int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (t >= nf) return;
-  const int A = front[t].x, B = front[t].y;
-  const int4 o = offs[t];
-  switch (action[t]) {
-    case kSelfLeaf:
-      self[self_base + o.w] = A;
-      break;
-    case kSelfSplit: {
-      const int f = first_child[A], k = nchild[A];
-      int q = o.x;
-      for (int i = 0; i < k; ++i) next[q++] = make_int2(f + i, f + i);
-      for (int i = 0; i < k; ++i)
-        for (int j = i + 1; j < k; ++j) next[q++] = make_int2(f + i, f + j);
-      break;
-    }
-    case kAccept:
-      m2l[m2l_base + o.y] = make_int2(min(A, B), max(A, B));
-      break;
-    case kNear:
-      p2p[p2p_base + o.z] = make_int2(min(A, B), max(A, B));
-      break;
-    case kSplitA: {
-      const int f = first_child[A], k = nchild[A];
-      for (int i = 0; i < k; ++i) next[o.x + i] = make_int2(f + i, B);
-      break;
-    }
-    default: {
-      const int f = first_child[B], k = nchild[B];
-      for (int i = 0; i < k; ++i) next[o.x + i] = make_int2(A, f + i);
-      break;
+__device__ __forceinline__ int4 add4(int4 a, int4 b) { return make_int4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+
+// State shared by the blocks of one generation (device memory):
+//   ticket       -- running block counter; a block's place in the scan is its
+//                   ticket minus the launch's base, so places follow the order
+//                   in which blocks start and every block waits only on blocks
+//                   that started before it;
+//   status       -- bit 0: an output did not fit its buffer; bit 1: a wait
+//                   for a predecessor gave up;
+//   total        -- the generation's output counts (written by the last block);
+//   flag/agg/inc -- per-place publication for the decoupled look-back, flag =
+//                   epoch << 2 | state (1: aggregate, 2: inclusive prefix).
+struct GenState {
+  unsigned ticket;
+  int status;
+  int pad[2];
+  int4 total;
+};
+
+constexpr int kGenItems = 4;
+constexpr int kGenTile = kBlock * kGenItems;
+constexpr long long kSpinLimit = 1LL << 22;
+
+__device__ __forceinline__ int4 ld_volatile4(const int4 *p) {
+  const volatile int *q = reinterpret_cast<const volatile int *>(p);
+  return make_int4(q[0], q[1], q[2], q[3]);
+}
+__device__ __forceinline__ void st_volatile4(int4 *p, int4 v) {
+  volatile int *q = reinterpret_cast<volatile int *>(p);
+  q[0] = v.x;
+  q[1] = v.y;
+  q[2] = v.z;
+  q[3] = v.w;
+}
+
+// One generation of the walk: every pair of the frontier is classified, the
+// output counts are scanned across the block and then across blocks (single
+// pass, decoupled look-back), and the outputs are written in frontier order.
+// Any write beyond a buffer's capacity is skipped and flagged; the host then
+// grows the buffers and runs the generation again.
+__global__ void __launch_bounds__(kBlock) k_walk_gen(
+    int64_t nf, const int2 *__restrict__ front, const int2 *__restrict__ nl, const double4_32a *__restrict__ zr,
+    const CellF *__restrict__ zf, double theta, const float *__restrict__ score, float target, const int32_t *__restrict__ first_child,
+    int2 *__restrict__ next, int64_t cap_next, int2 *__restrict__ m2l, int64_t m2l_base, int64_t cap_m2l,
+    int2 *__restrict__ p2p, int64_t p2p_base, int64_t cap_p2p, int32_t *__restrict__ self, int64_t self_base,
+    int64_t cap_self, GenState *__restrict__ gs, unsigned ticket_base, unsigned epoch, unsigned nblocks,
+    int *__restrict__ flag, int4 *__restrict__ agg, int4 *__restrict__ inc) {
+  __shared__ unsigned s_place;
+  const float th2f = static_cast<float>(theta) * static_cast<float>(theta);
+  __shared__ int4 s_warp[kBlock / 32];
+  __shared__ int4 s_prefix;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (t == 0) s_place = atomicAdd(&gs->ticket, 1u) - ticket_base;
+  __syncthreads();
+  const unsigned place = s_place;
+  const int64_t i0 = static_cast<int64_t>(place) * kGenTile + static_cast<int64_t>(t) * kGenItems;
+  int act[kGenItems];
+  int2 pr[kGenItems];
+  int4 mine = make_int4(0, 0, 0, 0);
+#pragma unroll
+  for (int k = 0; k < kGenItems; ++k) {
+    const int64_t i = i0 + k;
+    act[k] = -1;
+    if (i < nf) {
+      pr[k] = front[i];
+      int4 cnt;
+      const bool hint = score != nullptr && score[i] < target;
+      act[k] = classify(pr[k].x, pr[k].y, nl, zr, zf, theta, th2f, hint, cnt);
+      mine = add4(mine, cnt);
     }
   }
+  // block-wide exclusive scan of the per-thread counts
+  int4 incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int4 y = make_int4(__shfl_up_sync(0xffffffffu, incl.x, o), __shfl_up_sync(0xffffffffu, incl.y, o),
+                             __shfl_up_sync(0xffffffffu, incl.z, o), __shfl_up_sync(0xffffffffu, incl.w, o));
+    if (lane >= o) incl = add4(incl, y);
+  }
+  if (lane == 31) s_warp[w] = incl;
+  __syncthreads();
+  int4 before = make_int4(incl.x - mine.x, incl.y - mine.y, incl.z - mine.z, incl.w - mine.w);
+  int4 block_total = make_int4(0, 0, 0, 0);
+#pragma unroll
+  for (int q = 0; q < kBlock / 32; ++q) {
+    if (q < w) before = add4(before, s_warp[q]);
+    block_total = add4(block_total, s_warp[q]);
+  }
+  // look-back: the sum of the totals of all earlier places, read by the
+  // first warp 32 places at a time (lane k looks at place - 1 - k)
+  if (w == 0) {
+    const int ep = static_cast<int>(epoch & 0x3fffffffu) << 2;
+    if (lane == 0) {
+      if (place == 0) st_volatile4(&inc[0], block_total);
+      else st_volatile4(&agg[place], block_total);
+      __threadfence();
+      atomicExch(&flag[place], ep | (place == 0 ? 2 : 1));
+    }
+    int4 pre = make_int4(0, 0, 0, 0);
+    bool failed = false;
+    if (place > 0) {
+      int top = static_cast<int>(place) - 1;  // highest place not yet summed
+      long long spins = 0;
+      while (top >= 0) {
+        const int j = top - lane;
+        int f = j >= 0 ? *reinterpret_cast<volatile int *>(&flag[j]) : (ep | 2);
+        bool ready = (f & ~3) == ep && (f & 3) != 0;
+        // wait until every place of the window has published something
+        while (!__all_sync(0xffffffffu, ready)) {
+          if (++spins > kSpinLimit) break;
+          __nanosleep(32);
+          if (!ready) {
+            f = *reinterpret_cast<volatile int *>(&flag[j]);
+            ready = (f & ~3) == ep && (f & 3) != 0;
+          }
+        }
+        if (!__all_sync(0xffffffffu, ready)) {
+          failed = true;
+          break;
+        }
+        __threadfence();
+        // nearest place in the window that holds an inclusive prefix
+        const unsigned incl_mask = __ballot_sync(0xffffffffu, j >= 0 && (f & 3) == 2);
+        const int stop = incl_mask ? __ffs(incl_mask) - 1 : 32;  // lanes [0, stop) add aggregates
+        int4 v = make_int4(0, 0, 0, 0);
+        if (j >= 0 && lane < stop) v = ld_volatile4(&agg[j]);
+        if (j >= 0 && lane == stop) v = ld_volatile4(&inc[j]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+          v = add4(v, make_int4(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o),
+                                __shfl_xor_sync(0xffffffffu, v.z, o), __shfl_xor_sync(0xffffffffu, v.w, o)));
+        pre = add4(pre, v);
+        if (incl_mask) break;
+        top -= 32;
+      }
+      if (lane == 0) {
+        if (failed) atomicOr(&gs->status, 2);
+        st_volatile4(&inc[place], add4(pre, block_total));
+        __threadfence();
+        atomicExch(&flag[place], ep | 2);
+      }
+    }
+    if (lane == 0) {
+      if (place == nblocks - 1) gs->total = add4(pre, block_total);
+      s_prefix = pre;
+    }
+  }
+  __syncthreads();
+  const int4 base = add4(s_prefix, before);
+  int64_t ox = base.x, oy = m2l_base + base.y, oz = p2p_base + base.z, ow = self_base + base.w;
+  bool over = false;
+#pragma unroll
+  for (int k = 0; k < kGenItems; ++k) {
+    if (act[k] < 0) continue;
+    const int A = pr[k].x, B = pr[k].y;
+    switch (act[k]) {
+      case kSelfLeaf:
+        if (ow < cap_self) self[ow] = A;
+        else over = true;
+        ++ow;
+        break;
+      case kSelfSplit: {
+        const int f = first_child[A], kk = nl[A].x;
+        for (int a = 0; a < kk; ++a) {
+          if (ox < cap_next) next[ox] = make_int2(f + a, f + a);
+          else over = true;
+          ++ox;
+        }
+        for (int a = 0; a < kk; ++a)
+          for (int b = a + 1; b < kk; ++b) {
+            if (ox < cap_next) next[ox] = make_int2(f + a, f + b);
+            else over = true;
+            ++ox;
+          }
+        break;
+      }
+      case kAccept:
+        if (oy < cap_m2l) m2l[oy] = make_int2(min(A, B), max(A, B));
+        else over = true;
+        ++oy;
+        break;
+      case kNear:
+        if (oz < cap_p2p) p2p[oz] = make_int2(min(A, B), max(A, B));
+        else over = true;
+        ++oz;
+        break;
+      case kSplitA: {
+        const int f = first_child[A], kk = nl[A].x;
+        for (int a = 0; a < kk; ++a) {
+          if (ox < cap_next) next[ox] = make_int2(f + a, B);
+          else over = true;
+          ++ox;
+        }
+        break;
+      }
+      default: {
+        const int f = first_child[B], kk = nl[B].x;
+        for (int a = 0; a < kk; ++a) {
+          if (ox < cap_next) next[ox] = make_int2(A, f + a);
+          else over = true;
+          ++ox;
+        }
+        break;
+      }
+    }
+  }
+  if (over) atomicOr(&gs->status, 1);
 }
 
 __global__ void k_roots_front(int32_t nsys, int2 *__restrict__ front) {
@@ -142,6 +303,17 @@ __global__ void k_roots_front(int32_t nsys, int2 *__restrict__ front) {
 }
 
 }  // namespace
+
+int pack_walk_cells(fmm_ctx *c) {
+  const int64_t nc = c->sz.ncell;
+  AMFMM_TRY(ensure<double4_32a>(c, c->walk_zr, nc));
+  AMFMM_TRY(ensure<int2>(c, c->walk_nl, nc));
+  AMFMM_TRY(ensure<CellF>(c, c->walk_zf, nc));
+  k_pack_cells<<<grid_for(nc, kBlock), kBlock, 0, c->stream>>>(
+      static_cast<int32_t>(nc), ptr<double>(c->Z), ptr<double>(c->Rmax), ptr<int32_t>(c->nchild),
+      ptr<int32_t>(c->level), ptr<double4_32a>(c->walk_zr), ptr<CellF>(c->walk_zf), ptr<int2>(c->walk_nl));
+  return launched(c, "walk_pack");
+}
 
 int walk(fmm_ctx *c) {
   cudaStream_t st = c->stream;
@@ -164,59 +336,78 @@ int walk(fmm_ctx *c) {
     AMFMM_TRY(ensure<int32_t>(c, c->self_list, cap_self));
   }
 
-  int4 *total = ptr<int4>(c->totals);
-  const int64_t nc = c->sz.ncell;
-  AMFMM_TRY(ensure<double4_32a>(c, c->walk_zr, nc));
-  AMFMM_TRY(ensure<int2>(c, c->walk_nl, nc));
-  k_pack_cells<<<grid_for(nc, kBlock), kBlock, 0, st>>>(static_cast<int32_t>(nc), ptr<double>(c->Z), ptr<double>(c->Rmax),
-                                                       ptr<int32_t>(c->nchild), ptr<int32_t>(c->level),
-                                                       ptr<double4_32a>(c->walk_zr), ptr<int2>(c->walk_nl));
-  AMFMM_TRY(launched(c, "walk_pack"));
+  AMFMM_TRY(pack_walk_cells(c));
+  if (c->sel_enabled) AMFMM_TRY(cell_features(c));
   // one self pair per root: systems of a forest never interact
   const int64_t nsys = c->sz.nsys;
   if (nsys > static_cast<int64_t>(c->front[0].cap / sizeof(int2))) AMFMM_TRY(ensure<int2>(c, c->front[0], nsys));
   k_roots_front<<<grid_for(nsys, kBlock), kBlock, 0, st>>>(static_cast<int32_t>(nsys), ptr<int2>(c->front[0]));
   AMFMM_TRY(launched(c, "walk_roots"));
+  // state of the single-pass generations (allocated and zeroed once)
+  if (c->walk_state.cap < sizeof(GenState)) {
+    AMFMM_TRY(ensure_bytes(c, c->walk_state, sizeof(GenState)));
+    AMFMM_CUDA(c, cudaMemsetAsync(c->walk_state.p, 0, sizeof(GenState), st));
+    c->walk_ticket = 0;
+  }
+  GenState *gs = static_cast<GenState *>(c->walk_state.p);
   int64_t nf = nsys, n_m2l = 0, n_p2p = 0, n_self = 0;
   int cur = 0;
   while (nf > 0) {
-    AMFMM_TRY(ensure<int32_t>(c, c->action, nf));
-    AMFMM_TRY(ensure<int4>(c, c->wcount, nf));
-    AMFMM_TRY(ensure<int4>(c, c->woff, nf));
     const float *score = nullptr;
     if (c->sel_enabled) {
       AMFMM_TRY(ensure<float>(c, c->sel_score, nf));
       AMFMM_TRY(walk_scores(c, nf, ptr<int2>(c->front[cur]), ptr<float>(c->sel_score)));
       score = ptr<float>(c->sel_score);
     }
-    k_classify<<<grid_for(nf, kBlock), kBlock, 0, st>>>(
-        nf, ptr<int2>(c->front[cur]), ptr<int2>(c->walk_nl), ptr<double4_32a>(c->walk_zr), c->theta, score,
-        static_cast<float>(c->sel_log10_target), ptr<int32_t>(c->action), ptr<int4>(c->wcount));
-    AMFMM_TRY(launched(c, "walk_classify"));
-    AMFMM_TRY(exclusive_scan_i4(c, ptr<int4>(c->wcount), ptr<int4>(c->woff), nf, total));
-    int4 *h = static_cast<int4 *>(c->hpin);
-    AMFMM_CUDA(c, cudaMemcpyAsync(h, total, sizeof(int4), cudaMemcpyDeviceToHost, st));
-    AMFMM_CUDA(c, cudaStreamSynchronize(st));
-    const int4 tot = *h;
-    if (tot.x > 0 && tot.x > static_cast<int64_t>(c->front[cur ^ 1].cap / sizeof(int2)))
-      AMFMM_TRY(ensure<int2>(c, c->front[cur ^ 1], std::max<int64_t>(tot.x, 2 * (c->front[cur ^ 1].cap / sizeof(int2)))));
-    if (n_m2l + tot.y > cap_m2l) {
-      cap_m2l = std::max<int64_t>(2 * cap_m2l, n_m2l + tot.y);
-      AMFMM_TRY(ensure_keep_bytes(c, c->m2l, cap_m2l * sizeof(int2), n_m2l * sizeof(int2)));
+    const int64_t nb64 = (nf + kGenTile - 1) / kGenTile;
+    if (nb64 > 0x7fffffffLL) return set_error(c, FMM_EUNSUPPORTED, "walk frontier too large (%lld pairs)", (long long)nf);
+    const unsigned nb = static_cast<unsigned>(nb64);
+    // look-back records; fresh memory is zeroed so no stale flag matches an epoch
+    const size_t lb_bytes = static_cast<size_t>(nb) * (sizeof(int) + 2 * sizeof(int4)) + 64;
+    if (c->walk_lb.cap < lb_bytes) {
+      AMFMM_TRY(ensure_bytes(c, c->walk_lb, lb_bytes + lb_bytes / 2));
+      AMFMM_CUDA(c, cudaMemsetAsync(c->walk_lb.p, 0, c->walk_lb.cap, st));
     }
-    if (n_p2p + tot.z > cap_p2p) {
-      cap_p2p = std::max<int64_t>(2 * cap_p2p, n_p2p + tot.z);
-      AMFMM_TRY(ensure_keep_bytes(c, c->p2p, cap_p2p * sizeof(int2), n_p2p * sizeof(int2)));
+    const size_t nbc = (c->walk_lb.cap - 64) / (sizeof(int) + 2 * sizeof(int4));
+    int4 *agg = static_cast<int4 *>(c->walk_lb.p);
+    int4 *inc = agg + nbc;
+    int *flg = reinterpret_cast<int *>(inc + nbc);
+    int4 tot;
+    for (int attempt = 0;; ++attempt) {
+      const int64_t cap_next = static_cast<int64_t>(c->front[cur ^ 1].cap / sizeof(int2));
+      c->walk_epoch = (c->walk_epoch + 1) & 0x3fffffffu;
+      if (c->walk_epoch == 0) c->walk_epoch = 1;
+      k_walk_gen<<<nb, kBlock, 0, st>>>(
+          nf, ptr<int2>(c->front[cur]), ptr<int2>(c->walk_nl), ptr<double4_32a>(c->walk_zr),
+          ptr<CellF>(c->walk_zf), c->theta, score,
+          static_cast<float>(c->sel_log10_target), ptr<int32_t>(c->first_child), ptr<int2>(c->front[cur ^ 1]),
+          cap_next, ptr<int2>(c->m2l), n_m2l, cap_m2l, ptr<int2>(c->p2p), n_p2p, cap_p2p,
+          ptr<int32_t>(c->self_list), n_self, cap_self, gs, c->walk_ticket, c->walk_epoch, nb, flg, agg, inc);
+      c->walk_ticket += nb;
+      AMFMM_TRY(launched(c, "walk_gen"));
+      GenState *h = static_cast<GenState *>(c->hpin);
+      AMFMM_CUDA(c, cudaMemcpyAsync(h, gs, sizeof(GenState), cudaMemcpyDeviceToHost, st));
+      AMFMM_CUDA(c, cudaStreamSynchronize(st));
+      tot = h->total;
+      if (h->status & 2) return set_error(c, FMM_ETIMEOUT, "walk: a block waited too long for its predecessor");
+      if (!(h->status & 1)) break;
+      if (attempt > 0) return set_error(c, FMM_EINVAL, "walk: outputs overflowed after growing the buffers");
+      // an output did not fit: grow what overflowed and run the generation again
+      if (tot.x > cap_next) AMFMM_TRY(ensure<int2>(c, c->front[cur ^ 1], std::max<int64_t>(tot.x, 2 * cap_next)));
+      if (n_m2l + tot.y > cap_m2l) {
+        cap_m2l = std::max<int64_t>(2 * cap_m2l, n_m2l + tot.y);
+        AMFMM_TRY(ensure_keep_bytes(c, c->m2l, cap_m2l * sizeof(int2), n_m2l * sizeof(int2)));
+      }
+      if (n_p2p + tot.z > cap_p2p) {
+        cap_p2p = std::max<int64_t>(2 * cap_p2p, n_p2p + tot.z);
+        AMFMM_TRY(ensure_keep_bytes(c, c->p2p, cap_p2p * sizeof(int2), n_p2p * sizeof(int2)));
+      }
+      if (n_self + tot.w > cap_self) {
+        cap_self = std::max<int64_t>(2 * cap_self, n_self + tot.w);
+        AMFMM_TRY(ensure_keep_bytes(c, c->self_list, cap_self * sizeof(int32_t), n_self * sizeof(int32_t)));
+      }
+      AMFMM_CUDA(c, cudaMemsetAsync(&gs->status, 0, sizeof(int), st));
     }
-    if (n_self + tot.w > cap_self) {
-      cap_self = std::max<int64_t>(2 * cap_self, n_self + tot.w);
-      AMFMM_TRY(ensure_keep_bytes(c, c->self_list, cap_self * sizeof(int32_t), n_self * sizeof(int32_t)));
-    }
-    k_emit<<<grid_for(nf, kBlock), kBlock, 0, st>>>(
-        nf, ptr<int2>(c->front[cur]), ptr<int32_t>(c->action), ptr<int4>(c->woff),
-        ptr<int32_t>(c->first_child), ptr<int32_t>(c->nchild), ptr<int2>(c->front[cur ^ 1]),
-        ptr<int2>(c->m2l), n_m2l, ptr<int2>(c->p2p), n_p2p, ptr<int32_t>(c->self_list), n_self);
-    AMFMM_TRY(launched(c, "walk_emit"));
     n_m2l += tot.y;
     n_p2p += tot.z;
     n_self += tot.w;

@@ -63,7 +63,8 @@ def test_features_and_labels_match_oracle():
     cnt = o.cells().count
     p = b.pos()
     for k, (A, B) in enumerate(sel):
-        if R[B] > R[A] or (R[B] == R[A] and B < A):
+        ra, rb = np.float32(R[A]), np.float32(R[B])  # pairs are ordered by R_max in FP32
+        if rb > ra or (rb == ra and B < A):
             A, B = B, A
         r = np.linalg.norm(Zc[A] - Zc[B])
         assert abs(feat[k, 0] - np.log10(r)) < 1e-5
@@ -136,23 +137,25 @@ def test_training_reduces_the_loss():
 
 
 def test_selector_extremes_reduce_to_the_plain_criterion():
-    """theta is a floor: a network that accepts nothing leaves the walk of the
-    plain criterion at theta; one that accepts everything it may (the safety
-    bound) gives the walk of the criterion at theta = 1."""
+    """theta is a floor and theta_max a ceiling: a network that accepts nothing
+    leaves the walk of the plain criterion at theta; one that accepts every
+    pair of the band gives the walk of the criterion at theta_max."""
     b = ics.plummer(3000, seed=9)
     x, y, z, m = _dev(b)
     lists = {}
-    for th in (0.5, 1.0):
+    for th in (0.5, 0.7, 1.0):
         s = _solver(theta=th)
         s.solve(x, y, z, m)
         lists[th] = [t.cpu().numpy() for t in s.export_lists()]
     p = _params(3)
     p[M.NW - 65:M.NW - 1] = 0.0  # w4: constant output b4
-    for b4, th in ((100.0, 0.5), (-100.0, 1.0)):
+    for b4, th_max, th in ((100.0, 1.0, 0.5), (-100.0, 1.0, 1.0), (-100.0, 0.7, 0.7)):
         p[M.NW - 1] = b4
         s = _solver(theta=0.5)
-        s.selector_set(p, log10_target=-3.0, enable=True)
+        s.selector_set(p, log10_target=-3.0, enable=True, theta_max=th_max)
         s.solve(x, y, z, m)
         got = [t.cpu().numpy() for t in s.export_lists()]
         for g, r in zip(got, lists[th]):
-            assert np.array_equal(g, r), (b4, th)
+            assert np.array_equal(g, r), (b4, th_max, th)
+    with pytest.raises(Exception):
+        s.selector_set(p, log10_target=-3.0, enable=True, theta_max=1.5)
