@@ -90,6 +90,7 @@ typedef struct {
   /* per-stage device time in ms of the last solve, when timing is enabled
      with fmm_set_timing: tree, upward, walk, m2l, p2p, reduce, downward */
   float ms_tree, ms_upward, ms_walk, ms_m2l, ms_p2p, ms_reduce, ms_downward;
+  int64_t n_scored;   /* pairs the learned selector evaluated in the last solve (0 without it) */
 } fmm_stats;
 
 /* Creates a context bound to `cuda_stream` (a cudaStream_t; NULL = the
@@ -194,10 +195,15 @@ int fmm_selector_nparams(void);
  * criterion at the context's theta still accepts what it accepts; a pair it
  * rejects but that the criterion at theta_max (theta < theta_max <= 1;
  * theta_max = 1 is the safety bound |Z_A - Z_B| >= R_A + R_B) accepts is
- * accepted when the prediction is below log10_target.  Every other pair is
- * opened as usual.  The network only adds pairs, so the interaction lists
- * never grow beyond those of the plain criterion at theta.  FMM_EINVAL if
- * theta_max is outside (0, 1]. */
+ * accepted when its predicted absolute error, relative to the field at each
+ * side, is below 10^log10_target: the network predicts the larger side's
+ * error e in units of the partner's monopole field, and the pair is accepted
+ * when e max(M_B / (r^2 |a_A|), M_A / (r^2 |a_B|)) < 10^log10_target, with
+ * |a| a per-cell estimate from the softened monopoles of one coarse level.
+ * Every other pair is opened as usual.  The network only adds pairs, so the
+ * interaction lists never grow beyond those of the plain criterion at theta.
+ * One system per solve (fmm_solve_batch with the selector on returns
+ * FMM_EUNSUPPORTED).  FMM_EINVAL if theta_max is outside (0, 1]. */
 int fmm_selector_set(fmm_ctx *ctx, const float *params, double log10_target, double theta_max, int enable);
 
 /* Training samples for K given cell pairs of the current tree (after
@@ -206,7 +212,9 @@ int fmm_selector_set(fmm_ctx *ctx, const float *params, double log10_target, dou
  * the two sides' errors, where a side's error is the rms over its bodies of
  * |a_M2L - a_direct| for the pair alone (torque-corrected order-3
  * expansion) divided by the other cell's monopole field M_other/|r|^2;
- * floored at -12 (the FP64 rounding level).  Asynchronous. */
+ * floored at -12 (the FP64 rounding level).  A side of n > 128 bodies is
+ * represented by the 128 bodies at sorted positions floor(t n / 128) of the
+ * cell.  Asynchronous. */
 int fmm_selector_samples(fmm_ctx *ctx, const int32_t *pairs, int64_t K, float *feat, float *label);
 
 /* Network output for K samples of raw features (device in, device out). */

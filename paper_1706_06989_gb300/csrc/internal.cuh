@@ -86,11 +86,11 @@ struct fmm_ctx {
   amfmm::DBuf pkey[2], pval[2], p2p_A, p2p_offA, p2p_offB, p2p_pos, p2p_poff, p2p_len,
       p2p_slots, p2p_colOff, p2p_cols, p2p_nb, p2p_pre, p2p_bodyf;
   // scan / sort scratch; `totals` holds small device results (1 KiB):
-  // [0,16) scan totals, [64,72) near-field body-pair count, [96,104) slot total,
+  // [0,16) scan totals, [64,72) near-field body-pair count, [80,88) selector-scored pairs, [88,92) selector candidates, [96,104) slot total,
   // [128,132) near-field column total
   amfmm::DBuf scan_tmp, sort_hist, totals, diag;
   // learned pair selector
-  amfmm::DBuf sel_params, sel_cellfeat, sel_scratch, sel_part, sel_score, sel_grad, sel_perm, sel_xb, sel_yb;
+  amfmm::DBuf sel_params, sel_cellfeat, sel_cand, sel_lga, sel_scratch, sel_part, sel_score, sel_grad, sel_perm, sel_xb, sel_yb;
   bool sel_enabled = false;
   double sel_log10_target = -3.0;
   double sel_theta_max = 1.0;  // upper edge of the band the network decides
@@ -179,6 +179,7 @@ int downward_general(fmm_ctx *c);
 
 // learned selector (selector.cu, m2l.cu)
 int cell_features(fmm_ctx *c);  // per-cell parts of the selector's features
+int field_estimate(fmm_ctx *c);  // per-cell log10 |a| estimate of the selector's relative rule
 int walk_scores(fmm_ctx *c, int64_t nf, const int2 *front, float *score);
 int pair_locals_tc(fmm_ctx *c, const int2 *pairs, int64_t K, double *out);
 

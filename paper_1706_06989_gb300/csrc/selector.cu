@@ -104,13 +104,64 @@ __global__ void k_features(int64_t K, const int2 *__restrict__ pairs, const Cell
   for (int q = 0; q < kF; ++q) feat[k * kF + q] = f[q];
 }
 
+// Field at every cell for the relative acceptance rule: the monopoles of one
+// coarse level (at most 2048 cells), each softened by its own R_max (the
+// field of an extended mass, finite inside it), summed in FP32 at the cell's
+// centre.  A rough estimate is enough: it only scales the error target.
+// Stored as log10 |a|.
+constexpr int kFieldTile = 256;
+
+__global__ void __launch_bounds__(kFieldTile) k_field_estimate(int32_t ncell, const CellF *__restrict__ zf,
+                                                              const double *__restrict__ M, int32_t k0,
+                                                              int32_t k1, float *__restrict__ lga) {
+  __shared__ float4 src[kFieldTile];
+  __shared__ float eps2[kFieldTile];
+  const int c = blockIdx.x * kFieldTile + threadIdx.x;
+  float4 me = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (c < ncell) me = zf[c].h;
+  float ax = 0.f, ay = 0.f, az = 0.f;
+  for (int t0 = k0; t0 < k1; t0 += kFieldTile) {
+    const int k = t0 + threadIdx.x;
+    if (k < k1) {
+      const float4 h = zf[k].h;
+      src[threadIdx.x] = make_float4(h.x, h.y, h.z, static_cast<float>(M[k]));
+      eps2[threadIdx.x] = h.w * h.w;
+    }
+    __syncthreads();
+    const int nt = min(kFieldTile, k1 - t0);
+    for (int j = 0; j < nt; ++j) {
+      const float4 s = src[j];
+      const float e2 = eps2[j];
+      const float dx = s.x - me.x, dy = s.y - me.y, dz = s.z - me.z;
+      const float r2 = dx * dx + dy * dy + dz * dz + e2;
+      if (r2 > 0.f) {
+        const float ri = rsqrtf(r2);
+        const float w = s.w * ri * ri * ri;
+        ax += w * dx;
+        ay += w * dy;
+        az += w * dz;
+      }
+    }
+    __syncthreads();
+  }
+  if (c < ncell) lga[c] = lg(sqrtf(ax * ax + ay * ay + az * az) + 1e-30f);
+}
+
 // Label of one pair (block per pair): for each side, the rms over its bodies
 // of |a_M2L - a_direct| for the interaction of A with B alone (order 3, the
 // torque-corrected expansion of Eqs. 3, 4, 7), divided by the monopole field
 // of the other cell at that distance (M_B/|r|^2 on A, M_A/|r|^2 on B); the
 // label is log10 of the larger of the two, floored at -12.  Taking the worse
 // side keeps a small cell's large error from being averaged away by the
-// bodies of a big partner.
+// bodies of a big partner.  A side of more than kLabelTargets bodies is
+// represented by kLabelTargets of them at evenly spaced sorted positions
+// (t n / kLabelTargets), each still summed over every body of the partner,
+// so that pairs of big cells can be labelled too.
+constexpr int kLabelTargets = 128;
+
+__device__ __forceinline__ int label_target(int t, int n) {
+  return n <= kLabelTargets ? t : static_cast<int>((static_cast<int64_t>(t) * n) / kLabelTargets);
+}
 __global__ void __launch_bounds__(128) k_labels(int64_t K, const int2 *__restrict__ pairs,
                                                 const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
                                                 const double *__restrict__ X, const double *__restrict__ Y,
@@ -122,10 +173,11 @@ __global__ void __launch_bounds__(128) k_labels(int64_t K, const int2 *__restric
   int A = pairs[k].x, B = pairs[k].y;
   const double *CA = loc_pair + (2 * k) * 20, *CB = loc_pair + (2 * k + 1) * 20;
   const int bA = begin[A], nA = count[A], bB = begin[B], nB = count[B];
+  const int tA = min(nA, kLabelTargets), tB = min(nB, kLabelTargets);
   double errA = 0.0, errB = 0.0;
-  for (int t = threadIdx.x; t < nA + nB; t += blockDim.x) {
-    const bool onA = t < nA;
-    const int i = onA ? bA + t : bB + (t - nA);
+  for (int t = threadIdx.x; t < tA + tB; t += blockDim.x) {
+    const bool onA = t < tA;
+    const int i = onA ? bA + label_target(t, nA) : bB + label_target(t - tA, nB);
     const int c = onA ? A : B;
     const double *C = onA ? CA : CB;
     const int ob = onA ? bB : bA, on = onA ? nB : nA;
@@ -178,7 +230,7 @@ __global__ void __launch_bounds__(128) k_labels(int64_t K, const int2 *__restric
     for (int j = bB; j < bB + nB; ++j) mB += Mb[j];
     const double dx = Z[3 * A] - Z[3 * B], dy = Z[3 * A + 1] - Z[3 * B + 1], dz = Z[3 * A + 2] - Z[3 * B + 2];
     const double r2 = dx * dx + dy * dy + dz * dz;
-    const double eA = sqrt(sh[0][0] / nA) / (mB / r2), eB = sqrt(sh[1][0] / nB) / (mA / r2);
+    const double eA = sqrt(sh[0][0] / tA) / (mB / r2), eB = sqrt(sh[1][0] / tB) / (mA / r2);
     // below 1e-12 of the monopole scale the error is FP64 rounding noise
     label[k] = static_cast<float>(fmax(log10(fmax(eA, eB) + 1e-300), -12.0));
   }
@@ -329,6 +381,89 @@ __device__ void forward16(const NetSmem &s, const float (*xs)[kF], Act &act) {
   y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
   act.y[0] = y0 + s.b4;
   act.y[1] = y1 + s.b4;
+}
+
+// Inference forward with the tensor-core B fragments of all three layers in
+// registers (loaded once per warp, reused for every group of 16 samples); the
+// biases and the output layer stay in shared memory.  Same arithmetic as
+// forward16, without keeping the pre-activations.
+struct NetRegs {
+  uint32_t w1[8];
+  uint32_t w2[4][8][2];
+  uint32_t w3[4][8][2];
+};
+
+__device__ __forceinline__ void load_regs(const NetSmem &s, NetRegs &r) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int n = 0; n < 8; ++n) r.w1[n] = *reinterpret_cast<const uint32_t *>(&s.W1[8 * n + g][2 * t]);
+#pragma unroll
+  for (int kb = 0; kb < 4; ++kb)
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      bfrag_fwd(s.W2, kb, n, g, t, r.w2[kb][n][0], r.w2[kb][n][1]);
+      bfrag_fwd(s.W3, kb, n, g, t, r.w3[kb][n][0], r.w3[kb][n][1]);
+    }
+}
+
+__device__ __forceinline__ void infer16(const NetSmem &s, const NetRegs &r, const float (*xs)[kF], float &y0,
+                                        float &y1) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  uint32_t a[4];
+  a[0] = pack_bf16(xs[g][2 * t], xs[g][2 * t + 1]);
+  a[1] = pack_bf16(xs[g + 8][2 * t], xs[g + 8][2 * t + 1]);
+  a[2] = 0u;
+  a[3] = 0u;
+  float h[8][4];
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    mma16816(c, a, r.w1[n], 0u);
+    const float bb0 = s.b1[8 * n + 2 * t], bb1 = s.b1[8 * n + 2 * t + 1];
+    h[n][0] = silu(c[0] + bb0);
+    h[n][1] = silu(c[1] + bb1);
+    h[n][2] = silu(c[2] + bb0);
+    h[n][3] = silu(c[3] + bb1);
+  }
+#pragma unroll
+  for (int L = 1; L < 3; ++L) {
+    const float *bias = L == 1 ? s.b2 : s.b3;
+    uint32_t A[4][4];
+#pragma unroll
+    for (int kb = 0; kb < 4; ++kb) {
+      A[kb][0] = pack_bf16(h[2 * kb][0], h[2 * kb][1]);
+      A[kb][1] = pack_bf16(h[2 * kb][2], h[2 * kb][3]);
+      A[kb][2] = pack_bf16(h[2 * kb + 1][0], h[2 * kb + 1][1]);
+      A[kb][3] = pack_bf16(h[2 * kb + 1][2], h[2 * kb + 1][3]);
+    }
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kb = 0; kb < 4; ++kb) {
+        if (L == 1) mma16816(c, A[kb], r.w2[kb][n][0], r.w2[kb][n][1]);
+        else mma16816(c, A[kb], r.w3[kb][n][0], r.w3[kb][n][1]);
+      }
+      const float bb0 = bias[8 * n + 2 * t], bb1 = bias[8 * n + 2 * t + 1];
+      h[n][0] = silu(c[0] + bb0);
+      h[n][1] = silu(c[1] + bb1);
+      h[n][2] = silu(c[2] + bb0);
+      h[n][3] = silu(c[3] + bb1);
+    }
+  }
+  float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    const float w0 = s.w4[8 * n + 2 * t], w1 = s.w4[8 * n + 2 * t + 1];
+    s0 += h[n][0] * w0 + h[n][1] * w1;
+    s1 += h[n][2] * w0 + h[n][3] * w1;
+  }
+  s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+  s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+  s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+  s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+  y0 = s0 + s.b4;
+  y1 = s1 + s.b4;
 }
 
 // inference over K samples of raw features
@@ -538,66 +673,93 @@ __global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__re
 // ---------------------------------------------------------------------------
 // scoring of the walk's candidate pairs
 // ---------------------------------------------------------------------------
-// score[t] = predicted log10 normalised error for the frontier pairs in the
-// band the network decides: A != B, not accepted by the criterion at the
+// Scoring of the walk's frontier in two steps.  k_band_select marks the
+// pairs the network decides: A != B, not accepted by the criterion at the
 // floor theta_lo, and accepted by it at theta_hi <= 1 (theta_hi = 1 is the
-// safety bound |Z_A - Z_B| >= R_A + R_B); +inf for every other pair.  The
-// criteria are the walk's own exactly rounded FP64 expressions.  Persistent
-// blocks: the network is staged in shared memory once per block, then each
-// warp scores groups of 16 pairs, skipping the network for groups without a
-// pair in the band.
-__global__ void __launch_bounds__(128) k_walk_scores(int64_t nf, const int2 *__restrict__ front,
+// safety bound |Z_A - Z_B| >= R_A + R_B), with the walk's own criterion (FP32
+// filter, exact FP64 for close calls).  It sets score = +inf for every pair
+// and appends the marked ones to a candidate list (warp-aggregated).  The
+// list's order varies from run to run, but a pair's score depends only on the
+// pair (the rows of a tensor-core product are independent), so the walk does
+// not.  k_walk_scores then runs the network on the candidates only.
+__global__ void k_band_select(int64_t nf, const int2 *__restrict__ front, const double4_32a *__restrict__ zr,
+                              const CellF *__restrict__ zf, double th_lo, double th_hi,
+                              float *__restrict__ score, int32_t *__restrict__ cand,
+                              unsigned *__restrict__ ncand) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  bool ok = false;
+  if (t < nf) {
+    score[t] = INFINITY;
+    const int A = front[t].x, B = front[t].y;
+    if (A != B) {
+      const float th2f_lo = static_cast<float>(th_lo) * static_cast<float>(th_lo);
+      const float th2f_hi = static_cast<float>(th_hi) * static_cast<float>(th_hi);
+      const CellF fa = zf[A], fb = zf[B];
+      int hi = separated_fast(fa, fb, th2f_hi);
+      if (hi < 0) hi = well_separated(zr[A], zr[B], th_hi);
+      if (hi) {
+        int lo = separated_fast(fa, fb, th2f_lo);
+        if (lo < 0) lo = well_separated(zr[A], zr[B], th_lo);
+        ok = !lo;
+      }
+    }
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, ok);
+  if (m == 0u) return;
+  unsigned base = 0;
+  if (lane == 0) base = atomicAdd(ncand, static_cast<unsigned>(__popc(m)));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (ok) cand[base + __popc(m & ((1u << lane) - 1u))] = static_cast<int32_t>(t);
+}
+
+// The network on the candidates, 16 per warp step; persistent blocks stage
+// the network in shared memory once, every warp then holds its tensor-core
+// fragments in registers.  The score is the predicted absolute error of the
+// pair relative to the field at each side, in log10: the network predicts
+// the larger side's error in units of the partner's monopole field M/r^2, so
+// side A's error is at most 10^pred M_B/r^2, side B's 10^pred M_A/r^2, and
+//   score = pred + log10 max(M_B / (r^2 |a_A|), M_A / (r^2 |a_B|)),
+// compared by the walk with log10 of the relative target.
+__global__ void __launch_bounds__(128) k_walk_scores(const int2 *__restrict__ front,
+                                                     const int32_t *__restrict__ cand,
+                                                     const unsigned *__restrict__ ncand,
                                                      const float *__restrict__ params,
-                                                     const double4_32a *__restrict__ zr, const CellF *__restrict__ zf,
-                                                     const float4 *__restrict__ cf, double th_lo, double th_hi,
-                                                     float *__restrict__ score) {
-  const float th2f_lo = static_cast<float>(th_lo) * static_cast<float>(th_lo);
-  const float th2f_hi = static_cast<float>(th_hi) * static_cast<float>(th_hi);
+                                                     const CellF *__restrict__ zf, const float4 *__restrict__ cf,
+                                                     const float *__restrict__ lga, float *__restrict__ score,
+                                                     unsigned long long *__restrict__ scored) {
   __shared__ NetSmem s;
   __shared__ float xs[4][16][kF];
-  __shared__ int cand[4][16];
+  __shared__ float adj[4][16];
   load_net(s, params);
   __syncthreads();
+  NetRegs wr;
+  load_regs(s, wr);
+  const int64_t K = *ncand;
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(scored, static_cast<unsigned long long>(K));
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2;
-  for (int64_t grp = static_cast<int64_t>(blockIdx.x) * 4 + w; grp * 16 < nf;
+  for (int64_t grp = static_cast<int64_t>(blockIdx.x) * 4 + w; grp * 16 < K;
        grp += static_cast<int64_t>(gridDim.x) * 4) {
     const int64_t base = grp * 16;
-    int ok = 0;
     if (lane < 16) {
-      const int64_t k = base + lane;
       float f[kF] = {0, 0, 0, 0, 0, 0, 0, 0};
-      if (k < nf) {
-        const int A = front[k].x, B = front[k].y;
-        if (A != B) {
-          // the walk's criterion at theta_hi and theta_lo (FP32 filter, FP64
-          // for close calls)
-          const CellF fa = zf[A], fb = zf[B];
-          int hi = separated_fast(fa, fb, th2f_hi);
-          if (hi < 0) hi = well_separated(zr[A], zr[B], th_hi);
-          if (hi) {
-            int lo = separated_fast(fa, fb, th2f_lo);
-            if (lo < 0) lo = well_separated(zr[A], zr[B], th_lo);
-            ok = !lo;
-          }
-          if (ok) pair_features(A, B, zf, cf, f);
-        }
+      float ad = 0.f;
+      if (base + lane < K) {
+        const int2 pr = front[cand[base + lane]];
+        pair_features(pr.x, pr.y, zf, cf, f);
+        const float l2r = 2.f * f[0];
+        ad = fmaxf(cf[pr.y].y - l2r - lga[pr.x], cf[pr.x].y - l2r - lga[pr.y]);
       }
-      cand[w][lane] = ok;
+      adj[w][lane] = ad;
 #pragma unroll
       for (int q = 0; q < kF; ++q) xs[w][lane][q] = (f[q] - s.mean[q]) * s.scale[q];
     }
-    const bool any = __any_sync(0xffffffffu, ok);
     __syncwarp();
-    float y0 = INFINITY, y1 = INFINITY;
-    if (any) {
-      Act act;
-      forward16(s, xs[w], act);
-      y0 = act.y[0];
-      y1 = act.y[1];
-    }
+    float y0, y1;
+    infer16(s, wr, xs[w], y0, y1);
     if ((lane & 3) == 0) {
-      if (base + g < nf) score[base + g] = cand[w][g] ? y0 : INFINITY;
-      if (base + g + 8 < nf) score[base + g + 8] = cand[w][g + 8] ? y1 : INFINITY;
+      if (base + g < K) score[cand[base + g]] = y0 + adj[w][g];
+      if (base + g + 8 < K) score[cand[base + g + 8]] = y1 + adj[w][g + 8];
     }
     __syncwarp();
   }
@@ -626,13 +788,35 @@ int cell_features(fmm_ctx *c) {
   return launched(c, "cell_features");
 }
 
+int field_estimate(fmm_ctx *c) {
+  const int64_t nc = c->sz.ncell;
+  // the deepest level with at most 2048 cells
+  int L = 0;
+  for (int l = 0; l <= c->sz.depth; ++l)
+    if (c->sz.lvl_off[l + 1] - c->sz.lvl_off[l] <= 2048) L = l;
+  AMFMM_TRY(ensure<float>(c, c->sel_lga, nc));
+  k_field_estimate<<<grid_for(nc, kFieldTile), kFieldTile, 0, c->stream>>>(
+      static_cast<int32_t>(nc), ptr<CellF>(c->walk_zf), ptr<double>(c->M), static_cast<int32_t>(c->sz.lvl_off[L]),
+      static_cast<int32_t>(c->sz.lvl_off[L + 1]), ptr<float>(c->sel_lga));
+  return launched(c, "field_estimate");
+}
+
 int walk_scores(fmm_ctx *c, int64_t nf, const int2 *front, float *score) {
-  // persistent: at most 8 blocks of 4 warps per SM
-  const int64_t need = (nf + 63) / 64;
-  const unsigned g = static_cast<unsigned>(std::min<int64_t>(need, static_cast<int64_t>(c->num_sms) * 8));
+  cudaStream_t st = c->stream;
+  AMFMM_TRY(ensure<int32_t>(c, c->sel_cand, nf));
+  unsigned *ncand = reinterpret_cast<unsigned *>(ptr<int64_t>(c->totals) + 11);
+  AMFMM_CUDA(c, cudaMemsetAsync(ncand, 0, sizeof(unsigned), st));
   const double lo = c->opts.theta, hi = c->sel_theta_max;
-  k_walk_scores<<<g, 128, 0, c->stream>>>(nf, front, ptr<float>(c->sel_params), ptr<double4_32a>(c->walk_zr),
-                                          ptr<CellF>(c->walk_zf), ptr<float4>(c->sel_cellfeat), lo, hi, score);
+  k_band_select<<<grid_for(nf, 256), 256, 0, st>>>(nf, front, ptr<double4_32a>(c->walk_zr),
+                                                    ptr<CellF>(c->walk_zf), lo, hi, score,
+                                                    ptr<int32_t>(c->sel_cand), ncand);
+  AMFMM_TRY(launched(c, "band_select"));
+  // persistent: at most 4 blocks of 4 warps per SM, fewer for a short frontier
+  const int64_t need = (nf + 63) / 64;
+  const unsigned g = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(c->num_sms) * 4)));
+  k_walk_scores<<<g, 128, 0, st>>>(front, ptr<int32_t>(c->sel_cand), ncand, ptr<float>(c->sel_params),
+                                   ptr<CellF>(c->walk_zf), ptr<float4>(c->sel_cellfeat), ptr<float>(c->sel_lga),
+                                   score, ptr<unsigned long long>(c->totals) + 10);
   return launched(c, "walk_scores");
 }
 

@@ -435,103 +435,6 @@ __global__ void k_internal_upward(int32_t c0, int32_t c1, const int32_t *__restr
   for (int k = 0; k < kMomStride; ++k) out[k] = p[k];
 }
 
-// The same level with eight lanes per cell, one per child slot: the loads of
-// all children are in flight together instead of one child after another.
-// S and M are still summed in octant order (every lane forms the same
-// sequence of correctly rounded additions, so Z is bit-identical to the
-// one-lane version), and the shifted child moments are added in child order.
-__global__ void k_internal_upward8(int32_t c0, int32_t c1, const int32_t *__restrict__ first_child,
-                                   const int32_t *__restrict__ nchild, double *__restrict__ S,
-                                   double *__restrict__ M, double *__restrict__ Z,
-                                   double *__restrict__ invM, double *__restrict__ mom) {
-  const int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  const int lane = threadIdx.x & 31, k = lane & 7, base = lane & ~7;
-  const int64_t cc = c0 + (g >> 3);
-  const bool live = cc < c1;
-  const int c = live ? static_cast<int>(cc) : c0;
-  const int nch = live ? nchild[c] : 0;
-  const int f = live ? first_child[c] : 0;
-  const bool has = k < nch;
-  const int ch = f + k;
-  double sx = 0.0, sy = 0.0, sz = 0.0, mc = 0.0;
-  if (has) {
-    sx = S[3 * ch];
-    sy = S[3 * ch + 1];
-    sz = S[3 * ch + 2];
-    mc = M[ch];
-  }
-  // octant-order sums (same operations as parent_com)
-  double tx = 0.0, ty = 0.0, tz = 0.0, tm = 0.0;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const double vx = __shfl_sync(0xffffffffu, sx, base + j), vy = __shfl_sync(0xffffffffu, sy, base + j);
-    const double vz = __shfl_sync(0xffffffffu, sz, base + j), vm = __shfl_sync(0xffffffffu, mc, base + j);
-    if (j < nch) {
-      tx = __dadd_rn(tx, vx);
-      ty = __dadd_rn(ty, vy);
-      tz = __dadd_rn(tz, vz);
-      tm = __dadd_rn(tm, vm);
-    }
-  }
-  // leaves (and idle groups) write nothing; every lane stays for the shuffles
-  const bool active = nch > 0;
-  const double zx = __ddiv_rn(tx, tm), zy = __ddiv_rn(ty, tm), zz = __ddiv_rn(tz, tm);
-  if (active && k == 0) {
-    S[3 * c] = tx;
-    S[3 * c + 1] = ty;
-    S[3 * c + 2] = tz;
-    M[c] = tm;
-    Z[3 * c] = zx;
-    Z[3 * c + 1] = zy;
-    Z[3 * c + 2] = zz;
-    invM[c] = 1.0 / tm;
-  }
-  // this child's moments shifted to Z (zero for an empty slot)
-  double p[kMomStride];
-#pragma unroll
-  for (int q = 0; q < kMomStride; ++q) p[q] = 0.0;
-  if (has) {
-    const double *q = mom + static_cast<int64_t>(ch) * kMomStride;
-    const double s[3] = {Z[3 * ch] - zx, Z[3 * ch + 1] - zy, Z[3 * ch + 2] - zz};
-    const double Mc = q[0];
-    const double Ms[3] = {Mc * s[0], Mc * s[1], Mc * s[2]};
-    const double Q[3][3] = {{q[4], q[5], q[6]}, {q[5], q[7], q[8]}, {q[6], q[8], q[9]}};
-#pragma unroll
-    for (int i = 0; i < 3; ++i) p[1 + i] = Ms[i];
-    const int qi[6] = {0, 0, 0, 1, 1, 2}, qj[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-    for (int t = 0; t < 6; ++t) p[4 + t] = Q[qi[t]][qj[t]] + Ms[qi[t]] * s[qj[t]];
-    const int oi[10] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 2};
-    const int oj[10] = {0, 0, 0, 1, 1, 2, 1, 1, 2, 2};
-    const int ok[10] = {0, 1, 2, 1, 2, 2, 1, 2, 2, 2};
-#pragma unroll
-    for (int t = 0; t < 10; ++t) {
-      const int i = oi[t], j = oj[t], l = ok[t];
-      p[10 + t] = q[10 + t] + (Q[i][j] * s[l] + Q[i][l] * s[j] + Q[j][l] * s[i]) + Ms[i] * s[j] * s[l];
-    }
-  }
-  // child-order sums; lane k keeps the coefficients q = k, k + 8, k + 16
-  double out[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-  for (int q = 1; q < kMomStride; ++q) {
-    double acc = 0.0;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const double v = __shfl_sync(0xffffffffu, p[q], base + j);
-      if (j < nch) acc += v;
-    }
-    if ((q & 7) == k) out[q >> 3] = acc;
-  }
-  if (!active) return;
-  double *o = mom + static_cast<int64_t>(c) * kMomStride;
-#pragma unroll
-  for (int u = 0; u < 3; ++u) {
-    const int q = k + 8 * u;
-    if (q == 0) o[0] = tm;
-    else if (q < kMomStride) o[q] = out[u];
-  }
-}
-
 // R_max^2 of every cell: for each level, each body's squared distance to the
 // centre of its cell at that level; a segmented warp maximum (bodies of one
 // cell are contiguous) and one atomicMax per segment on the bit pattern
@@ -755,7 +658,7 @@ int upward(fmm_ctx *c) {
   AMFMM_TRY(launched(c, "leaf_upward"));
   for (int lev = c->sz.depth - 1; lev >= 0; --lev) {
     const int64_t c0 = c->sz.lvl_off[lev], c1 = c->sz.lvl_off[lev + 1];
-    k_internal_upward8<<<grid_for(8 * (c1 - c0), 128), 128, 0, st>>>(
+    k_internal_upward<<<grid_for(c1 - c0, 128), 128, 0, st>>>(
         static_cast<int32_t>(c0), static_cast<int32_t>(c1), ptr<int32_t>(c->first_child),
         ptr<int32_t>(c->nchild), ptr<double>(c->S), ptr<double>(c->M), ptr<double>(c->Z),
         ptr<double>(c->invM), ptr<double>(c->mom));

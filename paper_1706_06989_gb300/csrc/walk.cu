@@ -337,7 +337,13 @@ int walk(fmm_ctx *c) {
   }
 
   AMFMM_TRY(pack_walk_cells(c));
-  if (c->sel_enabled) AMFMM_TRY(cell_features(c));
+  if (c->sel_enabled) {
+    if (c->sz.nsys != 1)
+      return set_error(c, FMM_EUNSUPPORTED, "the learned selector works on one system at a time");
+    AMFMM_TRY(cell_features(c));
+    AMFMM_TRY(field_estimate(c));
+    AMFMM_CUDA(c, cudaMemsetAsync(ptr<int64_t>(c->totals) + 10, 0, sizeof(int64_t), st));
+  }
   // one self pair per root: systems of a forest never interact
   const int64_t nsys = c->sz.nsys;
   if (nsys > static_cast<int64_t>(c->front[0].cap / sizeof(int2))) AMFMM_TRY(ensure<int2>(c, c->front[0], nsys));

@@ -44,7 +44,7 @@ class _Stats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("lo", ctypes.c_double * 3), ("scale", ctypes.c_double),
                 ("ms_tree", ctypes.c_float), ("ms_upward", ctypes.c_float), ("ms_walk", ctypes.c_float),
                 ("ms_m2l", ctypes.c_float), ("ms_p2p", ctypes.c_float), ("ms_reduce", ctypes.c_float),
-                ("ms_downward", ctypes.c_float)]
+                ("ms_downward", ctypes.c_float), ("n_scored", ctypes.c_int64)]
 
 
 def load() -> ctypes.CDLL:
@@ -118,6 +118,7 @@ class Stats:
     lo: tuple
     scale: float
     ms: dict
+    n_scored: int = 0
 
 
 class FMM:
@@ -378,7 +379,7 @@ class FMM:
         ms = {k: float(getattr(s, "ms_" + k)) for k in ("tree", "upward", "walk", "m2l", "p2p", "reduce",
                                                          "downward")}
         return Stats(s.n, s.ncell, s.nleaf, s.depth, s.n_m2l, s.n_p2p, s.n_self, s.p2p_body_pairs,
-                     s.launches, tuple(s.lo), s.scale, ms)
+                     s.launches, tuple(s.lo), s.scale, ms, s.n_scored)
 
     def export_keys(self):
         t = self._torch

@@ -47,12 +47,14 @@ def init_params(feat: np.ndarray, seed: int = 0) -> np.ndarray:
 
 
 def pair_samples(solver, x, y, z, m, thetas=(0.3, 0.5, 0.7, 1.0), per_theta: int = 200_000,
-                 max_work: float = 4e6, seed: int = 0):
+                 max_work: float = 1e8, seed: int = 0):
     """Features and labels of pairs accepted at the given opening angles.
 
     solver: an fmm.FMM (order 3, selector disabled); x, y, z, m: device
     tensors.  At most per_theta pairs per angle, drawn (seeded) among those
-    with n_A n_B <= max_work.  Returns (feat [K, 8], label [K]) on the device.
+    whose label costs at most max_work body pairs (a label sums at most 128
+    targets per side over every body of the partner).  Returns (feat [K, 8],
+    label [K]) on the device.
     """
     import torch
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -62,7 +64,8 @@ def pair_samples(solver, x, y, z, m, thetas=(0.3, 0.5, 0.7, 1.0), per_theta: int
         solver.solve(x, y, z, m)
         m2l, _, _ = solver.export_lists()
         cnt = solver.export_tree(geometry=False)["count"].to(torch.int64)
-        work = (cnt[m2l[:, 0].long()] * cnt[m2l[:, 1].long()]).cpu().numpy()
+        na, nb = cnt[m2l[:, 0].long()], cnt[m2l[:, 1].long()]
+        work = (na.clamp(max=128) * nb + nb.clamp(max=128) * na).cpu().numpy()
         ok = np.nonzero(work <= max_work)[0]
         if ok.size == 0:
             continue
