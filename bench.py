@@ -61,10 +61,6 @@ def _args():
                    help="leapfrog: two-Plummer binary, uniform KDK steps, momentum drift per step")
     p.add_argument("--lf-steps", type=int, default=200)
     p.add_argument("--sel-steps", type=int, default=3000)
-    p.add_argument("--sel-floor", type=float, default=0.4,
-                   help="theta of the plain criterion kept under the learned selector (band floor)")
-    p.add_argument("--sel-theta-max", type=float, default=0.7,
-                   help="upper edge of the band the learned selector decides")
     p.add_argument("--lf-variants", default="TC:mixed,UC:mixed,TC:fp64")
     return p.parse_args()
 
@@ -488,10 +484,16 @@ def _time_solves(solver, x, y, z, m, out, flush, reps=3):
     return statistics.median(ts)
 
 
-def _interp_time_at_error(curve, err):
-    """Time of the fixed-theta form at a given rms error, interpolated
-    linearly in (log error, log time) between neighbouring thetas."""
-    pts = sorted((c["rms_err"], c["ms"]) for c in curve)
+def _work(c):
+    """Algorithmic flops of a solve's interactions (M2L TC + P2P)."""
+    return M2L_FLOPS["TC"] * c["n_m2l"] + P2P_FLOPS_PER_BODY_PAIR * c["p2p_body_pairs"]
+
+
+def _interp_time_at_error(curve, err, key="ms"):
+    """Time (or, with key=_work, interaction work) of the fixed-theta form at
+    a given rms error, interpolated linearly in (log error, log value)
+    between neighbouring thetas."""
+    pts = sorted((c["rms_err"], key(c) if callable(key) else c[key]) for c in curve)
     for (e0, t0), (e1, t1) in zip(pts, pts[1:]):
         if e0 <= err <= e1 and e1 > e0:
             u = (np.log(err) - np.log(e0)) / (np.log(e1) - np.log(e0))
@@ -500,23 +502,23 @@ def _interp_time_at_error(curve, err):
 
 
 def run_selector(a):
-    """Learned pair selector.  Trained on pairs of the Plummer N = 2,000 and
-    N = 1,048,576 spheres accepted by the plain walk at theta in the band and
-    around it (labels: the method's own M2L errors against direct sums).
-    Applied, with theta_lo as the floor and theta_hi as the ceiling of the band
-    the network decides, to a Plummer sphere and to a Hernquist halo +
-    exponential disc, both N = 4,194,304.  The fixed-theta form is swept over
-    theta to give its time-error curve; the selector is compared with it at
-    equal rms force error (4,096 bodies against exact direct sums)."""
+    """Learned pair selector.  Trained on about 10M pairs of the Plummer
+    N = 2,000 and N = 1,048,576 spheres, accepted by the plain walk at
+    theta 0.35 .. 0.85 (labels: the method's own M2L errors against direct
+    sums).  Applied to a Plummer sphere and to a Hernquist halo + exponential
+    disc, both N = 4,194,304: the selector decides the pairs of a band
+    (theta_lo, theta_hi] by the predicted pair error relative to the field
+    at each side.  The fixed-theta form is swept over theta to give its
+    time-error curve; the selector is compared with it at equal rms force
+    error (4,096 bodies against exact direct sums)."""
     import torch
     from paper_1706_06989_gb300 import fmm, ics, selector
     dev = torch.device("cuda", 0)
-    lo, hi = a.sel_floor, a.sel_theta_max
     t0 = time.perf_counter()
     s = fmm.FMM(theta=0.5, n_crit=25, variant="TC", precision="fp64")
-    thetas = tuple(float(t) for t in np.round(np.linspace(lo, min(1.0, hi + 0.1), 5), 3))
+    thetas = (0.35, 0.425, 0.5, 0.575, 0.65, 0.75, 0.85)
     feats, labs = [], []
-    for b, per in ((ics.plummer(2000, seed=0), 200_000), (ics.plummer(1 << 20, seed=0), 2_000_000)):
+    for b, per in ((ics.plummer(2000, seed=0), 200_000), (ics.plummer(1 << 20, seed=0), 1_400_000)):
         x, y, z, m = (torch.from_numpy(v).to(dev) for v in (b.x, b.y, b.z, b.m))
         f, l = selector.pair_samples(s, x, y, z, m, thetas=thetas, per_theta=per, seed=3)
         feats.append(f)
@@ -527,6 +529,12 @@ def run_selector(a):
     t_train = time.perf_counter() - t0 - t_data
     s.close()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    # (rule, band, min_work, targets); the absolute rule and other bands
+    # were measured too and did worse (design notes)
+    settings = [("relative", (0.4, 0.7), 256, (-4.0, -3.5, -3.25, -3.0, -2.75, -2.5)),
+                ("relative", (0.45, 0.75), 256, (-4.0, -3.5, -3.25, -3.0, -2.75, -2.5)),
+                ("relative", (0.45, 0.75), 2048, (-3.5, -3.25, -3.0, -2.75)),
+                ("relative", (0.45, 0.75), 16384, (-3.5, -3.25, -3.0, -2.75))]
     evals = []
     for wname, b in (("plummer, N=4194304 (seed 0)", ics.plummer(4194304, seed=0)),
                      ("hernquist(a=1, 70%) + exponential disc (30%), N=4194304", ics.hernquist_disc(4194304, seed=0))):
@@ -536,40 +544,47 @@ def run_selector(a):
         out = tuple(torch.empty(b.n, dtype=torch.float64, device=dev) for _ in range(3))
         ref = torch.stack(ev.direct(x, y, z, m, tgd), 1)
 
-        def measure(theta, prec, tgt=None):
+        def measure(theta, prec, tgt=None, hi=None, rule="relative", min_work=256):
             ev.set_opts(theta=theta, precision=prec)
             if tgt is None:
                 ev.selector_set(None, 0.0, enable=False)
             else:
-                ev.selector_set(params, float(tgt), enable=True, theta_max=hi)
+                ev.selector_set(params, float(tgt), enable=True, theta_max=hi, rule=rule, min_work=min_work)
             ev.solve(x, y, z, m, out)
             st = ev.stats()
             return {"ms": _time_solves(ev, x, y, z, m, out, flush), "rms_err": _rms_err(ev, x, y, z, m, out, tgd, ref),
-                    "n_m2l": st.n_m2l, "p2p_body_pairs": st.p2p_body_pairs}
+                    "n_m2l": st.n_m2l, "p2p_body_pairs": st.p2p_body_pairs, "n_scored": st.n_scored}
 
         fp64 = measure(0.5, "fp64")
         curve = []
-        for th in np.round(np.arange(0.35, 0.751, 0.05), 3):
+        for th in np.round(np.arange(0.3, 0.751, 0.05), 3):
             r = measure(float(th), a.precision)
             r["theta"] = float(th)
             curve.append(r)
         base = next(c for c in curve if abs(c["theta"] - 0.5) < 1e-9)
         scan, best = [], None
-        for tgt in np.arange(-3.5, -0.99, 0.25):
-            r = measure(lo, a.precision, tgt)
-            r["log10_target"] = float(tgt)
-            r["theta_curve_ms_at_same_error"] = _interp_time_at_error(curve, r["rms_err"])
-            if r["theta_curve_ms_at_same_error"]:
-                r["gain_vs_theta_curve"] = r["theta_curve_ms_at_same_error"] / r["ms"]
-            if r["rms_err"] <= base["rms_err"] and (best is None or r["ms"] < best["ms"]):
-                best = r
-            scan.append(r)
+        for rule, (lo, hi), mw, targets in settings:
+            for tgt in targets:
+                r = measure(lo, a.precision, tgt, hi, rule, mw)
+                r.update({"rule": rule, "band": [lo, hi], "min_work": mw, "log10_target": float(tgt)})
+                r["theta_curve_ms_at_same_error"] = _interp_time_at_error(curve, r["rms_err"])
+                if r["theta_curve_ms_at_same_error"]:
+                    r["gain_vs_theta_curve"] = r["theta_curve_ms_at_same_error"] / r["ms"]
+                w = _interp_time_at_error(curve, r["rms_err"], key=_work)
+                if w:
+                    r["work_gain_vs_theta_curve"] = w / _work(r)
+                if r["rms_err"] <= base["rms_err"] and (best is None or r["ms"] < best["ms"]):
+                    best = r
+                scan.append(r)
         ev.selector_set(None, 0.0, enable=False)
-        evals.append({"workload": wname, "fp64_theta0.5": fp64, "theta_curve": curve,
-                      "selector_band": [lo, hi], "selector_scan": scan,
+        gains = [r["gain_vs_theta_curve"] for r in scan if "gain_vs_theta_curve" in r]
+        wgains = [r["work_gain_vs_theta_curve"] for r in scan if "work_gain_vs_theta_curve" in r]
+        evals.append({"workload": wname, "fp64_theta0.5": fp64, "theta_curve": curve, "selector_scan": scan,
                       "selector_best_at_error_of_theta0.5": best,
                       "speedup_vs_theta0.5_same_precision": (base["ms"] / best["ms"]) if best else None,
-                      "speedup_vs_plain_fp64_theta0.5": (fp64["ms"] / best["ms"]) if best else None})
+                      "speedup_vs_plain_fp64_theta0.5": (fp64["ms"] / best["ms"]) if best else None,
+                      "max_gain_vs_theta_curve": max(gains) if gains else None,
+                      "max_work_gain_vs_theta_curve": max(wgains) if wgains else None})
         ev.close()
         del x, y, z, m, out, ref
         torch.cuda.empty_cache()

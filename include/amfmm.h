@@ -190,21 +190,30 @@ int fmm_leapfrog(fmm_ctx *ctx, double *x, double *y, double *z, double *vx, doub
  * the same for B, and N_A + N_B; normalised as (f - mean) * scale. */
 int fmm_selector_nparams(void);
 
+/* Acceptance rules of the learned selector (see fmm_selector_set). */
+#define FMM_SEL_ABSOLUTE 0 /* predicted absolute pair error below the target */
+#define FMM_SEL_RELATIVE 1 /* ... below the target times the field at each side */
+
 /* Enables (enable = 1) or disables the selector for the following solves.
  * params: HOST, fmm_selector_nparams() floats.  With it, the opening
  * criterion at the context's theta still accepts what it accepts; a pair it
  * rejects but that the criterion at theta_max (theta < theta_max <= 1;
- * theta_max = 1 is the safety bound |Z_A - Z_B| >= R_A + R_B) accepts is
- * accepted when its predicted absolute error, relative to the field at each
- * side, is below 10^log10_target: the network predicts the larger side's
- * error e in units of the partner's monopole field, and the pair is accepted
- * when e max(M_B / (r^2 |a_A|), M_A / (r^2 |a_B|)) < 10^log10_target, with
- * |a| a per-cell estimate from the softened monopoles of one coarse level.
- * Every other pair is opened as usual.  The network only adds pairs, so the
- * interaction lists never grow beyond those of the plain criterion at theta.
- * One system per solve (fmm_solve_batch with the selector on returns
- * FMM_EUNSUPPORTED).  FMM_EINVAL if theta_max is outside (0, 1]. */
-int fmm_selector_set(fmm_ctx *ctx, const float *params, double log10_target, double theta_max, int enable);
+ * theta_max = 1 is the safety bound |Z_A - Z_B| >= R_A + R_B) accepts, and
+ * whose n_A n_B >= min_work, is scored: the network predicts the larger
+ * side's error e in units of the partner's monopole field, so side A's error
+ * is at most e M_B/r^2 and side B's e M_A/r^2.  The pair is accepted when
+ *   FMM_SEL_ABSOLUTE:  e max(M_A, M_B) / r^2 < 10^log10_target (G = 1), or
+ *   FMM_SEL_RELATIVE:  e max(M_B / (r^2 |a_A|), M_A / (r^2 |a_B|))
+ *                      < 10^log10_target,
+ * with |a| a per-cell estimate of the field from the softened monopoles of
+ * one coarse level.  Pairs below min_work are not scored (opening a pair of
+ * few bodies costs less than the network, about 18k flop).  Every other pair
+ * is opened as usual.  The network only adds pairs, so the interaction lists
+ * never grow beyond those of the plain criterion at theta.  One system per
+ * solve (fmm_solve_batch with the selector on returns FMM_EUNSUPPORTED).
+ * FMM_EINVAL if theta_max is outside (0, 1] or the rule is unknown. */
+int fmm_selector_set(fmm_ctx *ctx, const float *params, double log10_target, double theta_max, int64_t min_work,
+                     int rule, int enable);
 
 /* Training samples for K given cell pairs of the current tree (after
  * fmm_upward, order 3): pairs: device, K x 2 int32; feat: device, K x 8 raw

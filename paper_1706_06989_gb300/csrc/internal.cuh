@@ -94,6 +94,8 @@ struct fmm_ctx {
   bool sel_enabled = false;
   double sel_log10_target = -3.0;
   double sel_theta_max = 1.0;  // upper edge of the band the network decides
+  int64_t sel_min_work = 256;  // pairs with n_A n_B below this are left to the floor
+  int sel_rule = FMM_SEL_RELATIVE;  // acceptance rule of the learned selector
   // host-solve staging
   amfmm::DBuf hx, hy, hz, hm, hax, hay, haz;
 };

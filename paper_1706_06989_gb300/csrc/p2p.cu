@@ -85,6 +85,34 @@ __device__ __forceinline__ float3 offset32(const BodyF &b, const float4 zh, cons
                      (b.h.z - zh.z) + (b.l.z - zl.z));
 }
 
+// A column body as loaded: hi/lo floats in the mixed form, FP64 otherwise.
+template <class T>
+struct RawBody {
+  double x, y, z, m;
+};
+template <>
+struct RawBody<float> {
+  BodyF b;
+};
+
+template <class T>
+__device__ __forceinline__ RawBody<T> load_body(int j, bool valid, const BodyF *__restrict__ bodyf,
+                                                const double *__restrict__ X, const double *__restrict__ Y,
+                                                const double *__restrict__ Zb, const double *__restrict__ Mb) {
+  RawBody<T> r{};
+  if (valid) {
+    if constexpr (sizeof(T) == sizeof(float)) {
+      r.b = bodyf[j];
+    } else {
+      r.x = X[j];
+      r.y = Y[j];
+      r.z = Zb[j];
+      r.m = Mb[j];
+    }
+  }
+  return r;
+}
+
 template <class T>
 __global__ void __launch_bounds__(kWarps * 32) k_p2p(
     int32_t nleaf, int64_t n, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin,
@@ -133,26 +161,31 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
     for (int v = 0; v < 3 * nr; ++v) sm.acc[v][l] = T(0);
     __syncwarp();
     // columns: A's own bodies (one-sided, self) then the bodies of every
-    // partner leaf B with A < B, packed 32 to a step
+    // partner leaf B with A < B, packed 32 to a step.  Loads run ahead: the
+    // column entry two steps ahead, the body of the next step.
+    int2 colN = cb + l < ce ? cols[cb + l] : make_int2(0, -2);
+    RawBody<T> rbN = load_body<T>(colN.x, cb + l < ce, bodyf, X, Y, Zb, Mb);
+    int2 colNN = cb + 32 + l < ce ? cols[cb + 32 + l] : make_int2(0, -2);
     for (int c0 = cb; c0 < ce; c0 += 32) {
-      const int c = c0 + l;
-      const bool valid = c < ce;
-      int2 col = make_int2(0, -2);
+      const bool valid = c0 + l < ce;
+      const int2 col = colN;
+      const RawBody<T> rb = rbN;
+      colN = colNN;
+      rbN = load_body<T>(colN.x, c0 + 32 + l < ce, bodyf, X, Y, Zb, Mb);
+      colNN = c0 + 64 + l < ce ? cols[c0 + 64 + l] : make_int2(0, -2);
       T xj = T(0), yj = T(0), zj = T(0), mj = T(0);
       if (valid) {
-        col = cols[c];
         if constexpr (sizeof(T) == sizeof(float)) {
-          const BodyF b = bodyf[col.x];
-          const float3 o = offset32(b, zh, zl);
+          const float3 o = offset32(rb.b, zh, zl);
           xj = o.x;
           yj = o.y;
           zj = o.z;
-          mj = b.h.w;
+          mj = rb.b.h.w;
         } else {
-          xj = coord<T>(X[col.x], zx);
-          yj = coord<T>(Y[col.x], zy);
-          zj = coord<T>(Zb[col.x], zz);
-          mj = T(Mb[col.x]);
+          xj = rb.x;
+          yj = rb.y;
+          zj = rb.z;
+          mj = rb.m;
         }
       }
       const bool mutual = col.y >= 0;

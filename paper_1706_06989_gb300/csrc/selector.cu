@@ -683,16 +683,17 @@ __global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__re
 // pair (the rows of a tensor-core product are independent), so the walk does
 // not.  k_walk_scores then runs the network on the candidates only.
 __global__ void k_band_select(int64_t nf, const int2 *__restrict__ front, const double4_32a *__restrict__ zr,
-                              const CellF *__restrict__ zf, double th_lo, double th_hi,
-                              float *__restrict__ score, int32_t *__restrict__ cand,
-                              unsigned *__restrict__ ncand) {
+                              const CellF *__restrict__ zf, const int32_t *__restrict__ count,
+                              int64_t min_work, double th_lo, double th_hi, float *__restrict__ score,
+                              int32_t *__restrict__ cand, unsigned *__restrict__ ncand) {
   const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   const int lane = threadIdx.x & 31;
   bool ok = false;
   if (t < nf) {
     score[t] = INFINITY;
     const int A = front[t].x, B = front[t].y;
-    if (A != B) {
+    // a pair of few bodies costs less to open than to score
+    if (A != B && static_cast<int64_t>(count[A]) * count[B] >= min_work) {
       const float th2f_lo = static_cast<float>(th_lo) * static_cast<float>(th_lo);
       const float th2f_hi = static_cast<float>(th_hi) * static_cast<float>(th_hi);
       const CellF fa = zf[A], fb = zf[B];
@@ -748,7 +749,8 @@ __global__ void __launch_bounds__(128) k_walk_scores(const int2 *__restrict__ fr
         const int2 pr = front[cand[base + lane]];
         pair_features(pr.x, pr.y, zf, cf, f);
         const float l2r = 2.f * f[0];
-        ad = fmaxf(cf[pr.y].y - l2r - lga[pr.x], cf[pr.x].y - l2r - lga[pr.y]);
+        ad = lga ? fmaxf(cf[pr.y].y - l2r - lga[pr.x], cf[pr.x].y - l2r - lga[pr.y])
+                 : fmaxf(cf[pr.y].y, cf[pr.x].y) - l2r;
       }
       adj[w][lane] = ad;
 #pragma unroll
@@ -790,10 +792,13 @@ int cell_features(fmm_ctx *c) {
 
 int field_estimate(fmm_ctx *c) {
   const int64_t nc = c->sz.ncell;
-  // the deepest level with at most 2048 cells
+  // the coarse level: the last one before the first level with more than
+  // 2048 cells (deep levels can be small again, but hold only a dense core)
   int L = 0;
-  for (int l = 0; l <= c->sz.depth; ++l)
-    if (c->sz.lvl_off[l + 1] - c->sz.lvl_off[l] <= 2048) L = l;
+  for (int l = 0; l <= c->sz.depth; ++l) {
+    if (c->sz.lvl_off[l + 1] - c->sz.lvl_off[l] > 2048) break;
+    L = l;
+  }
   AMFMM_TRY(ensure<float>(c, c->sel_lga, nc));
   k_field_estimate<<<grid_for(nc, kFieldTile), kFieldTile, 0, c->stream>>>(
       static_cast<int32_t>(nc), ptr<CellF>(c->walk_zf), ptr<double>(c->M), static_cast<int32_t>(c->sz.lvl_off[L]),
@@ -808,14 +813,15 @@ int walk_scores(fmm_ctx *c, int64_t nf, const int2 *front, float *score) {
   AMFMM_CUDA(c, cudaMemsetAsync(ncand, 0, sizeof(unsigned), st));
   const double lo = c->opts.theta, hi = c->sel_theta_max;
   k_band_select<<<grid_for(nf, 256), 256, 0, st>>>(nf, front, ptr<double4_32a>(c->walk_zr),
-                                                    ptr<CellF>(c->walk_zf), lo, hi, score,
+                                                    ptr<CellF>(c->walk_zf), ptr<int32_t>(c->count), c->sel_min_work, lo, hi, score,
                                                     ptr<int32_t>(c->sel_cand), ncand);
   AMFMM_TRY(launched(c, "band_select"));
   // persistent: at most 4 blocks of 4 warps per SM, fewer for a short frontier
   const int64_t need = (nf + 63) / 64;
   const unsigned g = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(c->num_sms) * 4)));
   k_walk_scores<<<g, 128, 0, st>>>(front, ptr<int32_t>(c->sel_cand), ncand, ptr<float>(c->sel_params),
-                                   ptr<CellF>(c->walk_zf), ptr<float4>(c->sel_cellfeat), ptr<float>(c->sel_lga),
+                                   ptr<CellF>(c->walk_zf), ptr<float4>(c->sel_cellfeat),
+                                   c->sel_rule == FMM_SEL_RELATIVE ? ptr<float>(c->sel_lga) : nullptr,
                                    score, ptr<unsigned long long>(c->totals) + 10);
   return launched(c, "walk_scores");
 }
@@ -828,10 +834,13 @@ extern "C" {
 
 int fmm_selector_nparams(void) { return kNParams; }
 
-int fmm_selector_set(fmm_ctx *c, const float *params, double log10_target, double theta_max, int enable) {
+int fmm_selector_set(fmm_ctx *c, const float *params, double log10_target, double theta_max, int64_t min_work,
+                     int rule, int enable) {
   if (!c) return FMM_EINVAL;
   if (enable) {
     if (!params) return set_error(c, FMM_EINVAL, "NULL parameters");
+    if (rule != FMM_SEL_ABSOLUTE && rule != FMM_SEL_RELATIVE)
+      return set_error(c, FMM_EINVAL, "unknown selector rule %d", rule);
     if (!(theta_max > 0.0 && theta_max <= 1.0))
       return set_error(c, FMM_EINVAL, "theta_max must lie in (0, 1] (got %g)", theta_max);
     AMFMM_TRY(ensure<float>(c, c->sel_params, kNParams));
@@ -841,7 +850,11 @@ int fmm_selector_set(fmm_ctx *c, const float *params, double log10_target, doubl
   }
   c->sel_enabled = enable != 0;
   c->sel_log10_target = log10_target;
-  if (enable) c->sel_theta_max = theta_max;
+  if (enable) {
+    c->sel_theta_max = theta_max;
+    c->sel_min_work = min_work < 0 ? 0 : min_work;
+    c->sel_rule = rule;
+  }
   c->stage = kNone;
   return FMM_OK;
 }

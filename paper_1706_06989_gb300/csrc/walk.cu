@@ -341,7 +341,7 @@ int walk(fmm_ctx *c) {
     if (c->sz.nsys != 1)
       return set_error(c, FMM_EUNSUPPORTED, "the learned selector works on one system at a time");
     AMFMM_TRY(cell_features(c));
-    AMFMM_TRY(field_estimate(c));
+    if (c->sel_rule == FMM_SEL_RELATIVE) AMFMM_TRY(field_estimate(c));
     AMFMM_CUDA(c, cudaMemsetAsync(ptr<int64_t>(c->totals) + 10, 0, sizeof(int64_t), st));
   }
   // one self pair per root: systems of a forest never interact

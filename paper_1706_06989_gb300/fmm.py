@@ -26,6 +26,9 @@ _lock = threading.Lock()
 _lib = None
 
 
+SELECTOR_RULES = {"absolute": 0, "relative": 1}
+
+
 class FMMError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"[{code}] {msg}")
@@ -79,7 +82,7 @@ def load() -> ctypes.CDLL:
                 "fmm_leapfrog": [P, P, P, P, P, P, P, P, I64, D, I, P, P, P, P],
                 "fmm_solve_batch": [P, P, P, P, P, P, I, P, P, P],
                 "fmm_autotune_ncrit": [P, P, P, P, P, P, I, P, I, I, P, P, P, P, P],
-                "fmm_selector_set": [P, P, D, D, I],
+                "fmm_selector_set": [P, P, D, D, I64, I, I],
                 "fmm_selector_samples": [P, P, I64, P, P],
                 "fmm_mlp_forward": [P, P, P, I64, P],
                 "fmm_mlp_grad": [P, P, P, P, I64, P, P],
@@ -286,15 +289,18 @@ class FMM:
     def selector_nparams(self) -> int:
         return int(self.lib.fmm_selector_nparams())
 
-    def selector_set(self, params, log10_target: float, enable: bool = True, theta_max: float = 1.0):
-        """Learned selection in the band (theta, theta_max]: pairs there are
-        accepted when the network predicts a log10 error below log10_target."""
+    def selector_set(self, params, log10_target: float, enable: bool = True, theta_max: float = 1.0,
+                     min_work: int = 256, rule: str = "relative"):
+        """Learned selection in the band (theta, theta_max] for pairs with
+        n_A n_B >= min_work: accepted when the predicted pair error (absolute,
+        or relative to the field at each side) is below 10**log10_target."""
         import numpy as np
         p = np.ascontiguousarray(params, dtype=np.float32) if params is not None else None
         if enable and (p is None or p.shape[0] != self.selector_nparams()):
             raise ValueError("params must hold fmm_selector_nparams() floats")
         self._check(self.lib.fmm_selector_set(self._h, ctypes.c_void_p(p.ctypes.data) if p is not None else None,
-                                              float(log10_target), float(theta_max), int(bool(enable))),
+                                              float(log10_target), float(theta_max), int(min_work),
+                                              SELECTOR_RULES[rule], int(bool(enable))),
                     "fmm_selector_set")
 
     def selector_samples(self, pairs, labels: bool = True):

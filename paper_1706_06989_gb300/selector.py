@@ -6,9 +6,18 @@ library's kernels; this module only chooses which pairs to label, how the
 features are normalised and the initial weights.
 
 Labels are the method's own errors: for a cell pair (A, B) accepted at some
-opening angle, the rms over the bodies of A and B of the difference between
-the torque-corrected order-3 M2L acceleration and the direct A<->B sum,
-normalised by (M_A + M_B)/|r|^2, in log10 (see fmm_selector_samples).
+opening angle, per side the rms over its bodies of the difference between the
+torque-corrected order-3 M2L acceleration and the direct A<->B sum, in units
+of the partner's monopole field M/|r|^2; the label is log10 of the larger
+side (see fmm_selector_samples).
+
+Scale invariance.  A label does not change when every mass is multiplied by
+one factor, or every length by another (the error and the monopole field
+scale alike).  Two features carry an absolute scale, log10 |r| and log10 M,
+so systems of other N or other units would ask the network about masses and
+lengths it never saw.  Training therefore adds, for every sample, a copy
+whose log10 |r| is shifted by one random amount and whose two log10 M are
+shifted by another (same label): the network learns the invariance.
 """
 from __future__ import annotations
 
@@ -78,10 +87,32 @@ def pair_samples(solver, x, y, z, m, thetas=(0.3, 0.5, 0.7, 1.0), per_theta: int
     return torch.cat(feats), torch.cat(labs)
 
 
+LOG_R_SHIFT = (-2.0, 2.0)  # range of the random log10 length factor
+LOG_M_SHIFT = (-3.0, 1.0)  # range of the random log10 mass factor
+
+
+def augment_scales(feat, label, seed: int = 0):
+    """The samples plus one copy of each under a random change of length and
+    mass units (features 0 and 3, 4 shifted; labels unchanged)."""
+    import torch
+    g = torch.Generator(device=feat.device)
+    g.manual_seed(seed)
+    k = feat.shape[0]
+    dr = torch.empty(k, device=feat.device).uniform_(*LOG_R_SHIFT, generator=g)
+    dm = torch.empty(k, device=feat.device).uniform_(*LOG_M_SHIFT, generator=g)
+    aug = feat.clone()
+    aug[:, 0] += dr
+    aug[:, 3] += dm
+    aug[:, 4] += dm
+    return torch.cat([feat, aug]).contiguous(), torch.cat([label, label]).contiguous()
+
+
 def train(solver, feat, label, steps: int = 2000, batch: int = 4096, lr: float = 2e-3, seed: int = 0,
-          params: np.ndarray | None = None):
+          params: np.ndarray | None = None, scale_augment: bool = True):
     """Trains the network; returns (params as numpy float32, losses)."""
     import torch
+    if scale_augment:
+        feat, label = augment_scales(feat, label, seed)
     p0 = init_params(feat.cpu().numpy(), seed) if params is None else params
     dev = torch.as_tensor(p0, device=feat.device).contiguous()
     losses, _ = solver.selector_train(dev, feat, label, batch=batch, steps=steps, lr=lr, seed=seed)

@@ -154,7 +154,7 @@ def test_selector_extremes_reduce_to_the_plain_criterion():
     for b4, th_max, th in ((100.0, 1.0, 0.5), (-100.0, 1.0, 1.0), (-100.0, 0.7, 0.7)):
         p[M.NW - 1] = b4
         s = _solver(theta=0.5)
-        s.selector_set(p, log10_target=-3.0, enable=True, theta_max=th_max)
+        s.selector_set(p, log10_target=-3.0, enable=True, theta_max=th_max, min_work=0)
         s.solve(x, y, z, m)
         got = [t.cpu().numpy() for t in s.export_lists()]
         for g, r in zip(got, lists[th]):
