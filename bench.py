@@ -39,6 +39,12 @@ FP64_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 4
 FP32_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 256
 # algorithmic flops (FMA = 2, rsqrt = 1) per unit of work; derivation in the design doc
 M2L_FLOPS = {"UC": 174, "TC": 295, "TCO": 276}
+# DRAM traffic of the dominant kernel per unit it processes, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of a launch at the
+# bench workload (Plummer N = 1,048,576, theta = 0.5, TC): k_p2p<double>
+# read 360,217,344 B and wrote 836,056,832 B for 421,686,939 body pairs
+# (profiles/p2p_fp64_plummer1m.md).  Scaled by the units of the launch timed.
+TRAFFIC_PER_UNIT = {("p2p", "fp64"): (360217344 + 836056832) / 421686939}
 P2P_FLOPS_PER_BODY_PAIR = 25
 ORACLE_SAMPLE_N = 131072
 
@@ -247,8 +253,11 @@ def run_ours(a):
     else:
         dom, dom_ms, dom_flops = "p2p", p2p_ms, p2p_flops
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12
+    tpu = TRAFFIC_PER_UNIT.get((dom, a.precision))
+    traffic = tpu * (st.p2p_body_pairs if dom == "p2p" else st.n_m2l) if tpu else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / (peak / 1e12), "traffic": None,
+                "frac": achieved / (peak / 1e12), "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu capture scaled by units)" if traffic else None,
                 "peak_source": ("derived: 152 SMs x 2070 MHz x %s flop/clk/SM (FMA = 2)"
                                 % ("4 FP64" if a.precision == "fp64" else "256 FP32")),
                 "other": {"m2l": {"ms": m2l_ms, "tflops": m2l_flops / (m2l_ms * 1e-3) / 1e12 if m2l_ms > 0 else None},

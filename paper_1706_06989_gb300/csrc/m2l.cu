@@ -461,15 +461,20 @@ __global__ void k_m2l_reduce(int32_t ncell, const int32_t *__restrict__ off, con
       acc += static_cast<double>(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
     }
   } else {
+    // eight slot rows in flight per lane; the additions keep the slot order
+    for (; s + 8 <= s1; s += 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = static_cast<double>(__ldg(&slots[static_cast<int64_t>(s + u) * kLocStride + q]));
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc += v[u];
+    }
     for (; s + 4 <= s1; s += 4) {
-      const double v0 = static_cast<double>(slots[static_cast<int64_t>(s) * kLocStride + q]);
-      const double v1 = static_cast<double>(slots[static_cast<int64_t>(s + 1) * kLocStride + q]);
-      const double v2 = static_cast<double>(slots[static_cast<int64_t>(s + 2) * kLocStride + q]);
-      const double v3 = static_cast<double>(slots[static_cast<int64_t>(s + 3) * kLocStride + q]);
-      acc += v0;
-      acc += v1;
-      acc += v2;
-      acc += v3;
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = static_cast<double>(__ldg(&slots[static_cast<int64_t>(s + u) * kLocStride + q]));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc += v[u];
     }
   }
   for (; s < s1; ++s) acc += static_cast<double>(slots[static_cast<int64_t>(s) * kLocStride + q]);

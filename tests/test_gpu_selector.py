@@ -161,3 +161,8 @@ def test_selector_extremes_reduce_to_the_plain_criterion():
             assert np.array_equal(g, r), (b4, th_max, th)
     with pytest.raises(Exception):
         s.selector_set(p, log10_target=-3.0, enable=True, theta_max=1.5)
+    # an unknown acceptance rule is refused at the C boundary
+    import ctypes
+    from paper_1706_06989_gb300 import fmm
+    rc = s.lib.fmm_selector_set(s._h, ctypes.c_void_p(p.ctypes.data), -3.0, 1.0, 0, 7, 1)
+    assert rc == fmm.FMM_EINVAL
