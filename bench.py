@@ -63,7 +63,7 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-other", action="store_true", help="skip timing the other precision form")
-    p.add_argument("--experiment", choices=["none", "leapfrog", "ensemble", "selector"], default="none",
+    p.add_argument("--experiment", choices=["none", "leapfrog", "ensemble", "selector", "orders"], default="none",
                    help="leapfrog: two-Plummer binary, uniform KDK steps, momentum drift per step")
     p.add_argument("--lf-steps", type=int, default=200)
     p.add_argument("--sel-steps", type=int, default=3000)
@@ -605,10 +605,42 @@ def run_selector(a):
                       "evaluations": evals}), flush=True)
 
 
+def run_orders(a):
+    """Expansion order P = 3, 4, 5 (App. A), FP64, on a Plummer sphere of
+    N = 262,144 (theta = 0.5, TC): time per solve and rms force error against
+    exact direct sums on 2,048 bodies."""
+    import torch
+    from paper_1706_06989_gb300 import fmm, ics
+    dev = torch.device("cuda", 0)
+    b = ics.plummer(262144, seed=0)
+    x, y, z, m = (torch.from_numpy(v).to(dev) for v in (b.x, b.y, b.z, b.m))
+    tg = torch.as_tensor(ics.error_subset(b.n, 2048, seed=1), device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    s = fmm.FMM(theta=0.5, n_crit=25, variant="TC", precision="fp64")
+    ref = torch.stack(s.direct(x, y, z, m, tg), 1)
+    rows = []
+    for P in (3, 4, 5):
+        sp = fmm.FMM(theta=0.5, n_crit=25, variant="TC", precision="fp64", order_P=P)
+        out = tuple(torch.empty(b.n, dtype=torch.float64, device=dev) for _ in range(3))
+        for _ in range(3):
+            sp.solve(x, y, z, m, out)
+        ms = _time_solves(sp, x, y, z, m, out, flush, reps=5)
+        g = torch.stack(out, 1)[tg]
+        rel = torch.linalg.norm(g - ref, dim=1) / torch.linalg.norm(ref, dim=1)
+        fb, tb = sp.balance(x, y, z, m, *out)
+        rows.append({"order_P": P, "ms": ms, "bodies_per_s": b.n / (ms / 1e3),
+                     "rms_err": float(torch.sqrt(torch.mean(rel * rel))), "force_balance": fb, "torque_balance": tb})
+        sp.close()
+    print(json.dumps({"experiment": "orders", "workload": "plummer_n262144_theta0.5_ncrit25_tc_fp64", "results": rows}), flush=True)
+
+
 def main():
     a = _args()
     if a.experiment == "selector":
         run_selector(a)
+        return
+    if a.experiment == "orders":
+        run_orders(a)
         return
     if a.experiment == "leapfrog":
         run_leapfrog(a)

@@ -37,6 +37,7 @@ struct Sizes {
   int nsys = 1;                  // independent systems (roots) in the forest
   double lo[3] = {0, 0, 0}, scale = 0;
   int64_t p2p_body_pairs = 0;
+  int64_t p2p_items = 0;         // near-field work items (chunks of the leaves' column streams)
   std::vector<int64_t> lvl_off;  // cells of level l are [lvl_off[l], lvl_off[l+1])
 };
 
@@ -84,10 +85,11 @@ struct fmm_ctx {
   amfmm::DBuf ekey[2], eval[2], m2l_pos, m2l_off, m2l_slots, cell32;
   // P2P grouping
   amfmm::DBuf pkey[2], pval[2], p2p_A, p2p_offA, p2p_offB, p2p_pos, p2p_poff, p2p_len,
-      p2p_slots, p2p_colOff, p2p_cols, p2p_nb, p2p_pre, p2p_bodyf;
+      p2p_slots, p2p_colOff, p2p_cols, p2p_nb, p2p_pre, p2p_bodyf, p2p_items, p2p_itemOff, p2p_extraOff,
+      p2p_extra;
   // scan / sort scratch; `totals` holds small device results (1 KiB):
   // [0,16) scan totals, [64,72) near-field body-pair count, [80,88) selector-scored pairs, [88,92) selector candidates, [96,104) slot total,
-  // [128,132) near-field column total
+  // [128,140) near-field column, work-item and extra-partial totals
   amfmm::DBuf scan_tmp, sort_hist, totals, diag;
   // learned pair selector
   amfmm::DBuf sel_params, sel_cellfeat, sel_cand, sel_lga, sel_scratch, sel_part, sel_score, sel_grad, sel_perm, sel_xb, sel_yb;

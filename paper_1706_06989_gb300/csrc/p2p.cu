@@ -115,17 +115,22 @@ __device__ __forceinline__ RawBody<T> load_body(int j, bool valid, const BodyF *
 
 template <class T>
 __global__ void __launch_bounds__(kWarps * 32) k_p2p(
-    int32_t nleaf, int64_t n, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin,
+    int32_t nitem, int64_t n, const int4 *__restrict__ items, const int32_t *__restrict__ begin,
     const int32_t *__restrict__ count, const double *__restrict__ Zc, const double *__restrict__ X,
     const double *__restrict__ Y, const double *__restrict__ Zb, const double *__restrict__ Mb,
-    const int32_t *__restrict__ colOff, const int2 *__restrict__ cols, double *__restrict__ near,
+    const int2 *__restrict__ cols, double *__restrict__ near, double *__restrict__ extra,
     T *__restrict__ slots, const BodyF *__restrict__ bodyf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   P2PSmem<T> &sm = reinterpret_cast<P2PSmem<T> *>(smem_raw)[w];
   const int q = blockIdx.x * kWarps + w;
-  if (q >= nleaf) return;
-  const int L = leaves[q];
+  if (q >= nitem) return;
+  // work item: leaf, column range; w < 0 marks the leaf's first chunk (which
+  // owns the near-field sums of the leaf), w >= 0 the offset of a later
+  // chunk's A-side partials in `extra`
+  const int4 it = items[q];
+  const int L = it.x;
+  const bool first = it.w < 0;
   const int bA = begin[L], nA = count[L];
   const double zx = Zc[3 * L], zy = Zc[3 * L + 1], zz = Zc[3 * L + 2];
   float4 zh = make_float4(0.f, 0.f, 0.f, 0.f), zl = zh;
@@ -133,11 +138,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
     zh = make_float4(static_cast<float>(zx), static_cast<float>(zy), static_cast<float>(zz), 0.f);
     zl = make_float4(static_cast<float>(zx - zh.x), static_cast<float>(zy - zh.y), static_cast<float>(zz - zh.z), 0.f);
   }
-  const int cb = colOff[L], ce = colOff[L + 1];
-  for (int t = l; t < nA; t += 32) {
-    near[bA + t] = 0.0;
-    near[n + bA + t] = 0.0;
-    near[2 * n + bA + t] = 0.0;
+  const int cb = it.y, ce = it.z;
+  if (first) {
+    for (int t = l; t < nA; t += 32) {
+      near[bA + t] = 0.0;
+      near[n + bA + t] = 0.0;
+      near[2 * n + bA + t] = 0.0;
+    }
   }
   __syncwarp();
   for (int r0 = 0; r0 < nA; r0 += kRows) {
@@ -273,9 +280,77 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
 #pragma unroll 8
         for (int t = 0; t < 32; ++t) s += static_cast<double>(sm.acc[v][t]);
       }
-      near[static_cast<int64_t>(v % 3) * n + bA + r0 + v / 3] += s;
+      if (first) near[static_cast<int64_t>(v % 3) * n + bA + r0 + v / 3] += s;
+      else extra[it.w + 3 * (r0 + v / 3) + v % 3] = s;
     }
     __syncwarp();
+  }
+}
+
+// A leaf whose column stream was split adds the A-side partials of its later
+// chunks, in chunk order, once every chunk is done (one thread per body).
+__global__ void k_p2p_chunks(int32_t nleaf, int64_t n, const int32_t *__restrict__ leaves,
+                             const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+                             const int32_t *__restrict__ itemOff, const int4 *__restrict__ items,
+                             const double *__restrict__ extra, double *__restrict__ near) {
+  const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int l = threadIdx.x & 31;
+  if (q >= nleaf) return;
+  const int i0 = itemOff[q], i1 = itemOff[q + 1];
+  if (i1 - i0 < 2) return;
+  const int L = leaves[q];
+  const int bA = begin[L], nA = count[L];
+  for (int r = l; r < nA; r += 32) {
+    double a0 = near[bA + r], a1 = near[n + bA + r], a2 = near[2 * n + bA + r];
+    for (int k = i0 + 1; k < i1; ++k) {
+      const double *e = extra + items[k].w + 3 * r;
+      a0 += e[0];
+      a1 += e[1];
+      a2 += e[2];
+    }
+    near[bA + r] = a0;
+    near[n + bA + r] = a1;
+    near[2 * n + bA + r] = a2;
+  }
+}
+
+// Work items: the column stream of a leaf is cut into chunks of at most
+// kChunk columns (the first chunk also holds all of the leaf's own bodies, so
+// that the one-sided self sums stay in one warp).  One warp per chunk keeps a
+// leaf that the walk paired with millions of bodies (a large sparse leaf next
+// to a dense region) from serialising the kernel.
+constexpr int kChunk = 16384;
+
+__device__ __forceinline__ int chunks_of(int ncol, int nself) {
+  const int first = max(kChunk, nself);
+  return ncol <= first ? 1 : 1 + (ncol - first + kChunk - 1) / kChunk;
+}
+
+__global__ void k_item_counts(int32_t nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ count,
+                              const int32_t *__restrict__ colOff, int32_t *__restrict__ nitems,
+                              int32_t *__restrict__ nextra) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nleaf) return;
+  const int L = leaves[q];
+  const int k = chunks_of(colOff[L + 1] - colOff[L], count[L]);
+  nitems[q] = k;
+  nextra[q] = (k - 1) * 3 * count[L];
+}
+
+__global__ void k_item_fill(int32_t nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ count,
+                            const int32_t *__restrict__ colOff, const int32_t *__restrict__ itemOff,
+                            const int32_t *__restrict__ extraOff, int4 *__restrict__ items) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nleaf) return;
+  const int L = leaves[q];
+  const int cb = colOff[L], ce = colOff[L + 1], nA = count[L];
+  const int k = chunks_of(ce - cb, nA);
+  const int first = max(kChunk, nA);
+  int o = itemOff[q];
+  items[o] = make_int4(L, cb, min(ce, cb + first), -1);
+  for (int j = 1; j < k; ++j) {
+    const int c0 = cb + first + (j - 1) * kChunk;
+    items[o + j] = make_int4(L, c0, min(ce, c0 + kChunk), extraOff[q] + (j - 1) * 3 * nA);
   }
 }
 
@@ -420,12 +495,20 @@ int launch_p2p(fmm_ctx *c) {
     AMFMM_CUDA(c, cudaFuncSetAttribute(k_p2p<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
     attr_set = true;
   }
-  k_p2p<T><<<grid_for(nleaf, kWarps), kWarps * 32, shm, c->stream>>>(
-      nleaf, n, ptr<int32_t>(c->leaves), ptr<int32_t>(c->begin), ptr<int32_t>(c->count),
+  const int32_t nitem = static_cast<int32_t>(c->sz.p2p_items);
+  k_p2p<T><<<grid_for(nitem, kWarps), kWarps * 32, shm, c->stream>>>(
+      nitem, n, ptr<int4>(c->p2p_items), ptr<int32_t>(c->begin), ptr<int32_t>(c->count),
       ptr<double>(c->Z), ptr<double>(c->X), ptr<double>(c->Y), ptr<double>(c->Zb), ptr<double>(c->Mb),
-      ptr<int32_t>(c->p2p_colOff), ptr<int2>(c->p2p_cols), ptr<double>(c->near),
+      ptr<int2>(c->p2p_cols), ptr<double>(c->near), ptr<double>(c->p2p_extra),
       static_cast<T *>(c->p2p_slots.p), sizeof(T) == sizeof(float) ? ptr<BodyF>(c->p2p_bodyf) : nullptr);
-  return launched(c, "p2p");
+  AMFMM_TRY(launched(c, "p2p"));
+  if (nitem > nleaf) {
+    k_p2p_chunks<<<grid_for(static_cast<int64_t>(nleaf) * 32, 256), 256, 0, c->stream>>>(
+        nleaf, n, ptr<int32_t>(c->leaves), ptr<int32_t>(c->begin), ptr<int32_t>(c->count),
+        ptr<int32_t>(c->p2p_itemOff), ptr<int4>(c->p2p_items), ptr<double>(c->p2p_extra), ptr<double>(c->near));
+    AMFMM_TRY(launched(c, "p2p_chunks"));
+  }
+  return FMM_OK;
 }
 
 template <class T>
@@ -511,10 +594,31 @@ int p2p_prepare(fmm_ctx *c) {
   k_p2p_work<<<grid_for(K + nleaf, 256), 256, 0, st>>>(K, ptr<int2>(c->p2p_A), nleaf, ptr<int32_t>(c->leaves),
                                                        ptr<int32_t>(c->count), stat);
   AMFMM_TRY(launched(c, "p2p_work"));
+  // work items: chunks of the column streams
+  AMFMM_TRY(ensure<int32_t>(c, c->p2p_itemOff, nleaf + 1));
+  AMFMM_TRY(ensure<int32_t>(c, c->p2p_extraOff, nleaf + 1));
+  int32_t *itemOff = ptr<int32_t>(c->p2p_itemOff), *extraOff = ptr<int32_t>(c->p2p_extraOff);
+  // totals: [32] columns, [33] work items, [34] extra partials (int32 slots)
+  int32_t *itot = ptr<int32_t>(c->totals) + 33, *etot = ptr<int32_t>(c->totals) + 34;
+  int32_t *icnt = cnt, *ecnt = ptr<int32_t>(c->flag);  // free scratch of >= nleaf + 1
+  AMFMM_CUDA(c, cudaMemsetAsync(icnt + nleaf, 0, sizeof(int32_t), st));
+  AMFMM_CUDA(c, cudaMemsetAsync(ecnt + nleaf, 0, sizeof(int32_t), st));
+  k_item_counts<<<grid_for(nleaf, 256), 256, 0, st>>>(nleaf, ptr<int32_t>(c->leaves), ptr<int32_t>(c->count),
+                                                      colOff, icnt, ecnt);
+  AMFMM_TRY(launched(c, "p2p_item_counts"));
+  AMFMM_TRY(exclusive_scan_i32(c, icnt, itemOff, nleaf + 1, itot));
+  AMFMM_TRY(exclusive_scan_i32(c, ecnt, extraOff, nleaf + 1, etot));
   int32_t *hc = reinterpret_cast<int32_t *>(h + 1);
-  AMFMM_CUDA(c, cudaMemcpyAsync(hc, ctot, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  AMFMM_CUDA(c, cudaMemcpyAsync(hc, ctot, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   AMFMM_CUDA(c, cudaStreamSynchronize(st));
   const int64_t nslot = h[0], ncol = hc[0];
+  const int64_t nitem = hc[1], nextra = hc[2];
+  c->sz.p2p_items = nitem;
+  AMFMM_TRY(ensure<int4>(c, c->p2p_items, nitem + 1));
+  AMFMM_TRY(ensure<double>(c, c->p2p_extra, nextra + 1));
+  k_item_fill<<<grid_for(nleaf, 256), 256, 0, st>>>(nleaf, ptr<int32_t>(c->leaves), ptr<int32_t>(c->count), colOff,
+                                                    itemOff, extraOff, ptr<int4>(c->p2p_items));
+  AMFMM_TRY(launched(c, "p2p_item_fill"));
   if (nslot + 3 > 0x7fffffffLL) return set_error(c, FMM_EUNSUPPORTED, "too many near-field slots (%lld)", (long long)nslot);
   AMFMM_TRY(ensure_bytes(c, c->p2p_slots, static_cast<size_t>(nslot + 3) * (fp32 ? sizeof(float) : sizeof(double))));
   AMFMM_TRY(ensure<int2>(c, c->p2p_cols, ncol + 1));

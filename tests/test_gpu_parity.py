@@ -315,3 +315,31 @@ def test_lists_when_the_walk_outgrows_its_buffers():
     x, y, z, m = _dev(b)
     a2 = torch.stack(s.solve(x, y, z, m), 1).cpu().numpy()
     assert np.array_equal(a, a2)
+
+
+_CHUNK_REF = {}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_long_column_streams_are_split(precision):
+    """At a small opening angle every leaf sums directly with most others, so
+    its column stream runs to tens of thousands of bodies and is cut into
+    chunks of 16,384 columns handled by separate warps (the later chunks'
+    A-side partials are added in chunk order afterwards).  The accelerations
+    must still match the oracle."""
+    b = ics.uniform_cube(40000, seed=12)
+    s, a = _solve(b, theta=0.05, precision=precision)
+    st = s.stats()
+    # mean column stream of a leaf (body pairs / leaves / mean leaf size) beyond one chunk
+    assert st.p2p_body_pairs / st.nleaf / (b.n / st.nleaf) > 16384
+    if "ref" not in _CHUNK_REF:
+        _CHUNK_REF["ref"] = oracle.Oracle(b.x, b.y, b.z, b.m, 0.05, 25).accel("TC")
+    ref = _CHUNK_REF["ref"]
+    dev = _rel_dev(a, ref)
+    if precision == "fp64":
+        assert dev.max() <= 1e-12
+    else:
+        assert np.sqrt(np.mean(dev ** 2)) <= 1e-6
+    x, y, z, m = _dev(b)
+    a2 = torch.stack(s.solve(x, y, z, m), 1).cpu().numpy()
+    assert np.array_equal(a, a2)
