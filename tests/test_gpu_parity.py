@@ -343,3 +343,22 @@ def test_long_column_streams_are_split(precision):
     x, y, z, m = _dev(b)
     a2 = torch.stack(s.solve(x, y, z, m), 1).cpu().numpy()
     assert np.array_equal(a, a2)
+
+
+@pytest.mark.parametrize("theta,n_crit", [(1.0, 25), (0.5, 1), (0.5, 64), (0.7, 5000)])
+def test_opening_angle_and_leaf_size_extremes(theta, n_crit):
+    """theta at its largest (Sec. 2 allows 0 < theta <= 1), one body per leaf,
+    large leaves, and a tree that is a single leaf: tree, lists and FP64
+    accelerations against the oracle."""
+    b = ics.plummer(3000, seed=13)
+    s, a = _solve(b, theta=theta, n_crit=n_crit)
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, theta, n_crit)
+    _compare_tree(s, o)
+    m2l, p2p, slf = s.export_lists()
+    om2l, op2p, oslf = o.lists()
+    assert np.array_equal(_canon_pairs(m2l.cpu().numpy()), _canon_pairs(om2l))
+    assert np.array_equal(_canon_pairs(p2p.cpu().numpy()), _canon_pairs(op2p))
+    assert np.array_equal(np.sort(slf.cpu().numpy()), np.sort(oslf))
+    assert _rel_dev(a, o.accel("TC")).max() <= 1e-12
+    if n_crit >= b.n:
+        assert s.stats().ncell == 1
