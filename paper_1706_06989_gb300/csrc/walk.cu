@@ -108,7 +108,8 @@ struct GenState {
 };
 
 constexpr int kGenItems = 4;
-constexpr int kGenTile = kBlock * kGenItems;
+constexpr int kGenBlock = 256;  // threads of a generation block (128: 1.29 ms, 512: 1.21 ms, 256: 1.16 ms per 1M solve)
+constexpr int kGenTile = kGenBlock * kGenItems;
 constexpr long long kSpinLimit = 1LL << 22;
 
 __device__ __forceinline__ int4 ld_volatile4(const int4 *p) {
@@ -128,7 +129,7 @@ __device__ __forceinline__ void st_volatile4(int4 *p, int4 v) {
 // pass, decoupled look-back), and the outputs are written in frontier order.
 // Any write beyond a buffer's capacity is skipped and flagged; the host then
 // grows the buffers and runs the generation again.
-__global__ void __launch_bounds__(kBlock) k_walk_gen(
+__global__ void __launch_bounds__(kGenBlock) k_walk_gen(
     int64_t nf, const int2 *__restrict__ front, const int2 *__restrict__ nl, const double4_32a *__restrict__ zr,
     const CellF *__restrict__ zf, double theta, const float *__restrict__ score, float target, const int32_t *__restrict__ first_child,
     int2 *__restrict__ next, int64_t cap_next, int2 *__restrict__ m2l, int64_t m2l_base, int64_t cap_m2l,
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kBlock) k_walk_gen(
     int *__restrict__ flag, int4 *__restrict__ agg, int4 *__restrict__ inc) {
   __shared__ unsigned s_place;
   const float th2f = static_cast<float>(theta) * static_cast<float>(theta);
-  __shared__ int4 s_warp[kBlock / 32];
+  __shared__ int4 s_warp[kGenBlock / 32];
   __shared__ int4 s_prefix;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   if (t == 0) s_place = atomicAdd(&gs->ticket, 1u) - ticket_base;
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(kBlock) k_walk_gen(
   int4 before = make_int4(incl.x - mine.x, incl.y - mine.y, incl.z - mine.z, incl.w - mine.w);
   int4 block_total = make_int4(0, 0, 0, 0);
 #pragma unroll
-  for (int q = 0; q < kBlock / 32; ++q) {
+  for (int q = 0; q < kGenBlock / 32; ++q) {
     if (q < w) before = add4(before, s_warp[q]);
     block_total = add4(block_total, s_warp[q]);
   }
@@ -383,7 +384,7 @@ int walk(fmm_ctx *c) {
       const int64_t cap_next = static_cast<int64_t>(c->front[cur ^ 1].cap / sizeof(int2));
       c->walk_epoch = (c->walk_epoch + 1) & 0x3fffffffu;
       if (c->walk_epoch == 0) c->walk_epoch = 1;
-      k_walk_gen<<<nb, kBlock, 0, st>>>(
+      k_walk_gen<<<nb, kGenBlock, 0, st>>>(
           nf, ptr<int2>(c->front[cur]), ptr<int2>(c->walk_nl), ptr<double4_32a>(c->walk_zr),
           ptr<CellF>(c->walk_zf), c->theta, score,
           static_cast<float>(c->sel_log10_target), ptr<int32_t>(c->first_child), ptr<int2>(c->front[cur ^ 1]),
