@@ -177,38 +177,6 @@ __global__ void __launch_bounds__(kBlock) k_m2l64(int64_t K, const int2 *__restr
   }
 }
 
-// Mixed form: reads the FP32 copy of the cell data (kCell32 floats per cell:
-// Z as hi/lo float pairs, M, 1/M, Q, O).  r = Z_A - Z_B is formed from the
-// pairs, (hi_A - hi_B) + (lo_A - lo_B), accurate to FP32 relative to |r|.
-template <int VARIANT>
-__global__ void __launch_bounds__(kBlock) k_m2l32(int64_t K, const int2 *__restrict__ pairs,
-                                                   const float *__restrict__ cell32,
-                                                   const int32_t *__restrict__ pos, float *__restrict__ slots) {
-  const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (k >= K) return;
-  const int A = pairs[k].x, B = pairs[k].y;
-  float a[kCell32], b[kCell32];
-  const float4 *pa = reinterpret_cast<const float4 *>(cell32 + static_cast<int64_t>(A) * kCell32);
-  const float4 *pb = reinterpret_cast<const float4 *>(cell32 + static_cast<int64_t>(B) * kCell32);
-#pragma unroll
-  for (int u = 0; u < kCell32 / 4; ++u) {
-    const float4 va = pa[u], vb = pb[u];
-    a[4 * u] = va.x; a[4 * u + 1] = va.y; a[4 * u + 2] = va.z; a[4 * u + 3] = va.w;
-    b[4 * u] = vb.x; b[4 * u + 1] = vb.y; b[4 * u + 2] = vb.z; b[4 * u + 3] = vb.w;
-  }
-  float CA[kLocStride], CB[kLocStride];
-  const float r[3] = {(a[0] - b[0]) + (a[3] - b[3]), (a[1] - b[1]) + (a[4] - b[4]), (a[2] - b[2]) + (a[5] - b[5])};
-  m2l_pair<float, VARIANT>(r, a[6], b[6], a[7], b[7], a + 8, b + 8, a + 14, b + 14, CA, CB);
-  CA[19] = CB[19] = 0.f;
-  float *sa = slots + static_cast<int64_t>(pos[2 * k]) * kLocStride;
-  float *sb = slots + static_cast<int64_t>(pos[2 * k + 1]) * kLocStride;
-#pragma unroll
-  for (int q = 0; q < kLocStride; q += 4) {
-    *reinterpret_cast<float4 *>(sa + q) = make_float4(CA[q], CA[q + 1], CA[q + 2], CA[q + 3]);
-    *reinterpret_cast<float4 *>(sb + q) = make_float4(CB[q], CB[q + 1], CB[q + 2], CB[q + 3]);
-  }
-}
-
 // One side of the same interaction: the local of a target cell T from a
 // source cell S, with r = Z_T - Z_S.  Written for T = A it is the C^A of
 // m2l_pair; for T = B it is C^B, because every term of C^B is the C^A form
@@ -428,57 +396,52 @@ __global__ void k_inverse(int64_t E, const uint32_t *__restrict__ sval, int32_t 
   if (s < E) pos[sval[s]] = static_cast<int32_t>(s);
 }
 
-// Every cell sums its slots in sorted (pair index) order: one warp per cell,
-// lane q < 20 owns coefficient q, so each slot is read as one contiguous
-// 160-byte (FP64) or 80-byte (FP32) row.  Loads run ahead; the additions keep
-// the slot order.
-template <class T>
-__global__ void k_m2l_reduce(int32_t ncell, const int32_t *__restrict__ off, const T *__restrict__ slots,
-                             double *__restrict__ loc) {
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int q = threadIdx.x & 31;
-  if (c >= ncell || q >= kLocStride) return;
-  const int s0 = off[c], s1 = off[c + 1];
-  double acc = 0.0;
-  int s = s0;
-  if (sizeof(T) == sizeof(float)) {
-    // FP32 slots: pairwise sums of 32 in FP32, accumulated in FP64
-    for (; s + 32 <= s1; s += 32) {
-      T g[4];
+// Every cell sums its FP64 slots (kLocStride = 20 doubles per slot, in the
+// stable order of the sort): one warp per cell reads the cell's slot rows as
+// one flat array, 32 consecutive doubles per load, so every lane is busy and
+// every load is two full 128-byte lines.  Element e of the block belongs to
+// coefficient e mod 20; lane l meets, at its j-th load, coefficient
+// (l + 32 j) mod 20, which repeats with period 5 (32 = 12 mod 20 and
+// 5 x 12 = 60 = 0 mod 20), so every lane keeps five partial sums (phase
+// u = j mod 5).  The partials of a coefficient are then added by one lane
+// in a fixed order (phase, then lane).
+constexpr int kRedWarps = 8;
+
+__global__ void __launch_bounds__(kRedWarps * 32) k_m2l_reduce(int32_t ncell, const int32_t *__restrict__ off,
+                                                               const double *__restrict__ slots,
+                                                               double *__restrict__ loc) {
+  __shared__ double part[kRedWarps][5][32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int c = blockIdx.x * kRedWarps + w;
+  if (c >= ncell) return;  // a whole warp: no block-wide synchronisation below
+  const int64_t e0 = static_cast<int64_t>(off[c]) * kLocStride, e1 = static_cast<int64_t>(off[c + 1]) * kLocStride;
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  int64_t e = e0 + l;
+  // whole periods of 5 x 32 elements: five independent loads in flight
+  for (; e + 4 * 32 < e1; e += 5 * 32) {
+    double v[5];
 #pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        T v[8];
+    for (int u = 0; u < 5; ++u) v[u] = __ldg(&slots[e + 32 * u]);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = slots[static_cast<int64_t>(s + 8 * h + u) * kLocStride + q];
-        g[h] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
-      }
-      acc += static_cast<double>((g[0] + g[1]) + (g[2] + g[3]));
-    }
-    for (; s + 8 <= s1; s += 8) {
-      T v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = slots[static_cast<int64_t>(s + u) * kLocStride + q];
-      acc += static_cast<double>(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
-    }
-  } else {
-    // eight slot rows in flight per lane; the additions keep the slot order
-    for (; s + 8 <= s1; s += 8) {
-      double v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = static_cast<double>(__ldg(&slots[static_cast<int64_t>(s + u) * kLocStride + q]));
-#pragma unroll
-      for (int u = 0; u < 8; ++u) acc += v[u];
-    }
-    for (; s + 4 <= s1; s += 4) {
-      double v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = static_cast<double>(__ldg(&slots[static_cast<int64_t>(s + u) * kLocStride + q]));
-#pragma unroll
-      for (int u = 0; u < 4; ++u) acc += v[u];
-    }
+    for (int u = 0; u < 5; ++u) acc[u] += v[u];
   }
-  for (; s < s1; ++s) acc += static_cast<double>(slots[static_cast<int64_t>(s) * kLocStride + q]);
-  loc[static_cast<int64_t>(c) * kLocStride + q] = acc;
+#pragma unroll
+  for (int u = 0; u < 5; ++u)
+    if (e + 32 * u < e1) acc[u] += __ldg(&slots[e + 32 * u]);
+#pragma unroll
+  for (int u = 0; u < 5; ++u) part[w][u][l] = acc[u];
+  __syncwarp();
+  if (l < kLocStride) {
+    // lanes holding coefficient q at phase u: l = (q - 12 u) mod 20, and that + 20
+    double s = 0.0;
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+      const int r = ((l - 12 * u) % 20 + 20) % 20;
+      s += part[w][u][r];
+      if (r + 20 < 32) s += part[w][u][r + 20];
+    }
+    loc[static_cast<int64_t>(c) * kLocStride + l] = s;
+  }
 }
 
 int launch_m2l64(fmm_ctx *c, int64_t K) {
@@ -509,21 +472,6 @@ int launch_m2l32_gather(fmm_ctx *c) {
     case FMM_UC: k_m2l32_gather<FMM_UC><<<g, kGatherWarps * 32, 0, st>>>(nc, off, partner, c32, loc); break;
     case FMM_TC: k_m2l32_gather<FMM_TC><<<g, kGatherWarps * 32, 0, st>>>(nc, off, partner, c32, loc); break;
     default: k_m2l32_gather<FMM_TCO><<<g, kGatherWarps * 32, 0, st>>>(nc, off, partner, c32, loc); break;
-  }
-  return launched(c, "m2l");
-}
-
-int launch_m2l32(fmm_ctx *c, int64_t K) {
-  const int2 *pairs = ptr<int2>(c->m2l);
-  const unsigned g = grid_for(K, kBlock);
-  const float *c32 = ptr<float>(c->cell32);
-  const int32_t *pos = ptr<int32_t>(c->m2l_pos);
-  float *slots = ptr<float>(c->m2l_slots);
-  cudaStream_t st = c->stream;
-  switch (c->opts.variant) {
-    case FMM_UC: k_m2l32<FMM_UC><<<g, kBlock, 0, st>>>(K, pairs, c32, pos, slots); break;
-    case FMM_TC: k_m2l32<FMM_TC><<<g, kBlock, 0, st>>>(K, pairs, c32, pos, slots); break;
-    default: k_m2l32<FMM_TCO><<<g, kBlock, 0, st>>>(K, pairs, c32, pos, slots); break;
   }
   return launched(c, "m2l");
 }
@@ -584,7 +532,6 @@ int m2l_run(fmm_ctx *c) {
   if (K == 0) return FMM_OK;
   if (c->opts.order_P != 3) return m2l_general(c);
   if (m2l_gathered(c)) return launch_m2l32_gather(c);
-  if (c->opts.precision == FMM_MIXED) return launch_m2l32(c, K);
   return launch_m2l64(c, K);
 }
 
@@ -598,13 +545,8 @@ int m2l_reduce(fmm_ctx *c) {
   }
   if (m2l_gathered(c)) return FMM_OK;  // the gather kernel wrote every local
   int32_t *off = ptr<int32_t>(c->m2l_off);
-  const unsigned g = grid_for(nc * 32, 256);
-  if (c->opts.precision == FMM_MIXED)
-    k_m2l_reduce<float><<<g, 256, 0, st>>>(static_cast<int32_t>(nc), off, ptr<float>(c->m2l_slots),
-                                           ptr<double>(c->loc));
-  else
-    k_m2l_reduce<double><<<g, 256, 0, st>>>(static_cast<int32_t>(nc), off, ptr<double>(c->m2l_slots),
-                                            ptr<double>(c->loc));
+  k_m2l_reduce<<<grid_for(nc * 32, kRedWarps * 32), kRedWarps * 32, 0, st>>>(
+      static_cast<int32_t>(nc), off, ptr<double>(c->m2l_slots), ptr<double>(c->loc));
   return launched(c, "m2l_reduce");
 }
 
