@@ -16,7 +16,6 @@ namespace amfmm {
 namespace {
 
 __device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
-__device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
 
 #include "expansion_gen.cuh"
 

@@ -62,8 +62,6 @@ template <class T>
 __device__ __forceinline__ T coord(double v, double z);
 template <>
 __device__ __forceinline__ double coord<double>(double v, double) { return v; }
-template <>
-__device__ __forceinline__ float coord<float>(double v, double z) { return static_cast<float>(v - z); }
 
 // Mixed form: bodies and the leaf centre as hi + lo floats, so an offset
 // (x_hi - z_hi) + (x_lo - z_lo) is formed with FP32 operations only (FP64
@@ -496,11 +494,8 @@ int launch_p2p(fmm_ctx *c) {
   const int64_t n = c->sz.n;
   const int32_t nleaf = static_cast<int32_t>(c->sz.nleaf);
   const size_t shm = kWarps * sizeof(P2PSmem<T>);
-  static bool attr_set = false;  // per T instantiation
-  if (!attr_set) {
-    AMFMM_CUDA(c, cudaFuncSetAttribute(k_p2p<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
-    attr_set = true;
-  }
+  // per function and device, so set on every launch (a host-side call)
+  AMFMM_CUDA(c, cudaFuncSetAttribute(k_p2p<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
   const int32_t nitem = static_cast<int32_t>(c->sz.p2p_items);
   k_p2p<T><<<grid_for(nitem, kWarps), kWarps * 32, shm, c->stream>>>(
       nitem, n, ptr<int4>(c->p2p_items), ptr<int32_t>(c->begin), ptr<int32_t>(c->count),

@@ -899,11 +899,8 @@ int fmm_mlp_grad(fmm_ctx *c, const float *params, const float *feat, const float
   float *part = ptr<float>(c->sel_part);
   float *lpart = part + static_cast<size_t>(nblk) * kNWeights;
   const size_t shm = sizeof(TrainSmem);
-  static bool attr = false;
-  if (!attr) {
-    AMFMM_CUDA(c, cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
-    attr = true;
-  }
+  // per function and device, so set on every launch (a host-side call)
+  AMFMM_CUDA(c, cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
   k_mlp_grad<<<nblk, 128, shm, c->stream>>>(B, params, feat, label, part, lpart);
   AMFMM_TRY(launched(c, "mlp_grad"));
   k_grad_reduce<<<grid_for(kNWeights, 256), 256, 0, c->stream>>>(nblk, part, lpart, B, grad, loss);
