@@ -82,6 +82,27 @@ def _dist():
     return ws, rank, local
 
 
+def job_throughput(total_s: float, n_per_rank: int, steps: int, ws: int, device=None):
+    """Whole-job bodies/s over `ws` replicas: every rank ran `steps` timed
+    solves of `n_per_rank` bodies in `total_s` seconds between barriers; the
+    slowest rank's time counts (maximum over ranks).  Returns (value,
+    slowest seconds).  With ws > 1 this is a collective on the default
+    process group (NCCL on the GPUs; gloo in the CPU tests)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as tdist
+        t = torch.tensor([total_s], dtype=torch.float64, device=device)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_s = float(t.item())
+    return ws * n_per_rank * steps / total_s, total_s
+
+
+def replica_seed(rank: int) -> int:
+    """Each rank solves its own Plummer replica, seeded by its rank (a single
+    solve is not sharded: replicas only)."""
+    return rank
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -200,7 +221,7 @@ def run_ours(a):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    b = ics.plummer(a.n, seed=rank)  # one independent replica per rank
+    b = ics.plummer(a.n, seed=replica_seed(rank))  # one independent replica per rank
     x, y, z, m = (torch.from_numpy(v).to(dev) for v in (b.x, b.y, b.z, b.m))
     out = tuple(torch.empty(a.n, dtype=torch.float64, device=dev) for _ in range(3))
     stream = torch.cuda.current_stream()
@@ -234,12 +255,7 @@ def run_ours(a):
     t_wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = ws * a.n * a.steps / total_s
+    value, total_s = job_throughput(sum(step_ms) / 1e3, a.n, a.steps, ws, dev)
     st = solver.stats()
 
     # roofline of the dominant interaction kernel (alu bound, FP64 or FP32)
@@ -279,12 +295,8 @@ def run_ours(a):
             t0 = time.perf_counter()
             solver.solve_host(*hb, out=ho)
             es.append(time.perf_counter() - t0)
-        etot = sum(es)
-        if dist:
-            t = torch.tensor([etot], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            etot = float(t.item())
-        e2e = {"value": ws * a.n * a.steps / etot, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * a.n,
+        e2e_value, etot = job_throughput(sum(es), a.n, a.steps, ws, dev)
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * a.n,
                "d2h_bytes_per_step": 3 * 8 * a.n, "ms_per_step": 1e3 * etot / a.steps}
 
     # accuracy of this solve: rms relative force error against exact direct
