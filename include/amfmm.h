@@ -244,6 +244,15 @@ int fmm_mlp_adam(fmm_ctx *ctx, float *params, float *m, float *v, const float *g
 int fmm_selector_train(fmm_ctx *ctx, float *params, float *adam, const float *X, const float *y, int64_t n,
                        int batch, int steps, float lr, unsigned long long seed, float *loss_out);
 
+/* ---- test hook (no counterpart in the paper) ------------------------------ */
+/* Exercises the bounded wait of the walk's single-pass scan: launches one
+ * walk generation of an empty frontier whose only block is told to wait for
+ * a predecessor that does not exist.  The wait gives up after its poll
+ * limit (about a second), the block writes nothing but its own scan record,
+ * and the call returns FMM_ETIMEOUT; the context stays usable (the next call
+ * must be fmm_build_tree or fmm_solve).  Synchronises the stream. */
+int fmm_debug_walk_wait_timeout(fmm_ctx *ctx);
+
 /* ---- a10 diagnostics (Sec. 3) ---------------------------------------------- */
 
 /* Exact accelerations of nt target bodies by direct summation over all n

@@ -4,11 +4,13 @@
 // selections driven by an error estimate (Dehnen 2014): every accepted pair
 // still interacts mutually, so force and torque stay balanced.  Here the
 // estimate is a small network: 8 pair features -> 3 x 64 SiLU -> 1, the
-// predicted log10 of the pair's normalised M2L error.  In the walk the
-// opening criterion at theta keeps deciding, except in a band: a pair that the
-// criterion rejects at theta but accepts at theta_max <= 1 (theta_max = 1 is
-// the safety bound |Z_A - Z_B| >= R_A,max + R_B,max) is accepted when the
-// prediction is below a target.
+// predicted log10 of the pair's M2L error in units of the partner's monopole
+// field (the worse side).  In the walk the opening criterion at theta keeps
+// deciding, except in a band: a pair that the criterion rejects at theta but
+// accepts at theta_max <= 1 (theta_max = 1 is the safety bound |Z_A - Z_B| >=
+// R_A,max + R_B,max), and that holds enough bodies to be worth scoring, is
+// accepted when its predicted error -- absolute, or relative to an estimate
+// of the field at each side -- is below a target.
 //
 // Network arithmetic: BF16 inputs and weights on the tensor cores
 // (mma.sync m16n8k16, FP32 accumulation); biases, SiLU and the output layer in

@@ -428,3 +428,57 @@ int walk(fmm_ctx *c) {
 }
 
 }  // namespace amfmm
+
+using namespace amfmm;
+
+// Test hook for the bounded wait of the walk's look-back (no counterpart in
+// the paper): one generation of an empty frontier is launched with a ticket
+// base one below the counter, so its only block takes place 1 and waits for
+// place 0, which no block holds.  The wait gives up after kSpinLimit polls,
+// the block skips its writes, and the call must return FMM_ETIMEOUT with the
+// context still usable.  Every access stays inside buffers of two places.
+extern "C" int fmm_debug_walk_wait_timeout(fmm_ctx *c) {
+  if (!c) return FMM_EINVAL;
+  cudaStream_t st = c->stream;
+  if (c->walk_state.cap < sizeof(GenState)) {
+    AMFMM_TRY(ensure_bytes(c, c->walk_state, sizeof(GenState)));
+    AMFMM_CUDA(c, cudaMemsetAsync(c->walk_state.p, 0, sizeof(GenState), st));
+    c->walk_ticket = 0;
+  }
+  const size_t lb_bytes = 2 * (sizeof(int) + 2 * sizeof(int4)) + 64;
+  if (c->walk_lb.cap < lb_bytes) {
+    AMFMM_TRY(ensure_bytes(c, c->walk_lb, lb_bytes));
+    AMFMM_CUDA(c, cudaMemsetAsync(c->walk_lb.p, 0, c->walk_lb.cap, st));
+  }
+  const size_t nbc = (c->walk_lb.cap - 64) / (sizeof(int) + 2 * sizeof(int4));
+  int4 *agg = static_cast<int4 *>(c->walk_lb.p);
+  int4 *inc = agg + nbc;
+  int *flg = reinterpret_cast<int *>(inc + nbc);
+  AMFMM_TRY(ensure<int2>(c, c->front[0], 1));
+  AMFMM_TRY(ensure<int2>(c, c->front[1], 1));
+  AMFMM_TRY(ensure<int2>(c, c->walk_nl, 1));
+  AMFMM_TRY(ensure<double4_32a>(c, c->walk_zr, 1));
+  AMFMM_TRY(ensure<CellF>(c, c->walk_zf, 1));
+  AMFMM_TRY(ensure<int32_t>(c, c->first_child, 1));
+  GenState *gs = static_cast<GenState *>(c->walk_state.p);
+  AMFMM_CUDA(c, cudaMemsetAsync(&gs->status, 0, sizeof(int), st));
+  c->walk_epoch = (c->walk_epoch + 1) & 0x3fffffffu;
+  if (c->walk_epoch == 0) c->walk_epoch = 1;
+  // nf = 0 and every capacity 0: nothing is read or written but the
+  // look-back records of places 0 and 1
+  k_walk_gen<<<1, kGenBlock, 0, st>>>(0, ptr<int2>(c->front[0]), ptr<int2>(c->walk_nl), ptr<double4_32a>(c->walk_zr),
+                                      ptr<CellF>(c->walk_zf), 0.5, nullptr, 0.f, ptr<int32_t>(c->first_child),
+                                      ptr<int2>(c->front[1]), 0, nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, 0, gs,
+                                      c->walk_ticket - 1u, c->walk_epoch, 2u, flg, agg, inc);
+  c->walk_ticket += 1;
+  AMFMM_TRY(launched(c, "walk_gen_wait_test"));
+  GenState *h = static_cast<GenState *>(c->hpin);
+  AMFMM_CUDA(c, cudaMemcpyAsync(h, gs, sizeof(GenState), cudaMemcpyDeviceToHost, st));
+  AMFMM_CUDA(c, cudaStreamSynchronize(st));
+  const int status = h->status;
+  AMFMM_CUDA(c, cudaMemsetAsync(&gs->status, 0, sizeof(int), st));
+  c->stage = kNone;
+  if (status & 2) return set_error(c, FMM_ETIMEOUT, "walk: a block waited too long for its predecessor");
+  return FMM_OK;
+}
+

@@ -83,6 +83,7 @@ def load() -> ctypes.CDLL:
                 "fmm_solve_batch": [P, P, P, P, P, P, I, P, P, P],
                 "fmm_autotune_ncrit": [P, P, P, P, P, P, I, P, I, I, P, P, P, P, P],
                 "fmm_selector_set": [P, P, D, D, I64, I, I],
+                "fmm_debug_walk_wait_timeout": [P],
                 "fmm_selector_samples": [P, P, I64, P, P],
                 "fmm_mlp_forward": [P, P, P, I64, P],
                 "fmm_mlp_grad": [P, P, P, P, I64, P, P],
@@ -358,6 +359,10 @@ class FMM:
                                           *(_dptr(a) for a in acc), _dptr(mom) if record else None),
                     "fmm_leapfrog")
         return acc, mom
+
+    def debug_walk_wait_timeout(self) -> int:
+        """Return code of fmm_debug_walk_wait_timeout (FMM_ETIMEOUT expected)."""
+        return int(self.lib.fmm_debug_walk_wait_timeout(self._h))
 
     # ---- diagnostics (Sec. 3) ---------------------------------------------------
     def direct(self, x, y, z, m, targets):

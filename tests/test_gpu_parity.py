@@ -362,3 +362,18 @@ def test_opening_angle_and_leaf_size_extremes(theta, n_crit):
     assert _rel_dev(a, o.accel("TC")).max() <= 1e-12
     if n_crit >= b.n:
         assert s.stats().ncell == 1
+
+
+def test_bounded_wait_returns_timeout_and_context_survives():
+    """The walk's look-back waits for earlier blocks with a poll limit.  The
+    test hook makes a block wait for a block that does not exist: the call
+    must return FMM_ETIMEOUT (not hang), and a solve on the same context must
+    still match the oracle."""
+    from paper_1706_06989_gb300 import fmm
+    b = ics.plummer(2000, seed=14)
+    s = _solver(theta=0.5)
+    assert s.debug_walk_wait_timeout() == fmm.FMM_ETIMEOUT
+    x, y, z, m = _dev(b)
+    a = torch.stack(s.solve(x, y, z, m), 1).cpu().numpy()
+    ref = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25).accel("TC")
+    assert _rel_dev(a, ref).max() <= 1e-12
