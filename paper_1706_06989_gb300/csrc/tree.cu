@@ -435,6 +435,99 @@ __global__ void k_internal_upward(int32_t c0, int32_t c1, const int32_t *__restr
   for (int k = 0; k < kMomStride; ++k) out[k] = p[k];
 }
 
+// index tables of the symmetric moments: Q in the order xx xy xz yy yz zz,
+// O in the order xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
+__constant__ int c_q2i[6] = {0, 0, 0, 1, 1, 2}, c_q2j[6] = {0, 1, 2, 1, 2, 2};
+__constant__ int c_o3i[10] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 2};
+__constant__ int c_o3j[10] = {0, 0, 0, 1, 1, 2, 1, 1, 2, 2};
+__constant__ int c_o3k[10] = {0, 1, 2, 1, 2, 2, 1, 2, 2, 2};
+// position of Q_ab in that order
+__device__ __forceinline__ int sym2(int a, int b) {
+  const int lo = min(a, b), hi = max(a, b);
+  return lo * 3 - lo * (lo - 1) / 2 + (hi - lo);
+}
+
+// The same level with one warp per cell, for levels of few cells.  With one
+// thread per cell a small level is a single warp's chain of FP64 operations,
+// and an FP64 warp instruction takes many cycles on this GPU (the top
+// levels took 30-40 us each).  Here lane k loads child k, every lane forms
+// the same octant-order sums of S and M from the shuffled child values (so Z
+// is bit-identical to the one-thread form), and lane q then adds moment
+// component q over the children in child order.
+__global__ void k_internal_upward_warp(int32_t c0, int32_t c1, const int32_t *__restrict__ first_child,
+                                       const int32_t *__restrict__ nchild, double *__restrict__ S,
+                                       double *__restrict__ M, double *__restrict__ Z,
+                                       double *__restrict__ invM, double *__restrict__ mom) {
+  const int64_t wg = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t cc = c0 + wg;
+  if (cc >= c1) return;  // whole warp
+  const int c = static_cast<int>(cc);
+  const int nch = nchild[c];
+  if (nch == 0) return;  // whole warp
+  const int f = first_child[c];
+  double sx = 0.0, sy = 0.0, sz = 0.0, mc = 0.0;
+  if (lane < nch) {
+    sx = S[3 * (f + lane)];
+    sy = S[3 * (f + lane) + 1];
+    sz = S[3 * (f + lane) + 2];
+    mc = M[f + lane];
+  }
+  double tx = 0.0, ty = 0.0, tz = 0.0, tm = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const double vx = __shfl_sync(0xffffffffu, sx, j), vy = __shfl_sync(0xffffffffu, sy, j);
+    const double vz = __shfl_sync(0xffffffffu, sz, j), vm = __shfl_sync(0xffffffffu, mc, j);
+    if (j < nch) {
+      tx = __dadd_rn(tx, vx);
+      ty = __dadd_rn(ty, vy);
+      tz = __dadd_rn(tz, vz);
+      tm = __dadd_rn(tm, vm);
+    }
+  }
+  const double zx = __ddiv_rn(tx, tm), zy = __ddiv_rn(ty, tm), zz = __ddiv_rn(tz, tm);
+  if (lane == 0) {
+    S[3 * c] = tx;
+    S[3 * c + 1] = ty;
+    S[3 * c + 2] = tz;
+    M[c] = tm;
+    Z[3 * c] = zx;
+    Z[3 * c + 1] = zy;
+    Z[3 * c + 2] = zz;
+    invM[c] = 1.0 / tm;
+    mom[static_cast<int64_t>(c) * kMomStride] = tm;
+  }
+  const int q = lane;
+  if (q < 1 || q >= kMomStride) return;
+  // component q: 1..3 dipole (i), 4..9 Q (i, j), 10..19 O (i, j, l); the
+  // indices of this lane, and the slots of the Q entries it needs
+  int i = 0, j = 0, l = 0;
+  if (q < 4) {
+    i = q - 1;
+  } else if (q < 10) {
+    i = c_q2i[q - 4];
+    j = c_q2j[q - 4];
+  } else {
+    i = c_o3i[q - 10];
+    j = c_o3j[q - 10];
+    l = c_o3k[q - 10];
+  }
+  const int qij = 4 + sym2(i, j), qil = 4 + sym2(i, l), qjl = 4 + sym2(j, l);
+  double acc = 0.0;
+  for (int k = f; k < f + nch; ++k) {
+    const double *cq = mom + static_cast<int64_t>(k) * kMomStride;
+    const double s0 = Z[3 * k] - zx, s1 = Z[3 * k + 1] - zy, s2 = Z[3 * k + 2] - zz;
+    const double si = i == 0 ? s0 : (i == 1 ? s1 : s2);
+    const double sj = j == 0 ? s0 : (j == 1 ? s1 : s2);
+    const double sl = l == 0 ? s0 : (l == 1 ? s1 : s2);
+    const double Msi = cq[0] * si;
+    if (q < 4) acc += Msi;
+    else if (q < 10) acc += cq[q] + Msi * sj;
+    else acc += cq[q] + (cq[qij] * sl + cq[qil] * sj + cq[qjl] * si) + Msi * sj * sl;
+  }
+  mom[static_cast<int64_t>(c) * kMomStride + q] = acc;
+}
+
 // R_max^2 of every cell: for each level, each body's squared distance to the
 // centre of its cell at that level; a segmented warp maximum (bodies of one
 // cell are contiguous) and one atomicMax per segment on the bit pattern
@@ -658,10 +751,17 @@ int upward(fmm_ctx *c) {
   AMFMM_TRY(launched(c, "leaf_upward"));
   for (int lev = c->sz.depth - 1; lev >= 0; --lev) {
     const int64_t c0 = c->sz.lvl_off[lev], c1 = c->sz.lvl_off[lev + 1];
-    k_internal_upward<<<grid_for(c1 - c0, 128), 128, 0, st>>>(
-        static_cast<int32_t>(c0), static_cast<int32_t>(c1), ptr<int32_t>(c->first_child),
-        ptr<int32_t>(c->nchild), ptr<double>(c->S), ptr<double>(c->M), ptr<double>(c->Z),
-        ptr<double>(c->invM), ptr<double>(c->mom));
+    // few cells: a warp per cell; many: a thread per cell (throughput-bound)
+    if (c1 - c0 < 8192)
+      k_internal_upward_warp<<<grid_for(32 * (c1 - c0), 128), 128, 0, st>>>(
+          static_cast<int32_t>(c0), static_cast<int32_t>(c1), ptr<int32_t>(c->first_child),
+          ptr<int32_t>(c->nchild), ptr<double>(c->S), ptr<double>(c->M), ptr<double>(c->Z),
+          ptr<double>(c->invM), ptr<double>(c->mom));
+    else
+      k_internal_upward<<<grid_for(c1 - c0, 128), 128, 0, st>>>(
+          static_cast<int32_t>(c0), static_cast<int32_t>(c1), ptr<int32_t>(c->first_child),
+          ptr<int32_t>(c->nchild), ptr<double>(c->S), ptr<double>(c->M), ptr<double>(c->Z),
+          ptr<double>(c->invM), ptr<double>(c->mom));
     AMFMM_TRY(launched(c, "internal_upward"));
   }
   }
