@@ -124,7 +124,7 @@ int fmm_create(fmm_ctx **out, const fmm_opts *opts, void *cuda_stream) {
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
-      cudaMallocHost(&c->hpin, 4096) != cudaSuccess) {
+      cudaMallocHost(&c->hpin, 16384) != cudaSuccess) {
     cudaGetLastError();
     delete c;
     return FMM_ECUDA;

@@ -80,7 +80,7 @@ struct fmm_ctx {
       rmax2, mom, loc, leaves;
   // walk
   amfmm::DBuf front[2], m2l, p2p, self_list, walk_zr, walk_zf, walk_nl, walk_state, walk_lb;
-  unsigned walk_ticket = 0, walk_epoch = 0;  // single-pass walk generations
+  unsigned walk_epoch = 0;  // epochs of the single-pass walk generations
   // M2L scatter
   amfmm::DBuf ekey[2], eval[2], m2l_pos, m2l_off, m2l_slots, cell32;
   // P2P grouping
@@ -184,7 +184,7 @@ int downward_general(fmm_ctx *c);
 // learned selector (selector.cu, m2l.cu)
 int cell_features(fmm_ctx *c);  // per-cell parts of the selector's features
 int field_estimate(fmm_ctx *c);  // per-cell log10 |a| estimate of the selector's relative rule
-int walk_scores(fmm_ctx *c, int64_t nf, const int2 *front, float *score);
+int walk_scores(fmm_ctx *c, const long long *nf_dev, int64_t cap, const int2 *front, float *score);
 int pair_locals_tc(fmm_ctx *c, const int2 *pairs, int64_t K, double *out);
 
 void timer(fmm_ctx *c, int slot);

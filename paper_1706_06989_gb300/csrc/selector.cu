@@ -684,12 +684,17 @@ __global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__re
 // list's order varies from run to run, but a pair's score depends only on the
 // pair (the rows of a tensor-core product are independent), so the walk does
 // not.  k_walk_scores then runs the network on the candidates only.
-__global__ void k_band_select(int64_t nf, const int2 *__restrict__ front, const double4_32a *__restrict__ zr,
-                              const CellF *__restrict__ zf, const int32_t *__restrict__ count,
-                              int64_t min_work, double th_lo, double th_hi, float *__restrict__ score,
-                              int32_t *__restrict__ cand, unsigned *__restrict__ ncand) {
-  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+__global__ void k_band_select(const long long *__restrict__ nf_dev, int64_t cap, const int2 *__restrict__ front,
+                              const double4_32a *__restrict__ zr, const CellF *__restrict__ zf,
+                              const int32_t *__restrict__ count, int64_t min_work, double th_lo, double th_hi,
+                              float *__restrict__ score, int32_t *__restrict__ cand, unsigned *__restrict__ ncand) {
+  // the frontier size comes from the walk's generation record; a frontier
+  // beyond the buffers (the walk then stops and runs again) is not scored
+  const int64_t nf = min(static_cast<int64_t>(*nf_dev), cap);
   const int lane = threadIdx.x & 31;
+  for (int64_t base = blockIdx.x * static_cast<int64_t>(blockDim.x); base < nf;
+       base += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+  const int64_t t = base + threadIdx.x;
   bool ok = false;
   if (t < nf) {
     score[t] = INFINITY;
@@ -709,11 +714,13 @@ __global__ void k_band_select(int64_t nf, const int2 *__restrict__ front, const 
     }
   }
   const unsigned m = __ballot_sync(0xffffffffu, ok);
-  if (m == 0u) return;
-  unsigned base = 0;
-  if (lane == 0) base = atomicAdd(ncand, static_cast<unsigned>(__popc(m)));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (ok) cand[base + __popc(m & ((1u << lane) - 1u))] = static_cast<int32_t>(t);
+  if (m != 0u) {
+    unsigned at = 0;
+    if (lane == 0) at = atomicAdd(ncand, static_cast<unsigned>(__popc(m)));
+    at = __shfl_sync(0xffffffffu, at, 0);
+    if (ok) cand[at + __popc(m & ((1u << lane) - 1u))] = static_cast<int32_t>(t);
+  }
+  }
 }
 
 // The network on the candidates, 16 per warp step; persistent blocks stage
@@ -808,19 +815,17 @@ int field_estimate(fmm_ctx *c) {
   return launched(c, "field_estimate");
 }
 
-int walk_scores(fmm_ctx *c, int64_t nf, const int2 *front, float *score) {
+int walk_scores(fmm_ctx *c, const long long *nf_dev, int64_t cap, const int2 *front, float *score) {
   cudaStream_t st = c->stream;
-  AMFMM_TRY(ensure<int32_t>(c, c->sel_cand, nf));
   unsigned *ncand = reinterpret_cast<unsigned *>(ptr<int64_t>(c->totals) + 11);
   AMFMM_CUDA(c, cudaMemsetAsync(ncand, 0, sizeof(unsigned), st));
   const double lo = c->opts.theta, hi = c->sel_theta_max;
-  k_band_select<<<grid_for(nf, 256), 256, 0, st>>>(nf, front, ptr<double4_32a>(c->walk_zr),
-                                                    ptr<CellF>(c->walk_zf), ptr<int32_t>(c->count), c->sel_min_work, lo, hi, score,
-                                                    ptr<int32_t>(c->sel_cand), ncand);
+  // persistent grids: the frontier size is only known on the device
+  k_band_select<<<static_cast<unsigned>(c->num_sms * 8), 256, 0, st>>>(
+      nf_dev, cap, front, ptr<double4_32a>(c->walk_zr), ptr<CellF>(c->walk_zf), ptr<int32_t>(c->count),
+      c->sel_min_work, lo, hi, score, ptr<int32_t>(c->sel_cand), ncand);
   AMFMM_TRY(launched(c, "band_select"));
-  // persistent: at most 4 blocks of 4 warps per SM, fewer for a short frontier
-  const int64_t need = (nf + 63) / 64;
-  const unsigned g = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(c->num_sms) * 4)));
+  const unsigned g = static_cast<unsigned>(c->num_sms * 4);
   k_walk_scores<<<g, 128, 0, st>>>(front, ptr<int32_t>(c->sel_cand), ncand, ptr<float>(c->sel_params),
                                    ptr<CellF>(c->walk_zf), ptr<float4>(c->sel_cellfeat),
                                    c->sel_rule == FMM_SEL_RELATIVE ? ptr<float>(c->sel_lga) : nullptr,

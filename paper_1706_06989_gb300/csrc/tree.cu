@@ -301,23 +301,17 @@ __global__ void k_cell_counts(int32_t off, int32_t nnew, int32_t *__restrict__ b
   atomicAdd(&nchild[p], 1);
 }
 
-__global__ void k_update_cur(int64_t n, int32_t off, const int32_t *__restrict__ flag,
-                             const int32_t *__restrict__ excl, int32_t *__restrict__ cur) {
-  int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (i >= n) return;
-  if (cur[i] < 0) return;
-  // Bodies of leaves were retired; a body of a split cell moves to the child
-  // that starts at the last flagged body at or before it (same cell).
-  cur[i] = off + excl[i] + flag[i] - 1;
-}
-
-// cur[i] after k_update_cur must be -1 for bodies of leaves: mark them first
-__global__ void k_retire_leaf_bodies(int64_t n, int lev, int n_crit, const int32_t *__restrict__ count,
-                                     int32_t *__restrict__ cur) {
+// Next level's cell of every body: -1 for a body of a leaf (retired); a body
+// of a split cell moves to the child that starts at the last flagged body at
+// or before it (same cell).
+__global__ void k_update_cur(int64_t n, int lev, int n_crit, int32_t off, const int32_t *__restrict__ count,
+                             const int32_t *__restrict__ flag, const int32_t *__restrict__ excl,
+                             int32_t *__restrict__ cur) {
   int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= n) return;
   const int c = cur[i];
-  if (c >= 0 && (count[c] <= n_crit || lev == kMaxLevel)) cur[i] = -1;
+  if (c < 0) return;
+  cur[i] = (count[c] <= n_crit || lev == kMaxLevel) ? -1 : off + excl[i] + flag[i] - 1;
 }
 
 __global__ void k_leaf_flags(int32_t ncell, const int32_t *__restrict__ nchild, int32_t *__restrict__ f) {
@@ -689,11 +683,8 @@ int build_tree(fmm_ctx *c) {
         static_cast<int32_t>(off), static_cast<int32_t>(nnew), ptr<int32_t>(c->begin),
         ptr<int32_t>(c->count), ptr<int32_t>(c->parent), ptr<int32_t>(c->nchild));
     AMFMM_TRY(launched(c, "cell_counts"));
-    k_retire_leaf_bodies<<<grid_for(n, kBlock), kBlock, 0, st>>>(n, lev, c->opts.n_crit,
-                                                                 ptr<int32_t>(c->count), ptr<int32_t>(c->cur));
-    AMFMM_TRY(launched(c, "retire_leaf_bodies"));
-    k_update_cur<<<grid_for(n, kBlock), kBlock, 0, st>>>(n, static_cast<int32_t>(off), flag, excl,
-                                                         ptr<int32_t>(c->cur));
+    k_update_cur<<<grid_for(n, kBlock), kBlock, 0, st>>>(n, lev, c->opts.n_crit, static_cast<int32_t>(off),
+                                                         ptr<int32_t>(c->count), flag, excl, ptr<int32_t>(c->cur));
     AMFMM_TRY(launched(c, "update_cur"));
     c->sz.lvl_off.push_back(off + nnew);
   }

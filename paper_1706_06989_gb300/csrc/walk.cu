@@ -17,6 +17,8 @@
 // independent of the traversal order.  The walk proceeds one generation of
 // pairs at a time; an exclusive scan of the per-pair output counts places
 // every output, which makes the list order deterministic.
+#include <cstring>
+
 #include "geom.cuh"
 #include "internal.cuh"
 
@@ -90,21 +92,30 @@ __device__ __forceinline__ int classify(int A, int B, const int2 *__restrict__ n
 
 __device__ __forceinline__ int4 add4(int4 a, int4 b) { return make_int4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
 
-// State shared by the blocks of one generation (device memory):
-//   ticket       -- running block counter; a block's place in the scan is its
-//                   ticket minus the launch's base, so places follow the order
-//                   in which blocks start and every block waits only on blocks
-//                   that started before it;
-//   status       -- bit 0: an output did not fit its buffer; bit 1: a wait
-//                   for a predecessor gave up;
-//   total        -- the generation's output counts (written by the last block);
-//   flag/agg/inc -- per-place publication for the decoupled look-back, flag =
-//                   epoch << 2 | state (1: aggregate, 2: inclusive prefix).
+// Device-resident state of one generation (one record per generation):
+//   ticket  -- tile counter; a block takes the tiles of the frontier in the
+//              order it draws tickets, so every block waits only on tiles
+//              that were taken before its own;
+//   status  -- bit 0: an output exceeded its buffer (the walk stops: the next
+//              generation gets an empty frontier); bit 1: a wait for a
+//              predecessor gave up; bit 2: too few look-back records;
+//   total   -- the generation's output counts (x: next frontier, y: M2L,
+//              z: P2P, w: leaf self), written by the block of the last tile;
+//   in      -- the generation's frontier size and the list offsets it writes
+//              at, written by the previous generation (by the host for the
+//              first one).
+// The look-back records flag/agg/inc are shared by all generations and told
+// apart by an epoch per generation (flag = epoch << 2 | state, state 1:
+// aggregate, 2: inclusive prefix).
+struct GenIn {
+  long long nf, m2l, p2p, self;
+};
 struct GenState {
   unsigned ticket;
   int status;
   int pad[2];
   int4 total;
+  GenIn in;
 };
 
 constexpr int kGenItems = 4;
@@ -125,25 +136,44 @@ __device__ __forceinline__ void st_volatile4(int4 *p, int4 v) {
 }
 
 // One generation of the walk: every pair of the frontier is classified, the
-// output counts are scanned across the block and then across blocks (single
+// output counts are scanned across the block and then across tiles (single
 // pass, decoupled look-back), and the outputs are written in frontier order.
-// Any write beyond a buffer's capacity is skipped and flagged; the host then
-// grows the buffers and runs the generation again.
+// The grid is persistent: blocks draw tiles until the frontier is done.  The
+// frontier size and the list offsets come from the generation's record, so
+// the host launches all generations without waiting.  Writes beyond a
+// buffer's capacity are skipped; the block of the last tile then stops the
+// walk and flags it, and the host grows the buffers (keeping what earlier
+// generations wrote) and resumes the walk at the flagged generation.
 __global__ void __launch_bounds__(kGenBlock) k_walk_gen(
-    int64_t nf, const int2 *__restrict__ front, const int2 *__restrict__ nl, const double4_32a *__restrict__ zr,
-    const CellF *__restrict__ zf, double theta, const float *__restrict__ score, float target, const int32_t *__restrict__ first_child,
-    int2 *__restrict__ next, int64_t cap_next, int2 *__restrict__ m2l, int64_t m2l_base, int64_t cap_m2l,
-    int2 *__restrict__ p2p, int64_t p2p_base, int64_t cap_p2p, int32_t *__restrict__ self, int64_t self_base,
-    int64_t cap_self, GenState *__restrict__ gs, unsigned ticket_base, unsigned epoch, unsigned nblocks,
-    int *__restrict__ flag, int4 *__restrict__ agg, int4 *__restrict__ inc) {
+    GenState *__restrict__ gs, int g, const int2 *__restrict__ front, const int2 *__restrict__ nl,
+    const double4_32a *__restrict__ zr, const CellF *__restrict__ zf, double theta, const float *__restrict__ score,
+    float target, const int32_t *__restrict__ first_child, int2 *__restrict__ next, int64_t cap_next,
+    int2 *__restrict__ m2l, int64_t cap_m2l, int2 *__restrict__ p2p, int64_t cap_p2p, int32_t *__restrict__ self,
+    int64_t cap_self, unsigned epoch, int64_t max_places, int *__restrict__ flag, int4 *__restrict__ agg,
+    int4 *__restrict__ inc) {
   __shared__ unsigned s_place;
-  const float th2f = static_cast<float>(theta) * static_cast<float>(theta);
   __shared__ int4 s_warp[kGenBlock / 32];
   __shared__ int4 s_prefix;
+  const float th2f = static_cast<float>(theta) * static_cast<float>(theta);
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  if (t == 0) s_place = atomicAdd(&gs->ticket, 1u) - ticket_base;
+  GenState &G = gs[g];
+  const GenIn in = G.in;
+  const int64_t nf = in.nf;
+  const int64_t nb = (nf + kGenTile - 1) / kGenTile;
+  if (nb == 0 || nb > max_places) {
+    if (blockIdx.x == 0 && t == 0) {
+      if (nb > max_places) atomicOr(&G.status, 4);
+      G.total = make_int4(0, 0, 0, 0);
+      gs[g + 1].in = GenIn{0, in.m2l, in.p2p, in.self};
+    }
+    return;
+  }
+  const int64_t m2l_base = in.m2l, p2p_base = in.p2p, self_base = in.self;
+  for (;;) {
+  if (t == 0) s_place = atomicAdd(&G.ticket, 1u);
   __syncthreads();
   const unsigned place = s_place;
+  if (place >= nb) break;
   const int64_t i0 = static_cast<int64_t>(place) * kGenTile + static_cast<int64_t>(t) * kGenItems;
   int act[kGenItems];
   int2 pr[kGenItems];
@@ -225,14 +255,21 @@ __global__ void __launch_bounds__(kGenBlock) k_walk_gen(
         top -= 32;
       }
       if (lane == 0) {
-        if (failed) atomicOr(&gs->status, 2);
+        if (failed) atomicOr(&G.status, 2);
         st_volatile4(&inc[place], add4(pre, block_total));
         __threadfence();
         atomicExch(&flag[place], ep | 2);
       }
     }
     if (lane == 0) {
-      if (place == nblocks - 1) gs->total = add4(pre, block_total);
+      if (place == nb - 1) {
+        const int4 tot = add4(pre, block_total);
+        G.total = tot;
+        const bool over = tot.x > cap_next || m2l_base + tot.y > cap_m2l || p2p_base + tot.z > cap_p2p ||
+                          self_base + tot.w > cap_self;
+        if (over) atomicOr(&G.status, 1);
+        gs[g + 1].in = GenIn{over ? 0 : tot.x, m2l_base + tot.y, p2p_base + tot.z, self_base + tot.w};
+      }
       s_prefix = pre;
     }
   }
@@ -295,7 +332,9 @@ __global__ void __launch_bounds__(kGenBlock) k_walk_gen(
       }
     }
   }
-  if (over) atomicOr(&gs->status, 1);
+  (void)over;  // the block of the last tile judges overflow from the totals
+  __syncthreads();  // shared memory is reused by the next tile
+  }
 }
 
 __global__ void k_roots_front(int32_t nsys, int2 *__restrict__ front) {
@@ -350,76 +389,105 @@ int walk(fmm_ctx *c) {
   if (nsys > static_cast<int64_t>(c->front[0].cap / sizeof(int2))) AMFMM_TRY(ensure<int2>(c, c->front[0], nsys));
   k_roots_front<<<grid_for(nsys, kBlock), kBlock, 0, st>>>(static_cast<int32_t>(nsys), ptr<int2>(c->front[0]));
   AMFMM_TRY(launched(c, "walk_roots"));
-  // state of the single-pass generations (allocated and zeroed once)
-  if (c->walk_state.cap < sizeof(GenState)) {
-    AMFMM_TRY(ensure_bytes(c, c->walk_state, sizeof(GenState)));
-    AMFMM_CUDA(c, cudaMemsetAsync(c->walk_state.p, 0, sizeof(GenState), st));
-    c->walk_ticket = 0;
-  }
+  // The walk lasts at most 2 depth + 1 generations with pairs (a generation
+  // raises the sum of the two cells' levels by one, or by two for a pair of
+  // a cell with itself); one more finds the frontier empty.
+  const int ngen = 2 * c->sz.depth + 3;
+  int64_t n_m2l = 0, n_p2p = 0, n_self = 0;
+  AMFMM_TRY(ensure_bytes(c, c->walk_state, sizeof(GenState) * (ngen + 1)));
+  if (sizeof(GenState) * (ngen + 1) > 8192) return set_error(c, FMM_EUNSUPPORTED, "tree too deep for the walk state");
   GenState *gs = static_cast<GenState *>(c->walk_state.p);
-  int64_t nf = nsys, n_m2l = 0, n_p2p = 0, n_self = 0;
-  int cur = 0;
-  while (nf > 0) {
-    const float *score = nullptr;
-    if (c->sel_enabled) {
-      AMFMM_TRY(ensure<float>(c, c->sel_score, nf));
-      AMFMM_TRY(walk_scores(c, nf, ptr<int2>(c->front[cur]), ptr<float>(c->sel_score)));
-      score = ptr<float>(c->sel_score);
+  const unsigned grid = static_cast<unsigned>(std::max(1, c->num_sms * 4));
+  // generation records: zero, then the first generation's inputs (the roots)
+  AMFMM_CUDA(c, cudaMemsetAsync(gs, 0, sizeof(GenState) * (ngen + 1), st));
+  GenIn *hin = reinterpret_cast<GenIn *>(static_cast<char *>(c->hpin) + 8192);
+  *hin = GenIn{nsys, 0, 0, 0};
+  AMFMM_CUDA(c, cudaMemcpyAsync(&gs[0].in, hin, sizeof(GenIn), cudaMemcpyHostToDevice, st));
+  int gstart = 0;  // first generation to (re)run
+  for (int attempt = 0;; ++attempt) {
+    if (attempt > 16) return set_error(c, FMM_EINVAL, "walk: outputs still overflow after growing the buffers");
+    const int64_t cap_next = std::min(c->front[0].cap, c->front[1].cap) / sizeof(int2);
+    cap_front = cap_next;
+    if (c->sel_enabled) {  // one score and one candidate slot per frontier pair
+      AMFMM_TRY(ensure<float>(c, c->sel_score, cap_front));
+      AMFMM_TRY(ensure<int32_t>(c, c->sel_cand, cap_front));
     }
-    const int64_t nb64 = (nf + kGenTile - 1) / kGenTile;
-    if (nb64 > 0x7fffffffLL) return set_error(c, FMM_EUNSUPPORTED, "walk frontier too large (%lld pairs)", (long long)nf);
-    const unsigned nb = static_cast<unsigned>(nb64);
+    const int64_t max_places = (cap_next + kGenTile - 1) / kGenTile + 1;
     // look-back records; fresh memory is zeroed so no stale flag matches an epoch
-    const size_t lb_bytes = static_cast<size_t>(nb) * (sizeof(int) + 2 * sizeof(int4)) + 64;
+    const size_t lb_bytes = static_cast<size_t>(max_places) * (sizeof(int) + 2 * sizeof(int4)) + 64;
     if (c->walk_lb.cap < lb_bytes) {
-      AMFMM_TRY(ensure_bytes(c, c->walk_lb, lb_bytes + lb_bytes / 2));
+      AMFMM_TRY(ensure_bytes(c, c->walk_lb, lb_bytes));
       AMFMM_CUDA(c, cudaMemsetAsync(c->walk_lb.p, 0, c->walk_lb.cap, st));
     }
-    const size_t nbc = (c->walk_lb.cap - 64) / (sizeof(int) + 2 * sizeof(int4));
+    const int64_t nbc = static_cast<int64_t>((c->walk_lb.cap - 64) / (sizeof(int) + 2 * sizeof(int4)));
     int4 *agg = static_cast<int4 *>(c->walk_lb.p);
     int4 *inc = agg + nbc;
     int *flg = reinterpret_cast<int *>(inc + nbc);
-    int4 tot;
-    for (int attempt = 0;; ++attempt) {
-      const int64_t cap_next = static_cast<int64_t>(c->front[cur ^ 1].cap / sizeof(int2));
-      c->walk_epoch = (c->walk_epoch + 1) & 0x3fffffffu;
-      if (c->walk_epoch == 0) c->walk_epoch = 1;
-      k_walk_gen<<<nb, kGenBlock, 0, st>>>(
-          nf, ptr<int2>(c->front[cur]), ptr<int2>(c->walk_nl), ptr<double4_32a>(c->walk_zr),
-          ptr<CellF>(c->walk_zf), c->theta, score,
-          static_cast<float>(c->sel_log10_target), ptr<int32_t>(c->first_child), ptr<int2>(c->front[cur ^ 1]),
-          cap_next, ptr<int2>(c->m2l), n_m2l, cap_m2l, ptr<int2>(c->p2p), n_p2p, cap_p2p,
-          ptr<int32_t>(c->self_list), n_self, cap_self, gs, c->walk_ticket, c->walk_epoch, nb, flg, agg, inc);
-      c->walk_ticket += nb;
+    const unsigned epoch0 = c->walk_epoch + 1;
+    c->walk_epoch = (c->walk_epoch + ngen + 1) & 0x3fffffffu;
+    if (c->walk_epoch < epoch0) c->walk_epoch = ngen + 1;  // wrapped: restart above zero
+    for (int g = gstart; g < ngen; ++g) {
+      const float *score = nullptr;
+      if (c->sel_enabled) {
+        AMFMM_TRY(walk_scores(c, &gs[g].in.nf, cap_front, ptr<int2>(c->front[g & 1]), ptr<float>(c->sel_score)));
+        score = ptr<float>(c->sel_score);
+      }
+      unsigned ep = (epoch0 + g) & 0x3fffffffu;
+      if (ep == 0) ep = 1;
+      k_walk_gen<<<grid, kGenBlock, 0, st>>>(
+          gs, g, ptr<int2>(c->front[g & 1]), ptr<int2>(c->walk_nl), ptr<double4_32a>(c->walk_zr),
+          ptr<CellF>(c->walk_zf), c->theta, score, static_cast<float>(c->sel_log10_target),
+          ptr<int32_t>(c->first_child), ptr<int2>(c->front[(g + 1) & 1]), cap_next, ptr<int2>(c->m2l), cap_m2l,
+          ptr<int2>(c->p2p), cap_p2p, ptr<int32_t>(c->self_list), cap_self, ep, std::min(max_places, nbc), flg,
+          agg, inc);
       AMFMM_TRY(launched(c, "walk_gen"));
-      GenState *h = static_cast<GenState *>(c->hpin);
-      AMFMM_CUDA(c, cudaMemcpyAsync(h, gs, sizeof(GenState), cudaMemcpyDeviceToHost, st));
-      AMFMM_CUDA(c, cudaStreamSynchronize(st));
-      tot = h->total;
-      if (h->status & 2) return set_error(c, FMM_ETIMEOUT, "walk: a block waited too long for its predecessor");
-      if (!(h->status & 1)) break;
-      if (attempt > 0) return set_error(c, FMM_EINVAL, "walk: outputs overflowed after growing the buffers");
-      // an output did not fit: grow what overflowed and run the generation again
-      if (tot.x > cap_next) AMFMM_TRY(ensure<int2>(c, c->front[cur ^ 1], std::max<int64_t>(tot.x, 2 * cap_next)));
-      if (n_m2l + tot.y > cap_m2l) {
-        cap_m2l = std::max<int64_t>(2 * cap_m2l, n_m2l + tot.y);
-        AMFMM_TRY(ensure_keep_bytes(c, c->m2l, cap_m2l * sizeof(int2), n_m2l * sizeof(int2)));
-      }
-      if (n_p2p + tot.z > cap_p2p) {
-        cap_p2p = std::max<int64_t>(2 * cap_p2p, n_p2p + tot.z);
-        AMFMM_TRY(ensure_keep_bytes(c, c->p2p, cap_p2p * sizeof(int2), n_p2p * sizeof(int2)));
-      }
-      if (n_self + tot.w > cap_self) {
-        cap_self = std::max<int64_t>(2 * cap_self, n_self + tot.w);
-        AMFMM_TRY(ensure_keep_bytes(c, c->self_list, cap_self * sizeof(int32_t), n_self * sizeof(int32_t)));
-      }
-      AMFMM_CUDA(c, cudaMemsetAsync(&gs->status, 0, sizeof(int), st));
     }
-    n_m2l += tot.y;
-    n_p2p += tot.z;
-    n_self += tot.w;
-    nf = tot.x;
-    cur ^= 1;
+    GenState *h = static_cast<GenState *>(c->hpin);
+    AMFMM_CUDA(c, cudaMemcpyAsync(h, gs, sizeof(GenState) * (ngen + 1), cudaMemcpyDeviceToHost, st));
+    AMFMM_CUDA(c, cudaStreamSynchronize(st));
+    int first_bad = -1;
+    for (int g = gstart; g < ngen; ++g) {
+      if (h[g].status & 2) return set_error(c, FMM_ETIMEOUT, "walk: a block waited too long for its predecessor");
+      if ((h[g].status & 5) && first_bad < 0) first_bad = g;
+    }
+    if (first_bad < 0) {
+      if (h[ngen].in.nf != 0) return set_error(c, FMM_EINVAL, "walk: more generations than the depth allows");
+      n_m2l = h[ngen].in.m2l;
+      n_p2p = h[ngen].in.p2p;
+      n_self = h[ngen].in.self;
+      break;
+    }
+    // An output of generation b did not fit (its counts are exact).  Grow
+    // what overflowed, keeping everything the earlier generations wrote (the
+    // lists up to b's bases and b's own frontier), and resume at b.
+    const int b = first_bad;
+    const GenState hb = h[b];
+    if ((hb.status & 4) || hb.total.x > cap_next) {
+      const int64_t want = std::max<int64_t>(2 * cap_next, hb.total.x);
+      AMFMM_TRY(ensure_keep_bytes(c, c->front[b & 1], want * sizeof(int2), hb.in.nf * sizeof(int2)));
+      AMFMM_TRY(ensure<int2>(c, c->front[(b + 1) & 1], want));
+    }
+    if (hb.in.m2l + hb.total.y > cap_m2l) {
+      AMFMM_TRY(ensure_keep_bytes(c, c->m2l, std::max<int64_t>(2 * cap_m2l, hb.in.m2l + hb.total.y) * sizeof(int2),
+                                  hb.in.m2l * sizeof(int2)));
+      cap_m2l = c->m2l.cap / sizeof(int2);
+    }
+    if (hb.in.p2p + hb.total.z > cap_p2p) {
+      AMFMM_TRY(ensure_keep_bytes(c, c->p2p, std::max<int64_t>(2 * cap_p2p, hb.in.p2p + hb.total.z) * sizeof(int2),
+                                  hb.in.p2p * sizeof(int2)));
+      cap_p2p = c->p2p.cap / sizeof(int2);
+    }
+    if (hb.in.self + hb.total.w > cap_self) {
+      AMFMM_TRY(ensure_keep_bytes(c, c->self_list,
+                                  std::max<int64_t>(2 * cap_self, hb.in.self + hb.total.w) * sizeof(int32_t),
+                                  hb.in.self * sizeof(int32_t)));
+      cap_self = c->self_list.cap / sizeof(int32_t);
+    }
+    // records from b on: b keeps its inputs, the later ones start empty
+    std::memset(static_cast<void *>(h + b), 0, sizeof(GenState) * (ngen + 1 - b));
+    h[b].in = hb.in;
+    AMFMM_CUDA(c, cudaMemcpyAsync(gs + b, h + b, sizeof(GenState) * (ngen + 1 - b), cudaMemcpyHostToDevice, st));
+    gstart = b;
   }
   c->sz.n_m2l = n_m2l;
   c->sz.n_p2p = n_p2p;
@@ -432,51 +500,55 @@ int walk(fmm_ctx *c) {
 using namespace amfmm;
 
 // Test hook for the bounded wait of the walk's look-back (no counterpart in
-// the paper): one generation of an empty frontier is launched with a ticket
-// base one below the counter, so its only block takes place 1 and waits for
-// place 0, which no block holds.  The wait gives up after kSpinLimit polls,
-// the block skips its writes, and the call must return FMM_ETIMEOUT with the
-// context still usable.  Every access stays inside buffers of two places.
+// the paper): one generation of two tiles is launched with one block and its
+// ticket counter already at 1, so the block takes the second tile and waits
+// for the first, which no block takes.  The wait gives up after kSpinLimit
+// polls, the block skips its output (all capacities are zero), and the call
+// must return FMM_ETIMEOUT with the context still usable.  Every read stays
+// inside a zeroed frontier of two tiles and one zeroed cell; every write
+// inside two generation records and two look-back records.
 extern "C" int fmm_debug_walk_wait_timeout(fmm_ctx *c) {
   if (!c) return FMM_EINVAL;
   cudaStream_t st = c->stream;
-  if (c->walk_state.cap < sizeof(GenState)) {
-    AMFMM_TRY(ensure_bytes(c, c->walk_state, sizeof(GenState)));
-    AMFMM_CUDA(c, cudaMemsetAsync(c->walk_state.p, 0, sizeof(GenState), st));
-    c->walk_ticket = 0;
-  }
+  const int64_t nf = kGenTile + 1;  // two tiles
+  AMFMM_TRY(ensure_bytes(c, c->walk_state, 2 * sizeof(GenState)));
   const size_t lb_bytes = 2 * (sizeof(int) + 2 * sizeof(int4)) + 64;
   if (c->walk_lb.cap < lb_bytes) {
     AMFMM_TRY(ensure_bytes(c, c->walk_lb, lb_bytes));
     AMFMM_CUDA(c, cudaMemsetAsync(c->walk_lb.p, 0, c->walk_lb.cap, st));
   }
-  const size_t nbc = (c->walk_lb.cap - 64) / (sizeof(int) + 2 * sizeof(int4));
+  const int64_t nbc = static_cast<int64_t>((c->walk_lb.cap - 64) / (sizeof(int) + 2 * sizeof(int4)));
   int4 *agg = static_cast<int4 *>(c->walk_lb.p);
   int4 *inc = agg + nbc;
   int *flg = reinterpret_cast<int *>(inc + nbc);
-  AMFMM_TRY(ensure<int2>(c, c->front[0], 1));
+  AMFMM_TRY(ensure<int2>(c, c->front[0], nf));
   AMFMM_TRY(ensure<int2>(c, c->front[1], 1));
   AMFMM_TRY(ensure<int2>(c, c->walk_nl, 1));
   AMFMM_TRY(ensure<double4_32a>(c, c->walk_zr, 1));
   AMFMM_TRY(ensure<CellF>(c, c->walk_zf, 1));
   AMFMM_TRY(ensure<int32_t>(c, c->first_child, 1));
+  AMFMM_CUDA(c, cudaMemsetAsync(c->front[0].p, 0, sizeof(int2) * nf, st));
+  AMFMM_CUDA(c, cudaMemsetAsync(c->walk_nl.p, 0, sizeof(int2), st));
+  AMFMM_CUDA(c, cudaMemsetAsync(c->walk_zr.p, 0, sizeof(double4_32a), st));
+  AMFMM_CUDA(c, cudaMemsetAsync(c->walk_zf.p, 0, sizeof(CellF), st));
   GenState *gs = static_cast<GenState *>(c->walk_state.p);
-  AMFMM_CUDA(c, cudaMemsetAsync(&gs->status, 0, sizeof(int), st));
+  GenState *hs = reinterpret_cast<GenState *>(static_cast<char *>(c->hpin) + 8192);
+  hs[0] = GenState{};
+  hs[0].ticket = 1;  // the only block takes the second tile
+  hs[0].in = GenIn{nf, 0, 0, 0};
+  hs[1] = GenState{};
+  AMFMM_CUDA(c, cudaMemcpyAsync(gs, hs, 2 * sizeof(GenState), cudaMemcpyHostToDevice, st));
   c->walk_epoch = (c->walk_epoch + 1) & 0x3fffffffu;
   if (c->walk_epoch == 0) c->walk_epoch = 1;
-  // nf = 0 and every capacity 0: nothing is read or written but the
-  // look-back records of places 0 and 1
-  k_walk_gen<<<1, kGenBlock, 0, st>>>(0, ptr<int2>(c->front[0]), ptr<int2>(c->walk_nl), ptr<double4_32a>(c->walk_zr),
-                                      ptr<CellF>(c->walk_zf), 0.5, nullptr, 0.f, ptr<int32_t>(c->first_child),
-                                      ptr<int2>(c->front[1]), 0, nullptr, 0, 0, nullptr, 0, 0, nullptr, 0, 0, gs,
-                                      c->walk_ticket - 1u, c->walk_epoch, 2u, flg, agg, inc);
-  c->walk_ticket += 1;
+  k_walk_gen<<<1, kGenBlock, 0, st>>>(gs, 0, ptr<int2>(c->front[0]), ptr<int2>(c->walk_nl),
+                                      ptr<double4_32a>(c->walk_zr), ptr<CellF>(c->walk_zf), 0.5, nullptr, 0.f,
+                                      ptr<int32_t>(c->first_child), ptr<int2>(c->front[1]), 0, nullptr, 0, nullptr,
+                                      0, nullptr, 0, c->walk_epoch, std::min<int64_t>(2, nbc), flg, agg, inc);
   AMFMM_TRY(launched(c, "walk_gen_wait_test"));
   GenState *h = static_cast<GenState *>(c->hpin);
   AMFMM_CUDA(c, cudaMemcpyAsync(h, gs, sizeof(GenState), cudaMemcpyDeviceToHost, st));
   AMFMM_CUDA(c, cudaStreamSynchronize(st));
   const int status = h->status;
-  AMFMM_CUDA(c, cudaMemsetAsync(&gs->status, 0, sizeof(int), st));
   c->stage = kNone;
   if (status & 2) return set_error(c, FMM_ETIMEOUT, "walk: a block waited too long for its predecessor");
   return FMM_OK;
