@@ -246,11 +246,12 @@ int fmm_selector_train(fmm_ctx *ctx, float *params, float *adam, const float *X,
 
 /* ---- test hook (no counterpart in the paper) ------------------------------ */
 /* Exercises the bounded wait of the walk's single-pass scan: launches one
- * walk generation of an empty frontier whose only block is told to wait for
- * a predecessor that does not exist.  The wait gives up after its poll
- * limit (about a second), the block writes nothing but its own scan record,
- * and the call returns FMM_ETIMEOUT; the context stays usable (the next call
- * must be fmm_build_tree or fmm_solve).  Synchronises the stream. */
+ * walk generation of two tiles with one block whose tile counter already
+ * stands at 1, so the block waits for a predecessor that no block takes.
+ * The wait gives up after its poll limit (about a second), the block writes
+ * nothing but its own scan records, and the call returns FMM_ETIMEOUT; the
+ * context stays usable (the next call must be fmm_build_tree or fmm_solve).
+ * Synchronises the stream. */
 int fmm_debug_walk_wait_timeout(fmm_ctx *ctx);
 
 /* ---- a10 diagnostics (Sec. 3) ---------------------------------------------- */
