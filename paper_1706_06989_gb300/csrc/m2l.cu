@@ -265,14 +265,21 @@ template <int VARIANT>
 __global__ void __launch_bounds__(kGatherWarps * 32) k_m2l32_gather(int32_t ncell, const int32_t *__restrict__ off,
                                                                     const uint32_t *__restrict__ partner,
                                                                     const float *__restrict__ cell32,
-                                                                    double *__restrict__ loc) {
+                                                                    double *__restrict__ loc,
+                                                                    int *__restrict__ queue) {
   // per warp, per coefficient, per lane: the lane's sum and (negated) error
   __shared__ float sh[kGatherWarps][19][33];
   __shared__ float sl[kGatherWarps][19][33];
   const int w = threadIdx.x >> 5;
-  const int c = blockIdx.x * kGatherWarps + w;
   const int lane = threadIdx.x & 31;
-  if (c >= ncell) return;
+  // cells differ widely in their number of partners: warps draw cells from a
+  // queue (the grid is what fits on the GPU at once); the result of a cell
+  // does not depend on which warp takes it
+  for (;;) {
+  int c = 0;
+  if (lane == 0) c = atomicAdd(queue, 1);
+  c = __shfl_sync(0xffffffffu, c, 0);
+  if (c >= ncell) break;
   const float *t = cell32 + static_cast<int64_t>(c) * kCell32;
   const float thx = t[0], thy = t[1], thz = t[2], tlx = t[3], tly = t[4], tlz = t[5];
   const float MT = t[6], iMT = t[7];
@@ -319,6 +326,8 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_m2l32_gather(int32_t ncel
     loc[static_cast<int64_t>(c) * kLocStride + lane] = static_cast<double>(hi) + static_cast<double>(lo);
   } else if (lane == 19) {
     loc[static_cast<int64_t>(c) * kLocStride + 19] = 0.0;
+  }
+  __syncwarp();  // sh and sl are written again by the next cell
   }
 }
 
@@ -462,17 +471,22 @@ int launch_m2l64(fmm_ctx *c, int64_t K) {
 
 int launch_m2l32_gather(fmm_ctx *c) {
   const int32_t nc = static_cast<int32_t>(c->sz.ncell);
-  const unsigned g = grid_for(static_cast<int64_t>(nc) * 32, kGatherWarps * 32);
   const int32_t *off = ptr<int32_t>(c->m2l_off);
   const uint32_t *partner = ptr<uint32_t>(c->eval[c->m2l_which]);
   const float *c32 = ptr<float>(c->cell32);
   double *loc = ptr<double>(c->loc);
   cudaStream_t st = c->stream;
-  switch (c->opts.variant) {
-    case FMM_UC: k_m2l32_gather<FMM_UC><<<g, kGatherWarps * 32, 0, st>>>(nc, off, partner, c32, loc); break;
-    case FMM_TC: k_m2l32_gather<FMM_TC><<<g, kGatherWarps * 32, 0, st>>>(nc, off, partner, c32, loc); break;
-    default: k_m2l32_gather<FMM_TCO><<<g, kGatherWarps * 32, 0, st>>>(nc, off, partner, c32, loc); break;
-  }
+  int *queue = ptr<int32_t>(c->totals) + 41;
+  AMFMM_CUDA(c, cudaMemsetAsync(queue, 0, sizeof(int), st));
+  auto kern = c->opts.variant == FMM_UC   ? k_m2l32_gather<FMM_UC>
+              : c->opts.variant == FMM_TC ? k_m2l32_gather<FMM_TC>
+                                          : k_m2l32_gather<FMM_TCO>;
+  int per_sm = 0;
+  AMFMM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGatherWarps * 32, 0));
+  const int64_t resident = static_cast<int64_t>(std::max(1, per_sm)) * std::max(1, c->num_sms);
+  const unsigned g =
+      static_cast<unsigned>(std::min<int64_t>(grid_for(static_cast<int64_t>(nc) * 32, kGatherWarps * 32), resident));
+  kern<<<g, kGatherWarps * 32, 0, st>>>(nc, off, partner, c32, loc, queue);
   return launched(c, "m2l");
 }
 

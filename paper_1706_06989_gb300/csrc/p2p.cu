@@ -142,12 +142,20 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
     const int32_t *__restrict__ count, const double *__restrict__ Zc, const double *__restrict__ X,
     const double *__restrict__ Y, const double *__restrict__ Zb, const double *__restrict__ Mb,
     const int2 *__restrict__ cols, double *__restrict__ near, double *__restrict__ extra,
-    T *__restrict__ slots, const BodyF *__restrict__ bodyf) {
+    T *__restrict__ slots, const BodyF *__restrict__ bodyf, int *__restrict__ queue) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   P2PSmem<T> &sm = reinterpret_cast<P2PSmem<T> *>(smem_raw)[w];
-  const int q = blockIdx.x * kWarps + w;
-  if (q >= nitem) return;
+  // Work items differ in size by orders of magnitude, so warps draw them
+  // from a queue until it is empty instead of taking a fixed one: a block's
+  // warps then never wait for one another's items (the grid is as large as
+  // fits on the GPU at once).  Which warp takes an item does not change what
+  // it computes or where it writes.
+  for (;;) {
+  int q = 0;
+  if (l == 0) q = atomicAdd(queue, 1);
+  q = __shfl_sync(0xffffffffu, q, 0);
+  if (q >= nitem) break;
   // work item: leaf, column range; w < 0 marks the leaf's first chunk (which
   // owns the near-field sums of the leaf), w >= 0 the offset of a later
   // chunk's A-side partials in `extra`
@@ -304,6 +312,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
       else extra[it.w + 3 * (r0 + v / 3) + v % 3] = s;
     }
     __syncwarp();
+  }
   }
 }
 
@@ -513,11 +522,17 @@ int launch_p2p(fmm_ctx *c) {
   // per function and device, so set on every launch (a host-side call)
   AMFMM_CUDA(c, cudaFuncSetAttribute(k_p2p<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
   const int32_t nitem = static_cast<int32_t>(c->sz.p2p_items);
-  k_p2p<T><<<grid_for(nitem, kWarps), kWarps * 32, shm, c->stream>>>(
+  int per_sm = 0;
+  AMFMM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p<T>, kWarps * 32, shm));
+  const int64_t resident = static_cast<int64_t>(std::max(1, per_sm)) * std::max(1, c->num_sms);
+  const unsigned grid = static_cast<unsigned>(std::min<int64_t>(grid_for(nitem, kWarps), resident));
+  int *queue = ptr<int32_t>(c->totals) + 40;
+  AMFMM_CUDA(c, cudaMemsetAsync(queue, 0, sizeof(int), c->stream));
+  k_p2p<T><<<grid, kWarps * 32, shm, c->stream>>>(
       nitem, n, ptr<int4>(c->p2p_items), ptr<int32_t>(c->begin), ptr<int32_t>(c->count),
       ptr<double>(c->Z), ptr<double>(c->X), ptr<double>(c->Y), ptr<double>(c->Zb), ptr<double>(c->Mb),
       ptr<int2>(c->p2p_cols), ptr<double>(c->near), ptr<double>(c->p2p_extra),
-      static_cast<T *>(c->p2p_slots.p), sizeof(T) == sizeof(float) ? ptr<BodyF>(c->p2p_bodyf) : nullptr);
+      static_cast<T *>(c->p2p_slots.p), sizeof(T) == sizeof(float) ? ptr<BodyF>(c->p2p_bodyf) : nullptr, queue);
   AMFMM_TRY(launched(c, "p2p"));
   if (nitem > nleaf) {
     k_p2p_chunks<<<grid_for(static_cast<int64_t>(nleaf) * 32, 256), 256, 0, c->stream>>>(
