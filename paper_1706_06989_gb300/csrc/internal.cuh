@@ -89,7 +89,7 @@ struct fmm_ctx {
       p2p_extra;
   // scan / sort scratch; `totals` holds small device results (1 KiB):
   // [0,16) scan totals, [64,72) near-field body-pair count, [80,88) selector-scored pairs, [88,92) selector candidates, [96,104) slot total,
-  // [128,140) near-field column, work-item and extra-partial totals, [160,168) near- and far-field work queues
+  // [128,140) near-field column, work-item and extra-partial totals, [160,168) work queues (near field, gathered far field)
   amfmm::DBuf scan_tmp, sort_hist, totals, diag;
   // learned pair selector
   amfmm::DBuf sel_params, sel_cellfeat, sel_cand, sel_lga, sel_scratch, sel_part, sel_score, sel_grad, sel_perm, sel_xb, sel_yb;

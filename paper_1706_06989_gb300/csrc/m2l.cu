@@ -389,15 +389,31 @@ __global__ void k_m2l_entries(int64_t K, const int2 *__restrict__ pairs, int gat
 // off[c] = first sorted position of cell c (cells without entries get the
 // position of the next cell): every position s starts the cells
 // (key[s-1], key[s]], and the last entry closes the cells after it.
+// Four positions per thread, read as one 16-byte load (key is 16-byte aligned).
 __global__ void k_segment_offsets(int64_t E, int32_t ncell, const uint32_t *__restrict__ key,
                                   int32_t *__restrict__ off) {
-  const int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (s >= E) return;
-  const int k = static_cast<int>(key[s]);
-  const int kp = s == 0 ? -1 : static_cast<int>(key[s - 1]);
-  for (int c = kp + 1; c <= k; ++c) off[c] = static_cast<int32_t>(s);
-  if (s == E - 1)
-    for (int c = k + 1; c <= ncell; ++c) off[c] = static_cast<int32_t>(E);
+  const int64_t s0 = 4 * (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x);
+  if (s0 >= E) return;
+  int k[4];
+  if (s0 + 4 <= E) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(key + s0);
+    k[0] = static_cast<int>(v.x), k[1] = static_cast<int>(v.y), k[2] = static_cast<int>(v.z),
+    k[3] = static_cast<int>(v.w);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) k[u] = s0 + u < E ? static_cast<int>(key[s0 + u]) : ncell;
+  }
+  int kp = s0 == 0 ? -1 : static_cast<int>(key[s0 - 1]);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t s = s0 + u;
+    if (s < E) {
+      for (int c = kp + 1; c <= k[u]; ++c) off[c] = static_cast<int32_t>(s);
+      if (s == E - 1)
+        for (int c = k[u] + 1; c <= ncell; ++c) off[c] = static_cast<int32_t>(E);
+    }
+    kp = k[u];
+  }
 }
 
 __global__ void k_inverse(int64_t E, const uint32_t *__restrict__ sval, int32_t *__restrict__ pos) {
@@ -518,7 +534,8 @@ int m2l_prepare(fmm_ctx *c) {
   int which = 0;
   AMFMM_TRY(radix_sort_u32(c, c->ekey, c->eval, E, bits_for(nc), &which));
   c->m2l_which = which;
-  k_segment_offsets<<<grid_for(E, 256), 256, 0, st>>>(E, static_cast<int32_t>(nc), ptr<uint32_t>(c->ekey[which]), off);
+  k_segment_offsets<<<grid_for((E + 3) / 4, 256), 256, 0, st>>>(E, static_cast<int32_t>(nc),
+                                                               ptr<uint32_t>(c->ekey[which]), off);
   AMFMM_TRY(launched(c, "segment_offsets"));
   if (!gather) {
     k_inverse<<<grid_for(E, 256), 256, 0, st>>>(E, ptr<uint32_t>(c->eval[which]), ptr<int32_t>(c->m2l_pos));
@@ -559,6 +576,8 @@ int m2l_reduce(fmm_ctx *c) {
   }
   if (m2l_gathered(c)) return FMM_OK;  // the gather kernel wrote every local
   int32_t *off = ptr<int32_t>(c->m2l_off);
+  // (warps drawing cells from a queue, as the gather does, measured 2.44 ms
+  // against 2.39 ms for one warp per cell at N = 1M)
   k_m2l_reduce<<<grid_for(nc * 32, kRedWarps * 32), kRedWarps * 32, 0, st>>>(
       static_cast<int32_t>(nc), off, ptr<double>(c->m2l_slots), ptr<double>(c->loc));
   return launched(c, "m2l_reduce");

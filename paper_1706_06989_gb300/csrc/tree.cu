@@ -524,9 +524,10 @@ __global__ void k_internal_upward_warp(int32_t c0, int32_t c1, const int32_t *__
 
 // R_max^2 of every cell: for each level, each body's squared distance to the
 // centre of its cell at that level; a segmented warp maximum (bodies of one
-// cell are contiguous) and one atomicMax per segment on the bit pattern
-// (monotone for non-negative doubles).  max is exact, so the order of
-// combination does not matter.
+// cell are contiguous) and one atomicMax per segment, both on the bit pattern
+// (monotone for non-negative doubles, and integer work, which keeps the
+// maximum off the FP64 pipe).  max is exact, so the order of combination
+// does not matter.
 __global__ void k_rmax_bodies(int64_t n, const int32_t *__restrict__ cell_at,
                               const double *__restrict__ X, const double *__restrict__ Y,
                               const double *__restrict__ Zb, const double *__restrict__ Z,
@@ -535,25 +536,26 @@ __global__ void k_rmax_bodies(int64_t n, const int32_t *__restrict__ cell_at,
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   const int lane = threadIdx.x & 31;
   int c = -1;
-  double d2 = 0.0;
+  unsigned long long d2 = 0;  // bit pattern of |X - Z|^2 >= +0
   if (i < n) {
     c = cell_at[static_cast<int64_t>(lev) * n + i];
     if (c >= 0) {
       const double dx = __dsub_rn(X[i], Z[3 * c]);
       const double dy = __dsub_rn(Y[i], Z[3 * c + 1]);
       const double dz = __dsub_rn(Zb[i], Z[3 * c + 2]);
-      d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+      d2 = static_cast<unsigned long long>(
+          __double_as_longlong(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz))));
     }
   }
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const double v = __shfl_down_sync(0xffffffffu, d2, o);
+    const unsigned long long v = __shfl_down_sync(0xffffffffu, d2, o);
     const int co = __shfl_down_sync(0xffffffffu, c, o);
-    if (lane + o < 32 && co == c) d2 = fmax(d2, v);
+    if (lane + o < 32 && co == c && v > d2) d2 = v;
   }
   const int cprev = __shfl_up_sync(0xffffffffu, c, 1);
   const bool head = (lane == 0) || (cprev != c);
-  if (c >= 0 && head) atomicMax(&rmax2[c], static_cast<unsigned long long>(__double_as_longlong(d2)));
+  if (c >= 0 && head) atomicMax(&rmax2[c], d2);
 }
 
 __global__ void k_rmax_final(int32_t ncell, const unsigned long long *__restrict__ rmax2,
