@@ -166,9 +166,26 @@ __global__ void k_radix_hist(const K *__restrict__ key, int64_t n, int shift,
   for (int d = threadIdx.x; d < kRadix; d += kSortBlock) cnt[d] = 0;
   __syncthreads();
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
-  for (int k = 0; k < kSortItems; ++k) {
-    int64_t i = base + static_cast<int64_t>(k) * kSortBlock + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[static_cast<int>((key[i] >> shift) & kDigitMask)], 1);
+  if (base + kSortTile <= n) {
+    // whole tile: 16-byte loads (the tile starts 16-byte aligned), all in
+    // flight before the counting
+    constexpr int kPer = 16 / sizeof(K), kLoads = kSortItems / kPer;
+    using V = uint4;
+    V v[kLoads];
+    const V *kv = reinterpret_cast<const V *>(key + base);
+#pragma unroll
+    for (int k = 0; k < kLoads; ++k) v[k] = kv[k * kSortBlock + threadIdx.x];
+#pragma unroll
+    for (int k = 0; k < kLoads; ++k) {
+      const K *e = reinterpret_cast<const K *>(&v[k]);
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) atomicAdd(&cnt[static_cast<int>((e[u] >> shift) & kDigitMask)], 1);
+    }
+  } else {
+    for (int k = 0; k < kSortItems; ++k) {
+      int64_t i = base + static_cast<int64_t>(k) * kSortBlock + threadIdx.x;
+      if (i < n) atomicAdd(&cnt[static_cast<int>((key[i] >> shift) & kDigitMask)], 1);
+    }
   }
   __syncthreads();
   for (int d = threadIdx.x; d < kRadix; d += kSortBlock)

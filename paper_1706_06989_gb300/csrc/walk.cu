@@ -121,6 +121,7 @@ struct GenState {
 constexpr int kGenItems = 4;
 constexpr int kGenBlock = 256;  // threads of a generation block (128: 1.29 ms, 512: 1.21 ms, 256: 1.16 ms per 1M solve)
 constexpr int kGenTile = kGenBlock * kGenItems;
+constexpr int kGenBlocksPerSM = 5;  // resident blocks per SM the registers are limited for
 constexpr long long kSpinLimit = 1LL << 22;
 
 __device__ __forceinline__ int4 ld_volatile4(const int4 *p) {
@@ -144,7 +145,7 @@ __device__ __forceinline__ void st_volatile4(int4 *p, int4 v) {
 // buffer's capacity are skipped; the block of the last tile then stops the
 // walk and flags it, and the host grows the buffers (keeping what earlier
 // generations wrote) and resumes the walk at the flagged generation.
-__global__ void __launch_bounds__(kGenBlock) k_walk_gen(
+__global__ void __launch_bounds__(kGenBlock, kGenBlocksPerSM) k_walk_gen(
     GenState *__restrict__ gs, int g, const int2 *__restrict__ front, const int2 *__restrict__ nl,
     const double4_32a *__restrict__ zr, const CellF *__restrict__ zf, double theta, const float *__restrict__ score,
     float target, const int32_t *__restrict__ first_child, int2 *__restrict__ next, int64_t cap_next,
@@ -397,7 +398,7 @@ int walk(fmm_ctx *c) {
   AMFMM_TRY(ensure_bytes(c, c->walk_state, sizeof(GenState) * (ngen + 1)));
   if (sizeof(GenState) * (ngen + 1) > 8192) return set_error(c, FMM_EUNSUPPORTED, "tree too deep for the walk state");
   GenState *gs = static_cast<GenState *>(c->walk_state.p);
-  const unsigned grid = static_cast<unsigned>(std::max(1, c->num_sms * 4));
+  const unsigned grid = static_cast<unsigned>(std::max(1, c->num_sms * kGenBlocksPerSM));
   // generation records: zero, then the first generation's inputs (the roots)
   AMFMM_CUDA(c, cudaMemsetAsync(gs, 0, sizeof(GenState) * (ngen + 1), st));
   GenIn *hin = reinterpret_cast<GenIn *>(static_cast<char *>(c->hpin) + 8192);
