@@ -43,8 +43,8 @@ __device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
 // one running partial of the A-side sum for every lane.
 template <class T>
 struct P2PSmem {
-  T row[kRowsOf<T>][4];       // x, y, z, m of the current row chunk
-  T acc[kRowsOf<T> * 3][32];  // A-side partial sums, [3 i + d][lane]
+  alignas(16) T row[kRowsOf<T>][4];  // x, y, z, m of the current row chunk (16-byte loads)
+  T acc[kRowsOf<T> * 3][32];         // A-side partial sums, [3 i + d][lane]
 };
 template <class T>
 __device__ __forceinline__ void acc_zero(P2PSmem<T> &sm, int nr, int l) {
@@ -77,6 +77,33 @@ __device__ __forceinline__ float p2p_min_r2<float>() { return 1e-30f; }
 // squares, so never negative) to keep the comparison off the FP64 pipe
 __device__ __forceinline__ bool p2p_apart(double r2) { return __double_as_longlong(r2) != 0; }
 __device__ __forceinline__ bool p2p_apart(float r2) { return r2 > p2p_min_r2<float>(); }
+
+// R consecutive rows i.. against one column body (FP32 form): the B-side sum
+// in row order, then the A-side partials.
+template <int R>
+__device__ __forceinline__ void rows32(P2PSmem<float> &sm, int i, int l, bool valid, bool mutual, float xj,
+                                       float yj, float zj, float mj, float &bx, float &by, float &bz) {
+  float dx[R], dy[R], dz[R], r3[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const float4 rw = *reinterpret_cast<const float4 *>(sm.row[i + u]);
+    dx[u] = rw.x - xj;
+    dy[u] = rw.y - yj;
+    dz[u] = rw.z - zj;
+    const float r2 = dx[u] * dx[u] + dy[u] * dy[u] + dz[u] * dz[u];
+    const bool ok = valid && r2 > p2p_min_r2<float>();
+    const float ri = ok ? rsqrtf(r2) : 0.f;
+    r3[u] = ri * ri * ri;
+    const float si = rw.w * r3[u];
+    bx += si * dx[u];
+    by += si * dy[u];
+    bz += si * dz[u];
+  }
+  if (mutual) {
+#pragma unroll
+    for (int u = 0; u < R; ++u) acc_sub(sm, i + u, l, mj * r3[u], dx[u], dy[u], dz[u]);
+  }
+}
 
 template <class T>
 __device__ __forceinline__ T coord(double v, double z);
@@ -229,29 +256,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
       }
       const bool mutual = col.y >= 0;
       T bx = T(0), by = T(0), bz = T(0);
-      // FP32: two rows per step, independent dependency chains for the
-      // pipelines (FP64 is issue-bound and runs faster one row at a time)
+      // FP32: four rows per step, then two, independent dependency chains
+      // for the pipelines and less loop control per pair (FP64 is bound by
+      // its pipe and runs faster one row at a time)
       int i = 0;
-      if constexpr (sizeof(T) == sizeof(float)) for (; i + 1 < nr; i += 2) {
-        const T dx0 = sm.row[i][0] - xj, dy0 = sm.row[i][1] - yj, dz0 = sm.row[i][2] - zj;
-        const T dx1 = sm.row[i + 1][0] - xj, dy1 = sm.row[i + 1][1] - yj, dz1 = sm.row[i + 1][2] - zj;
-        const T r20 = dx0 * dx0 + dy0 * dy0 + dz0 * dz0;
-        const T r21 = dx1 * dx1 + dy1 * dy1 + dz1 * dz1;
-        const bool ok0 = valid && r20 > p2p_min_r2<T>(), ok1 = valid && r21 > p2p_min_r2<T>();
-        const T ri0 = ok0 ? rsqrt_t(r20) : T(0), ri1 = ok1 ? rsqrt_t(r21) : T(0);
-        const T r30 = ri0 * ri0 * ri0, r31 = ri1 * ri1 * ri1;
-        const T si0 = sm.row[i][3] * r30, si1 = sm.row[i + 1][3] * r31;
-        bx += si0 * dx0;
-        by += si0 * dy0;
-        bz += si0 * dz0;
-        bx += si1 * dx1;
-        by += si1 * dy1;
-        bz += si1 * dz1;
-        if (mutual) {
-          const T sj0 = mj * r30, sj1 = mj * r31;
-          acc_sub(sm, i, l, sj0, dx0, dy0, dz0);
-          acc_sub(sm, i + 1, l, sj1, dx1, dy1, dz1);
-        }
+      if constexpr (sizeof(T) == sizeof(float)) {
+        for (; i + 3 < nr; i += 4) rows32<4>(sm, i, l, valid, mutual, xj, yj, zj, mj, bx, by, bz);
+        for (; i + 1 < nr; i += 2) rows32<2>(sm, i, l, valid, mutual, xj, yj, zj, mj, bx, by, bz);
       }
       for (; i < nr; ++i) {
         const T dx = sm.row[i][0] - xj, dy = sm.row[i][1] - yj, dz = sm.row[i][2] - zj;
@@ -348,7 +359,7 @@ __global__ void k_p2p_chunks(int32_t nleaf, int64_t n, const int32_t *__restrict
 // that the one-sided self sums stay in one warp).  One warp per chunk keeps a
 // leaf that the walk paired with millions of bodies (a large sparse leaf next
 // to a dense region) from serialising the kernel.
-constexpr int kChunk = 16384;
+constexpr int kChunk = 4096;
 
 __device__ __forceinline__ int chunks_of(int ncol, int nself) {
   const int first = max(kChunk, nself);
