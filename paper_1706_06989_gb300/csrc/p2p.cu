@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
       // its pipe and runs faster one row at a time)
       int i = 0;
       if constexpr (sizeof(T) == sizeof(float)) {
+        for (; i + 7 < nr; i += 8) rows32<8>(sm, i, l, valid, mutual, xj, yj, zj, mj, bx, by, bz);
         for (; i + 3 < nr; i += 4) rows32<4>(sm, i, l, valid, mutual, xj, yj, zj, mj, bx, by, bz);
         for (; i + 1 < nr; i += 2) rows32<2>(sm, i, l, valid, mutual, xj, yj, zj, mj, bx, by, bz);
       }
