@@ -80,6 +80,7 @@ struct fmm_ctx {
       rmax2, mom, loc, leaves;
   // walk
   amfmm::DBuf front[2], m2l, p2p, self_list, walk_zr, walk_zf, walk_nl, walk_state, walk_lb;
+  int last_depth = 0;        // depth of the previous tree: levels of the first batch of the next build
   unsigned walk_epoch = 0;  // epochs of the single-pass walk generations
   // M2L scatter
   amfmm::DBuf ekey[2], eval[2], m2l_pos, m2l_off, m2l_slots, cell32;

@@ -212,8 +212,14 @@ __global__ void k_gather_sorted(int64_t n, const uint32_t *__restrict__ perm, co
 // level 0: one root per system
 __global__ void k_roots(int32_t nsys, const int64_t *__restrict__ off, int32_t *__restrict__ begin,
                         int32_t *__restrict__ count, int32_t *__restrict__ level, int32_t *__restrict__ parent,
-                        int32_t *__restrict__ first_child, int32_t *__restrict__ nchild) {
+                        int32_t *__restrict__ first_child, int32_t *__restrict__ nchild, int32_t *__restrict__ lvl,
+                        int *__restrict__ ovf) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s == 0) {
+    lvl[0] = 0;
+    lvl[1] = nsys;
+    *ovf = 0;
+  }
   if (s >= nsys) return;
   begin[s] = static_cast<int32_t>(off[s]);
   count[s] = static_cast<int32_t>(off[s + 1] - off[s]);
@@ -254,12 +260,16 @@ __global__ void k_permute(const double *__restrict__ x, const double *__restrict
 // A body starts a child cell at level lev+1 when its cell at level lev is split
 // and it is the cell's first body or its key differs from its predecessor's
 // in digit lev+1.
+// The level kernels read the level's first new cell id from lvl[lev + 1]
+// (device-resident, so that several levels are enqueued before the host
+// looks) and do nothing once a level has run out of cell capacity (*ovf).
 __global__ void k_level_flags(int64_t n, int lev, int n_crit, const int32_t *__restrict__ lcp,
                               const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
                               const int32_t *__restrict__ cur, int32_t *__restrict__ flag,
-                              int32_t *__restrict__ cell_at_lev, int32_t *__restrict__ leaf_of) {
+                              int32_t *__restrict__ cell_at_lev, int32_t *__restrict__ leaf_of,
+                              const int *__restrict__ ovf) {
   int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || *ovf) return;
   const int c = cur[i];
   cell_at_lev[i] = c;
   int f = 0;
@@ -271,15 +281,22 @@ __global__ void k_level_flags(int64_t n, int lev, int n_crit, const int32_t *__r
   flag[i] = f;
 }
 
-__global__ void k_make_cells(int64_t n, int lev, int32_t off, const int32_t *__restrict__ flag,
-                             const int32_t *__restrict__ excl, const int32_t *__restrict__ cur,
-                             int32_t *__restrict__ begin, int32_t *__restrict__ level,
-                             int32_t *__restrict__ parent, int32_t *__restrict__ first_child,
-                             int32_t *__restrict__ nchild) {
+// Also closes the level: lvl[lev + 2] = lvl[lev + 1] + (new cells).
+__global__ void k_make_cells(int64_t n, int lev, int32_t *__restrict__ lvl, const int32_t *__restrict__ ntot,
+                             int64_t cap, const int32_t *__restrict__ flag, const int32_t *__restrict__ excl,
+                             const int32_t *__restrict__ cur, int32_t *__restrict__ begin,
+                             int32_t *__restrict__ level, int32_t *__restrict__ parent,
+                             int32_t *__restrict__ first_child, int32_t *__restrict__ nchild, int *__restrict__ ovf) {
   int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (i >= n || !flag[i]) return;
+  const int off = lvl[lev + 1];
+  if (i == 0) {
+    lvl[lev + 2] = off + *ntot;
+    if (static_cast<int64_t>(off) + *ntot > cap) atomicOr(ovf, 1);
+  }
+  if (i >= n || !flag[i] || *ovf) return;
   const int c = cur[i];
   const int id = off + excl[i];
+  if (id >= cap) return;  // flagged above; the tree is built again with more room
   begin[id] = static_cast<int32_t>(i);
   level[id] = lev + 1;
   parent[id] = c;
@@ -288,11 +305,12 @@ __global__ void k_make_cells(int64_t n, int lev, int32_t off, const int32_t *__r
   if (i == begin[c]) first_child[c] = id;
 }
 
-__global__ void k_cell_counts(int32_t off, int32_t nnew, int32_t *__restrict__ begin,
+__global__ void k_cell_counts(int lev, const int32_t *__restrict__ lvl, int32_t *__restrict__ begin,
                               int32_t *__restrict__ count, const int32_t *__restrict__ parent,
-                              int32_t *__restrict__ nchild) {
+                              int32_t *__restrict__ nchild, const int *__restrict__ ovf) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nnew) return;
+  const int off = lvl[lev + 1], nnew = lvl[lev + 2] - off;
+  if (k >= nnew || *ovf) return;
   const int id = off + k;
   const int p = parent[id];
   int end = begin[p] + count[p];
@@ -304,14 +322,15 @@ __global__ void k_cell_counts(int32_t off, int32_t nnew, int32_t *__restrict__ b
 // Next level's cell of every body: -1 for a body of a leaf (retired); a body
 // of a split cell moves to the child that starts at the last flagged body at
 // or before it (same cell).
-__global__ void k_update_cur(int64_t n, int lev, int n_crit, int32_t off, const int32_t *__restrict__ count,
-                             const int32_t *__restrict__ flag, const int32_t *__restrict__ excl,
-                             int32_t *__restrict__ cur) {
+__global__ void k_update_cur(int64_t n, int lev, int n_crit, const int32_t *__restrict__ lvl,
+                             const int32_t *__restrict__ count, const int32_t *__restrict__ flag,
+                             const int32_t *__restrict__ excl, int32_t *__restrict__ cur,
+                             const int *__restrict__ ovf) {
   int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || *ovf) return;
   const int c = cur[i];
   if (c < 0) return;
-  cur[i] = (count[c] <= n_crit || lev == kMaxLevel) ? -1 : off + excl[i] + flag[i] - 1;
+  cur[i] = (count[c] <= n_crit || lev == kMaxLevel) ? -1 : lvl[lev + 1] + excl[i] + flag[i] - 1;
 }
 
 __global__ void k_leaf_flags(int32_t ncell, const int32_t *__restrict__ nchild, int32_t *__restrict__ f) {
@@ -588,14 +607,14 @@ int build_tree(fmm_ctx *c) {
   AMFMM_TRY(ensure<int32_t>(c, c->incl, n + 1));
   AMFMM_TRY(ensure<int32_t>(c, c->leaf_of, n));
   AMFMM_TRY(ensure<int32_t>(c, c->cell_at, static_cast<size_t>(kMaxLevel + 1) * n));
-  AMFMM_TRY(ensure<int>(c, c->status, 4));
+  AMFMM_TRY(ensure<int>(c, c->status, 8 + kMaxLevel + 3));
   const int nbb = std::max(1, std::min<int>(c->num_sms * 4, static_cast<int>((n + kBlock - 1) / kBlock)));
   AMFMM_TRY(ensure<double>(c, c->bbox_part, 6 * nbb));
   AMFMM_TRY(ensure<double>(c, c->bbox, 8));
   
 
   int *status = ptr<int>(c->status);
-  AMFMM_CUDA(c, cudaMemsetAsync(status, 0, sizeof(int) * 4, st));
+  AMFMM_CUDA(c, cudaMemsetAsync(status, 0, sizeof(int) * (8 + kMaxLevel + 3), st));
   const int nsys = c->sz.nsys;
   int which = 0;
   if (nsys == 1) {
@@ -637,59 +656,88 @@ int build_tree(fmm_ctx *c) {
   const uint32_t *sidx = ptr<uint32_t>(c->idx[which]);
   AMFMM_TRY(ensure<int32_t>(c, c->lcp, n));
   int32_t *lcp = ptr<int32_t>(c->lcp);
-  k_permute<<<grid_for(n, kBlock), kBlock, 0, st>>>(c->x, c->y, c->z, c->m, skey, sidx, n,
-                                                    ptr<double>(c->X), ptr<double>(c->Y),
-                                                    ptr<double>(c->Zb), ptr<double>(c->Mb),
-                                                    ptr<int32_t>(c->order), lcp, ptr<int32_t>(c->cur),
-                                                    nsys == 1 ? nullptr : ptr<int32_t>(c->sysid));
-  AMFMM_TRY(launched(c, "permute"));
   c->sz.key_which = which;
 
-  // octree level by level, from one root per system
-  int64_t cap_cells = std::max<int64_t>(std::max<int64_t>(1024, n / 2 + 64), 2 * static_cast<int64_t>(nsys));
-  AMFMM_TRY(ensure_cells(c, cap_cells, 0));
-  k_roots<<<grid_for(nsys, kBlock), kBlock, 0, st>>>(nsys, ptr<int64_t>(c->sys_off), ptr<int32_t>(c->begin),
-                                                     ptr<int32_t>(c->count), ptr<int32_t>(c->level),
-                                                     ptr<int32_t>(c->parent), ptr<int32_t>(c->first_child),
-                                                     ptr<int32_t>(c->nchild));
-  AMFMM_TRY(launched(c, "roots"));
-  c->sz.lvl_off.assign({0, static_cast<int64_t>(nsys)});
+  // Octree level by level, from one root per system.  The levels' first cell
+  // ids live on the device (lvl), so levels are enqueued in batches and the
+  // host reads the counts once per batch: the first batch runs as many
+  // levels as the previous tree had (a repeated or slowly changing system
+  // needs one round trip), later ones two at a time.  Levels past the last
+  // find no body left and do nothing.  A level that runs out of cell room
+  // stops the batch; the tree is then built again with twice the room.
+  int *ovf = status + 1;
+  int32_t *lvl = reinterpret_cast<int32_t *>(status + 8);  // kMaxLevel + 3 entries
   int32_t *flag = ptr<int32_t>(c->flag);
   int32_t *excl = ptr<int32_t>(c->incl);
   int32_t *total = ptr<int32_t>(c->totals);
+  int64_t cap_cells = std::max<int64_t>(std::max<int64_t>(1024, n / 2 + 64), 2 * static_cast<int64_t>(nsys));
   int lev = 0;
-  for (;; ++lev) {
-    const int64_t off = c->sz.lvl_off.back();
-    k_level_flags<<<grid_for(n, kBlock), kBlock, 0, st>>>(
-        n, lev, c->opts.n_crit, lcp, ptr<int32_t>(c->begin), ptr<int32_t>(c->count),
-        ptr<int32_t>(c->cur), flag, ptr<int32_t>(c->cell_at) + static_cast<int64_t>(lev) * n,
-        ptr<int32_t>(c->leaf_of));
-    AMFMM_TRY(launched(c, "level_flags"));
-    AMFMM_TRY(exclusive_scan_i32(c, flag, excl, n, total));
+  for (int attempt = 0;; ++attempt) {
+    if (attempt > 16) return set_error(c, FMM_EINVAL, "octree: cell room still short after growing");
+    AMFMM_TRY(ensure_cells(c, cap_cells, 0));
+    const int64_t cap = static_cast<int64_t>(std::min({c->begin.cap, c->count.cap, c->level.cap, c->parent.cap,
+                                                       c->first_child.cap, c->nchild.cap}) /
+                                             sizeof(int32_t));
+    k_permute<<<grid_for(n, kBlock), kBlock, 0, st>>>(c->x, c->y, c->z, c->m, skey, sidx, n,
+                                                      ptr<double>(c->X), ptr<double>(c->Y),
+                                                      ptr<double>(c->Zb), ptr<double>(c->Mb),
+                                                      ptr<int32_t>(c->order), lcp, ptr<int32_t>(c->cur),
+                                                      nsys == 1 ? nullptr : ptr<int32_t>(c->sysid));
+    AMFMM_TRY(launched(c, "permute"));
+    k_roots<<<grid_for(nsys, kBlock), kBlock, 0, st>>>(nsys, ptr<int64_t>(c->sys_off), ptr<int32_t>(c->begin),
+                                                       ptr<int32_t>(c->count), ptr<int32_t>(c->level),
+                                                       ptr<int32_t>(c->parent), ptr<int32_t>(c->first_child),
+                                                       ptr<int32_t>(c->nchild), lvl, ovf);
+    AMFMM_TRY(launched(c, "roots"));
+    bool done = false, over = false;
     int32_t *h = static_cast<int32_t *>(c->hpin);
-    AMFMM_CUDA(c, cudaMemcpyAsync(h, total, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    AMFMM_CUDA(c, cudaStreamSynchronize(st));
-    const int64_t nnew = h[0];
-    if (nnew == 0) break;
-    if (off + nnew > cap_cells) {
-      int64_t want = std::max<int64_t>(cap_cells * 2, off + nnew + 1024);
-      AMFMM_TRY(ensure_cells(c, want, off));
-      cap_cells = want;
+    for (lev = 0; !done;) {
+      const int batch = lev == 0 ? std::max(1, c->last_depth + 1) : 2;
+      const int lev_end = std::min(lev + batch, kMaxLevel + 1);
+      for (int l = lev; l < lev_end; ++l) {
+        k_level_flags<<<grid_for(n, kBlock), kBlock, 0, st>>>(
+            n, l, c->opts.n_crit, lcp, ptr<int32_t>(c->begin), ptr<int32_t>(c->count), ptr<int32_t>(c->cur),
+            flag, ptr<int32_t>(c->cell_at) + static_cast<int64_t>(l) * n, ptr<int32_t>(c->leaf_of), ovf);
+        AMFMM_TRY(launched(c, "level_flags"));
+        AMFMM_TRY(exclusive_scan_i32(c, flag, excl, n, total));
+        k_make_cells<<<grid_for(n, kBlock), kBlock, 0, st>>>(
+            n, l, lvl, total, cap, flag, excl, ptr<int32_t>(c->cur), ptr<int32_t>(c->begin),
+            ptr<int32_t>(c->level), ptr<int32_t>(c->parent), ptr<int32_t>(c->first_child),
+            ptr<int32_t>(c->nchild), ovf);
+        AMFMM_TRY(launched(c, "make_cells"));
+        // no more new cells than bodies
+        k_cell_counts<<<grid_for(n, kBlock), kBlock, 0, st>>>(l, lvl, ptr<int32_t>(c->begin), ptr<int32_t>(c->count),
+                                                             ptr<int32_t>(c->parent), ptr<int32_t>(c->nchild), ovf);
+        AMFMM_TRY(launched(c, "cell_counts"));
+        k_update_cur<<<grid_for(n, kBlock), kBlock, 0, st>>>(n, l, c->opts.n_crit, lvl, ptr<int32_t>(c->count),
+                                                             flag, excl, ptr<int32_t>(c->cur), ovf);
+        AMFMM_TRY(launched(c, "update_cur"));
+      }
+      AMFMM_CUDA(c, cudaMemcpyAsync(h, status, sizeof(int) * (8 + kMaxLevel + 3), cudaMemcpyDeviceToHost, st));
+      AMFMM_CUDA(c, cudaStreamSynchronize(st));
+      const int32_t *hl = h + 8;
+      if (h[1]) {  // out of cell room: grow beyond what the levels so far asked for
+        int64_t need = cap;
+        for (int l = 0; l < lev_end; ++l) need = std::max<int64_t>(need, hl[l + 2]);
+        cap_cells = std::max<int64_t>(2 * cap, need + n / 2 + 64);
+        over = true;
+        break;
+      }
+      for (int l = lev; l < lev_end && !done; ++l)
+        if (hl[l + 2] == hl[l + 1]) {  // level l made no new cells: the tree is complete
+          done = true;
+          lev = l;
+        }
+      if (!done) {
+        if (lev_end > kMaxLevel) return set_error(c, FMM_EINVAL, "octree: cells below the deepest level");
+        lev = lev_end;
+      }
     }
-    k_make_cells<<<grid_for(n, kBlock), kBlock, 0, st>>>(
-        n, lev, static_cast<int32_t>(off), flag, excl, ptr<int32_t>(c->cur), ptr<int32_t>(c->begin),
-        ptr<int32_t>(c->level), ptr<int32_t>(c->parent), ptr<int32_t>(c->first_child),
-        ptr<int32_t>(c->nchild));
-    AMFMM_TRY(launched(c, "make_cells"));
-    k_cell_counts<<<grid_for(nnew, kBlock), kBlock, 0, st>>>(
-        static_cast<int32_t>(off), static_cast<int32_t>(nnew), ptr<int32_t>(c->begin),
-        ptr<int32_t>(c->count), ptr<int32_t>(c->parent), ptr<int32_t>(c->nchild));
-    AMFMM_TRY(launched(c, "cell_counts"));
-    k_update_cur<<<grid_for(n, kBlock), kBlock, 0, st>>>(n, lev, c->opts.n_crit, static_cast<int32_t>(off),
-                                                         ptr<int32_t>(c->count), flag, excl, ptr<int32_t>(c->cur));
-    AMFMM_TRY(launched(c, "update_cur"));
-    c->sz.lvl_off.push_back(off + nnew);
+    if (over) continue;
+    c->sz.lvl_off.assign(h + 8, h + 8 + lev + 2);
+    break;
   }
+  c->last_depth = lev;
   c->sz.depth = lev;
   c->sz.ncell = c->sz.lvl_off.back();
   // leaves in id order
