@@ -377,3 +377,30 @@ def test_bounded_wait_returns_timeout_and_context_survives():
     a = torch.stack(s.solve(x, y, z, m), 1).cpu().numpy()
     ref = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25).accel("TC")
     assert _rel_dev(a, ref).max() <= 1e-12
+
+
+def test_tree_levels_on_a_reused_context():
+    """The tree is built in batches of levels sized by the previous tree's
+    depth.  One context solves a deep system, a shallow one, the deep one
+    again and then a system whose tree outgrows the cell room of the first
+    build (one body per leaf): every tree, list set and FP64 result must
+    match the oracle."""
+    from paper_1706_06989_gb300 import fmm
+    deep = ics.plummer(6000, seed=21)
+    shallow = ics.uniform_cube(1500, seed=22)
+    s = fmm.FMM(theta=0.5, n_crit=25, variant="TC", precision="fp64")
+    depths = []
+    for b, n_crit in ((deep, 25), (shallow, 25), (deep, 25), (deep, 1)):
+        s.set_opts(n_crit=n_crit)
+        x, y, z, m = _dev(b)
+        a = torch.stack(s.solve(x, y, z, m), 1).cpu().numpy()
+        o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, n_crit)
+        _compare_tree(s, o)
+        m2l, p2p, slf = s.export_lists()
+        om2l, op2p, oslf = o.lists()
+        assert np.array_equal(_canon_pairs(m2l.cpu().numpy()), _canon_pairs(om2l))
+        assert np.array_equal(_canon_pairs(p2p.cpu().numpy()), _canon_pairs(op2p))
+        assert _rel_dev(a, o.accel("TC")).max() <= 1e-12
+        depths.append(s.stats().depth)
+    assert depths[0] > depths[1] and depths[3] > depths[0]
+    assert s.stats().ncell > 6000 // 2 + 64  # beyond the first build's cell room
