@@ -70,8 +70,6 @@ __device__ __forceinline__ T acc_get(const P2PSmem<T> &sm, int v, int t) { retur
 template <class T>
 __device__ __forceinline__ T p2p_min_r2();
 template <>
-__device__ __forceinline__ double p2p_min_r2<double>() { return 0.0; }
-template <>
 __device__ __forceinline__ float p2p_min_r2<float>() { return 1e-30f; }
 // r2 above that bound; FP64 tests r2 != +0 on its bit pattern (r2 is a sum of
 // squares, so never negative) to keep the comparison off the FP64 pipe
@@ -435,14 +433,19 @@ __global__ void k_p2p_reduce(int64_t n, const int32_t *__restrict__ leaf_of, con
   near[2 * n + i] = a2;
 }
 
+// Sort keys of the pairs by one side, the per-cell pair counts, and (if nb is
+// given) every pair's column count n_B.
 __global__ void k_pair_keys(int64_t K, const int2 *__restrict__ pairs, int side, uint32_t *__restrict__ key,
-                            uint32_t *__restrict__ val, int32_t *__restrict__ cnt) {
+                            uint32_t *__restrict__ val, int32_t *__restrict__ cnt,
+                            const int32_t *__restrict__ count, int32_t *__restrict__ nb) {
   const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (k >= K) return;
-  const int c = side == 0 ? pairs[k].x : pairs[k].y;
+  const int2 p = pairs[k];
+  const int c = side == 0 ? p.x : p.y;
   key[k] = static_cast<uint32_t>(c);
   val[k] = static_cast<uint32_t>(k);
   atomicAdd(&cnt[c], 1);
+  if (nb) nb[k] = count[p.y];
 }
 
 __global__ void k_gather_pairs(int64_t K, const int2 *__restrict__ in, const uint32_t *__restrict__ sval,
@@ -471,19 +474,25 @@ int bits_for(int64_t v) {
 // Columns of every leaf: first its own bodies (marked -1: one-sided), then the
 // bodies of its partner leaves in the A-sorted pair order, each with the slot
 // that receives its B-side partial.
-__global__ void k_col_count_pairs(int64_t K, const int2 *__restrict__ pairs, const int32_t *__restrict__ count,
-                                  int32_t *__restrict__ ccount, int32_t *__restrict__ nb) {
-  const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (k >= K) return;
-  const int2 p = pairs[k];
-  nb[k] = count[p.y];
-  atomicAdd(&ccount[p.x], count[p.y]);
-}
-
-__global__ void k_col_count_leaves(int32_t nleaf, const int32_t *__restrict__ leaves,
-                                   const int32_t *__restrict__ count, int32_t *__restrict__ ccount) {
+// Column count of every leaf A: its own bodies plus, from the prefix sums
+// pre of the partners' sizes over the A-sorted pairs, the bodies of its
+// partners.  Also the near-field work: n_A n_B per leaf pair plus
+// n (n - 1) / 2 per leaf (one atomic per warp, integer: exact).
+__global__ void k_leaf_cols(int32_t nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ count,
+                            const int32_t *__restrict__ offA, const int32_t *__restrict__ pre,
+                            int32_t *__restrict__ ccount, unsigned long long *__restrict__ work) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < nleaf) ccount[leaves[q]] += count[leaves[q]];
+  unsigned long long v = 0;
+  if (q < nleaf) {
+    const int L = leaves[q];
+    const int a = count[L];
+    const int cols = pre ? pre[offA[L + 1]] - pre[offA[L]] : 0;
+    ccount[L] = a + cols;
+    v = static_cast<unsigned long long>(a) * cols + static_cast<unsigned long long>(a) * (a - 1) / 2;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(work, v);
 }
 
 __global__ void k_cols_self(int32_t nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin,
@@ -501,29 +510,46 @@ __global__ void k_cols_pairs(int64_t K, const int2 *__restrict__ pairs, const in
                              const int32_t *__restrict__ offA, const int32_t *__restrict__ pre,
                              const int32_t *__restrict__ pos, const int64_t *__restrict__ poff,
                              int2 *__restrict__ cols) {
+  // A warp writes the runs of its 32 pairs together: entry j of the warp's
+  // concatenated runs goes to lane j mod 32, which finds the pair owning it
+  // by a binary search over the warp's prefix sums, so consecutive lanes
+  // store consecutive entries of a run.
   const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (k >= K) return;
-  const int2 p = pairs[k];
-  const int base = colOff[p.x] + count[p.x] + (pre[k] - pre[offA[p.x]]);
-  const int bB = begin[p.y];
-  const int64_t o = poff[pos[k]];
-  for (int t = 0; t < count[p.y]; ++t) cols[base + t] = make_int2(bB + t, static_cast<int32_t>(o + 3 * t));
-}
-
-// near-field work: n_A n_B per leaf pair plus n (n - 1) / 2 per leaf
-__global__ void k_p2p_work(int64_t K, const int2 *__restrict__ pairs, int32_t nleaf,
-                           const int32_t *__restrict__ leaves, const int32_t *__restrict__ count,
-                           unsigned long long *__restrict__ out) {
-  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  unsigned long long v = 0;
-  if (t < K) v = static_cast<unsigned long long>(count[pairs[t].x]) * count[pairs[t].y];
-  else if (t < K + nleaf) {
-    const unsigned long long a = count[leaves[t - K]];
-    v = a * (a - 1) / 2;
+  const int lane = threadIdx.x & 31;
+  int nB = 0, base = 0, bB = 0;
+  long long o = 0;
+  if (k < K) {
+    const int2 p = pairs[k];
+    base = colOff[p.x] + count[p.x] + (pre[k] - pre[offA[p.x]]);
+    bB = begin[p.y];
+    o = poff[pos[k]];
+    nB = count[p.y];
   }
+  int incl = nB;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  const int excl = incl - nB;
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  for (int j0 = 0; j0 < total; j0 += 32) {
+    const int j = j0 + lane;
+    int own = 0;  // number of lanes whose run ends at or before j
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int e = __shfl_sync(0xffffffffu, incl, own + step - 1);
+      if (e <= j) own += step;
+    }
+    own = min(own, 31);
+    const int b = __shfl_sync(0xffffffffu, base, own), x = __shfl_sync(0xffffffffu, excl, own);
+    const int bb = __shfl_sync(0xffffffffu, bB, own);
+    const long long oo = __shfl_sync(0xffffffffu, o, own);
+    if (j < total) {
+      const int t = j - x;
+      cols[b + t] = make_int2(bb + t, static_cast<int32_t>(oo + 3 * t));
+    }
+  }
 }
 
 template <class T>
@@ -591,6 +617,9 @@ int p2p_prepare(fmm_ctx *c) {
                                                ptr<double>(c->Mb), ptr<BodyF>(c->p2p_bodyf));
     AMFMM_TRY(launched(c, "p2p_body32"));
   }
+  AMFMM_TRY(ensure<int32_t>(c, c->p2p_nb, K + 1));
+  AMFMM_TRY(ensure<int32_t>(c, c->p2p_pre, K + 1));
+  int32_t *nb = ptr<int32_t>(c->p2p_nb), *pre = ptr<int32_t>(c->p2p_pre);
   int64_t *h = static_cast<int64_t *>(c->hpin);
   h[0] = 0;
   if (K > 0) {
@@ -599,7 +628,7 @@ int p2p_prepare(fmm_ctx *c) {
     // group by A (stable)
     AMFMM_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nc + 1), st));
     k_pair_keys<<<grid_for(K, 256), 256, 0, st>>>(K, ptr<int2>(c->p2p), 0, ptr<uint32_t>(c->pkey[0]),
-                                                  ptr<uint32_t>(c->pval[0]), cnt);
+                                                  ptr<uint32_t>(c->pval[0]), cnt, nullptr, nullptr);
     AMFMM_TRY(launched(c, "p2p_keysA"));
     AMFMM_TRY(exclusive_scan_i32(c, cnt, offA, nc + 1, nullptr));
     int which = 0;
@@ -607,10 +636,10 @@ int p2p_prepare(fmm_ctx *c) {
     k_gather_pairs<<<grid_for(K, 256), 256, 0, st>>>(K, ptr<int2>(c->p2p), ptr<uint32_t>(c->pval[which]),
                                                      ptr<int2>(c->p2p_A));
     AMFMM_TRY(launched(c, "p2p_gather"));
-    // CSR on the B side
+    // CSR on the B side; column counts n_B in A-sorted order
     AMFMM_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nc + 1), st));
     k_pair_keys<<<grid_for(K, 256), 256, 0, st>>>(K, ptr<int2>(c->p2p_A), 1, ptr<uint32_t>(c->pkey[0]),
-                                                  ptr<uint32_t>(c->pval[0]), cnt);
+                                                  ptr<uint32_t>(c->pval[0]), cnt, ptr<int32_t>(c->count), nb);
     AMFMM_TRY(launched(c, "p2p_keysB"));
     AMFMM_TRY(exclusive_scan_i32(c, cnt, offB, nc + 1, nullptr));
     AMFMM_TRY(radix_sort_u32(c, c->pkey, c->pval, K, bits_for(nc), &which));
@@ -624,20 +653,17 @@ int p2p_prepare(fmm_ctx *c) {
     AMFMM_TRY(exclusive_scan_i64(c, len, ptr<int64_t>(c->p2p_poff), K, ptot));
     AMFMM_CUDA(c, cudaMemcpyAsync(h, ptot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   }
-  // column stream per leaf
-  AMFMM_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nc + 1), st));
-  AMFMM_TRY(ensure<int32_t>(c, c->p2p_nb, K + 1));
-  int32_t *nb = ptr<int32_t>(c->p2p_nb);
+  // column stream per leaf: pre = prefix sums of n_B over the A-sorted pairs
+  // (K + 1 entries, so pre[K] is the total)
   if (K > 0) {
-    k_col_count_pairs<<<grid_for(K, 256), 256, 0, st>>>(K, ptr<int2>(c->p2p_A), ptr<int32_t>(c->count), cnt, nb);
-    AMFMM_TRY(launched(c, "p2p_col_count_pairs"));
+    AMFMM_CUDA(c, cudaMemsetAsync(nb + K, 0, sizeof(int32_t), st));
+    AMFMM_TRY(exclusive_scan_i32(c, nb, pre, K + 1, nullptr));
   }
-  k_col_count_leaves<<<grid_for(nleaf, 256), 256, 0, st>>>(nleaf, ptr<int32_t>(c->leaves), ptr<int32_t>(c->count), cnt);
-  AMFMM_TRY(launched(c, "p2p_col_count_leaves"));
+  AMFMM_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nc + 1), st));
+  k_leaf_cols<<<grid_for(nleaf, 256), 256, 0, st>>>(nleaf, ptr<int32_t>(c->leaves), ptr<int32_t>(c->count), offA,
+                                                    K > 0 ? pre : nullptr, cnt, stat);
+  AMFMM_TRY(launched(c, "p2p_leaf_cols"));
   AMFMM_TRY(exclusive_scan_i32(c, cnt, colOff, nc + 1, ctot));
-  k_p2p_work<<<grid_for(K + nleaf, 256), 256, 0, st>>>(K, ptr<int2>(c->p2p_A), nleaf, ptr<int32_t>(c->leaves),
-                                                       ptr<int32_t>(c->count), stat);
-  AMFMM_TRY(launched(c, "p2p_work"));
   // work items: chunks of the column streams
   AMFMM_TRY(ensure<int32_t>(c, c->p2p_itemOff, nleaf + 1));
   AMFMM_TRY(ensure<int32_t>(c, c->p2p_extraOff, nleaf + 1));
@@ -670,10 +696,8 @@ int p2p_prepare(fmm_ctx *c) {
                                                     ptr<int32_t>(c->count), colOff, ptr<int2>(c->p2p_cols));
   AMFMM_TRY(launched(c, "p2p_cols_self"));
   if (K > 0) {
-    AMFMM_TRY(ensure<int32_t>(c, c->p2p_pre, K + 1));
-    AMFMM_TRY(exclusive_scan_i32(c, nb, ptr<int32_t>(c->p2p_pre), K, nullptr));
     k_cols_pairs<<<grid_for(K, 256), 256, 0, st>>>(K, ptr<int2>(c->p2p_A), ptr<int32_t>(c->begin),
-                                                   ptr<int32_t>(c->count), colOff, offA, ptr<int32_t>(c->p2p_pre),
+                                                   ptr<int32_t>(c->count), colOff, offA, pre,
                                                    ptr<int32_t>(c->p2p_pos), ptr<int64_t>(c->p2p_poff),
                                                    ptr<int2>(c->p2p_cols));
     AMFMM_TRY(launched(c, "p2p_cols_pairs"));

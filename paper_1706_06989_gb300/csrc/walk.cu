@@ -65,7 +65,14 @@ __device__ __forceinline__ int classify(int A, int B, const int2 *__restrict__ n
     cnt.x = k + k * (k - 1) / 2;
     return kSelfSplit;
   }
-  int sep = accept_hint ? 1 : separated_fast(zf[A], zf[B], th2f);
+  int sep = 1;
+  float rA = 0.f, rB = 0.f;  // FP32 R_max, kept for the split choice
+  if (!accept_hint) {
+    const CellF fA = zf[A], fB = zf[B];
+    sep = separated_fast(fA, fB, th2f);
+    rA = fA.h.w;
+    rB = fB.h.w;
+  }
   if (sep < 0) sep = well_separated(zr[A], zr[B], theta);
   if (sep) {
     cnt.y = 1;
@@ -80,7 +87,11 @@ __device__ __forceinline__ int classify(int A, int B, const int2 *__restrict__ n
   bool pickA;
   if (kb == 0) pickA = true;
   else if (ka == 0) pickA = false;
-  else {
+  else if (rA != rB) {
+    // R_max rounded to FP32 (monotone rounding): unequal FP32 values order
+    // the FP64 values the same way, strictly
+    pickA = rA > rB;
+  } else {
     const double ra = zr[A].w, rb = zr[B].w;
     if (ra != rb) pickA = ra > rb;
     else if (nlA.y != nlB.y) pickA = nlA.y < nlB.y;
