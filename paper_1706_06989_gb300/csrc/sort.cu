@@ -9,6 +9,7 @@ namespace {
 constexpr int kScanBlock = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanBlock * kScanItems;
+constexpr int kRedundantTiles = 4096;  // up to 8M elements: two launches per scan
 
 constexpr int kSortBlock = 256;
 constexpr int kSortItems = 16;
@@ -86,12 +87,21 @@ __global__ void k_tile_reduce(const T *__restrict__ in, int64_t n, T *__restrict
   if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
-// Exclusive scan of one tile; tile offsets come from `offs` (or zero), and
-// the last tile writes the grand total.
+// Exclusive scan of one tile; the tile's offset is offs[tile] when offs is
+// given, else the sum of the tile sums sums[0, tile) taken by this block
+// (integer addition: exact in any order), else zero.  The last tile writes
+// the grand total.
 template <class T>
 __global__ void k_tile_scan(const T *__restrict__ in, T *__restrict__ out, int64_t n,
-                            const T *__restrict__ offs, T *__restrict__ total) {
+                            const T *__restrict__ offs, T *__restrict__ total,
+                            const T *__restrict__ sums = nullptr) {
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile;
+  T pre = vzero<T>();
+  if (!offs && sums) {
+    for (int q = threadIdx.x; q < static_cast<int>(blockIdx.x); q += kScanBlock) pre = vadd(pre, sums[q]);
+    T ignore;
+    pre = block_exclusive(pre, &ignore);  // the block total of the partial sums
+  }
   // each thread owns kScanItems consecutive elements
   T v[kScanItems];
   const int64_t mybase = base + static_cast<int64_t>(threadIdx.x) * kScanItems;
@@ -104,7 +114,7 @@ __global__ void k_tile_scan(const T *__restrict__ in, T *__restrict__ out, int64
   }
   T excl;
   T tot = block_exclusive(s, &excl);
-  T off = offs ? offs[blockIdx.x] : vzero<T>();
+  T off = offs ? offs[blockIdx.x] : pre;
   T run = vadd(off, excl);
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
@@ -137,6 +147,12 @@ int scan_impl(fmm_ctx *c, const T *in, T *out, int64_t n, T *total, size_t tmp_o
   size_t next = tmp_off + ((2 * static_cast<size_t>(nt) * sizeof(T) + 255) / 256) * 256;
   k_tile_reduce<T><<<static_cast<unsigned>(nt), kScanBlock, 0, c->stream>>>(in, n, sums);
   AMFMM_TRY(launched(c, "tile_reduce"));
+  if (nt <= kRedundantTiles) {
+    // few tiles: every block adds up the sums of the tiles before it (at
+    // most kRedundantTiles reads, from L2) instead of a separate scan of them
+    k_tile_scan<T><<<static_cast<unsigned>(nt), kScanBlock, 0, c->stream>>>(in, out, n, nullptr, total, sums);
+    return launched(c, "tile_scan");
+  }
   AMFMM_TRY(scan_impl<T>(c, sums, offs, nt, nullptr, next));
   k_tile_scan<T><<<static_cast<unsigned>(nt), kScanBlock, 0, c->stream>>>(in, out, n, offs, total);
   return launched(c, "tile_scan");
