@@ -263,14 +263,23 @@ __global__ void k_permute(const double *__restrict__ x, const double *__restrict
 // The level kernels read the level's first new cell id from lvl[lev + 1]
 // (device-resident, so that several levels are enqueued before the host
 // looks) and do nothing once a level has run out of cell capacity (*ovf).
+// From the second level on it first moves every body to its cell of this
+// level: -1 for a body of a leaf of the previous level (retired), else the
+// child of its previous cell that starts at the last flagged body at or
+// before it (same cell), from that level's flags and their exclusive sums.
 __global__ void k_level_flags(int64_t n, int lev, int n_crit, const int32_t *__restrict__ lcp,
                               const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
-                              const int32_t *__restrict__ cur, int32_t *__restrict__ flag,
+                              int32_t *__restrict__ cur, int32_t *__restrict__ flag,
+                              const int32_t *__restrict__ excl, const int32_t *__restrict__ lvl,
                               int32_t *__restrict__ cell_at_lev, int32_t *__restrict__ leaf_of,
                               const int *__restrict__ ovf) {
   int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= n || *ovf) return;
-  const int c = cur[i];
+  int c = cur[i];
+  if (lev > 0 && c >= 0) {
+    c = count[c] <= n_crit ? -1 : lvl[lev] + excl[i] + flag[i] - 1;
+    cur[i] = c;
+  }
   cell_at_lev[i] = c;
   int f = 0;
   if (c >= 0) {
@@ -317,20 +326,6 @@ __global__ void k_cell_counts(int lev, const int32_t *__restrict__ lvl, int32_t 
   if (k + 1 < nnew) end = min(end, begin[id + 1]);
   count[id] = end - begin[id];
   atomicAdd(&nchild[p], 1);
-}
-
-// Next level's cell of every body: -1 for a body of a leaf (retired); a body
-// of a split cell moves to the child that starts at the last flagged body at
-// or before it (same cell).
-__global__ void k_update_cur(int64_t n, int lev, int n_crit, const int32_t *__restrict__ lvl,
-                             const int32_t *__restrict__ count, const int32_t *__restrict__ flag,
-                             const int32_t *__restrict__ excl, int32_t *__restrict__ cur,
-                             const int *__restrict__ ovf) {
-  int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (i >= n || *ovf) return;
-  const int c = cur[i];
-  if (c < 0) return;
-  cur[i] = (count[c] <= n_crit || lev == kMaxLevel) ? -1 : lvl[lev + 1] + excl[i] + flag[i] - 1;
 }
 
 __global__ void k_leaf_flags(int32_t ncell, const int32_t *__restrict__ nchild, int32_t *__restrict__ f) {
@@ -697,7 +692,7 @@ int build_tree(fmm_ctx *c) {
       for (int l = lev; l < lev_end; ++l) {
         k_level_flags<<<grid_for(n, kBlock), kBlock, 0, st>>>(
             n, l, c->opts.n_crit, lcp, ptr<int32_t>(c->begin), ptr<int32_t>(c->count), ptr<int32_t>(c->cur),
-            flag, ptr<int32_t>(c->cell_at) + static_cast<int64_t>(l) * n, ptr<int32_t>(c->leaf_of), ovf);
+            flag, excl, lvl, ptr<int32_t>(c->cell_at) + static_cast<int64_t>(l) * n, ptr<int32_t>(c->leaf_of), ovf);
         AMFMM_TRY(launched(c, "level_flags"));
         AMFMM_TRY(exclusive_scan_i32(c, flag, excl, n, total));
         k_make_cells<<<grid_for(n, kBlock), kBlock, 0, st>>>(
@@ -709,9 +704,6 @@ int build_tree(fmm_ctx *c) {
         k_cell_counts<<<grid_for(n, kBlock), kBlock, 0, st>>>(l, lvl, ptr<int32_t>(c->begin), ptr<int32_t>(c->count),
                                                              ptr<int32_t>(c->parent), ptr<int32_t>(c->nchild), ovf);
         AMFMM_TRY(launched(c, "cell_counts"));
-        k_update_cur<<<grid_for(n, kBlock), kBlock, 0, st>>>(n, l, c->opts.n_crit, lvl, ptr<int32_t>(c->count),
-                                                             flag, excl, ptr<int32_t>(c->cur), ovf);
-        AMFMM_TRY(launched(c, "update_cur"));
       }
       AMFMM_CUDA(c, cudaMemcpyAsync(h, status, sizeof(int) * (8 + kMaxLevel + 3), cudaMemcpyDeviceToHost, st));
       AMFMM_CUDA(c, cudaStreamSynchronize(st));
