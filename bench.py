@@ -42,9 +42,9 @@ M2L_FLOPS = {"UC": 174, "TC": 295, "TCO": 276}
 # DRAM traffic of the dominant kernel per unit it processes, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of a launch at the
 # bench workload (Plummer N = 1,048,576, theta = 0.5, TC): k_p2p<double>
-# read 387,522,048 B and wrote 866,940,160 B for 421,686,939 body pairs
+# read 468,709,376 B and wrote 939,030,528 B for 421,686,939 body pairs
 # (profiles/p2p_fp64_plummer1m.md).  Scaled by the units of the launch timed.
-TRAFFIC_PER_UNIT = {("p2p", "fp64"): (387522048 + 866940160) / 421686939}
+TRAFFIC_PER_UNIT = {("p2p", "fp64"): (468709376 + 939030528) / 421686939}
 P2P_FLOPS_PER_BODY_PAIR = 25
 ORACLE_SAMPLE_N = 131072
 
