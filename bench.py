@@ -63,7 +63,8 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-other", action="store_true", help="skip timing the other precision form")
-    p.add_argument("--experiment", choices=["none", "leapfrog", "ensemble", "selector", "orders"], default="none",
+    p.add_argument("--experiment", choices=["none", "leapfrog", "ensemble", "selector", "orders", "sweep"],
+                   default="none",
                    help="leapfrog: two-Plummer binary, uniform KDK steps, momentum drift per step")
     p.add_argument("--lf-steps", type=int, default=200)
     p.add_argument("--sel-steps", type=int, default=3000)
@@ -646,6 +647,58 @@ def run_orders(a):
     print(json.dumps({"experiment": "orders", "workload": "plummer_n262144_theta0.5_ncrit25_tc_fp64", "results": rows}), flush=True)
 
 
+def torque_errors(x, g, g_ref):
+    """Relative torque error of every body (Sec. 3): |X x g - X x g_PP| /
+    |X x g_PP|, torques about the coordinate origin, with g_PP the exact
+    direct-sum acceleration.  x, g, g_ref: (k, 3) arrays or tensors."""
+    import torch
+    x, g, g_ref = (torch.as_tensor(v, dtype=torch.float64) for v in (x, g, g_ref))
+    t, t_ref = torch.linalg.cross(x, g, dim=1), torch.linalg.cross(x, g_ref, dim=1)
+    return torch.linalg.norm(t - t_ref, dim=1) / torch.linalg.norm(t_ref, dim=1)
+
+
+def run_sweep(a):
+    """The experiment grid of Sec. 3 on a Plummer sphere (FP64, n_crit = 25):
+    theta = 0.2 ... 1.0 for the variants UC, TC and TCO.  Per point: time per
+    solve, mean and rms relative force error and mean relative torque error
+    over 4,096 bodies against exact direct sums, and the net force and torque
+    balance of all bodies (the quantities the paper plots against theta)."""
+    import torch
+    from paper_1706_06989_gb300 import fmm, ics
+    dev = torch.device("cuda", 0)
+    b = ics.plummer(a.n, seed=0)
+    x, y, z, m = (torch.from_numpy(v).to(dev) for v in (b.x, b.y, b.z, b.m))
+    tg = torch.as_tensor(ics.error_subset(b.n, 4096, seed=1), device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    s = fmm.FMM(theta=0.5, n_crit=a.n_crit, variant="TC", precision=a.precision)
+    ref = torch.stack(s.direct(x, y, z, m, tg), 1)
+    pos = torch.stack((x, y, z), 1)[tg]
+    out = tuple(torch.empty(b.n, dtype=torch.float64, device=dev) for _ in range(3))
+    rows = []
+    for th in (0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0):
+        for var in ("UC", "TC", "TCO"):
+            s.set_opts(theta=th, variant=var)
+            s.solve(x, y, z, m, out)
+            ms = _time_solves(s, x, y, z, m, out, flush, reps=3)
+            g = torch.stack(out, 1)[tg]
+            rel = torch.linalg.norm(g - ref, dim=1) / torch.linalg.norm(ref, dim=1)
+            terr = torque_errors(pos, g, ref)
+            fb, tb = s.balance(x, y, z, m, *out)
+            st = s.stats()
+            rows.append({"theta": th, "variant": var, "ms": ms, "mean_force_err": float(rel.mean()),
+                         "rms_force_err": float(torch.sqrt(torch.mean(rel * rel))),
+                         "mean_torque_err": float(terr.mean()), "force_balance": fb, "torque_balance": tb,
+                         "n_m2l": st.n_m2l, "p2p_body_pairs": st.p2p_body_pairs})
+    s.close()
+    cost = {}
+    for th in sorted({r["theta"] for r in rows}):
+        t = {r["variant"]: r["ms"] for r in rows if r["theta"] == th}
+        cost[str(th)] = {"TC/UC": t["TC"] / t["UC"], "TCO/UC": t["TCO"] / t["UC"]}
+    print(json.dumps({"experiment": "sweep", "workload": f"plummer_n{b.n}_ncrit{a.n_crit}_{a.precision}",
+                      "subset": "4096 bodies drawn without replacement, seed 1; exact FP64 direct sums",
+                      "results": rows, "time_ratio": cost}), flush=True)
+
+
 def main():
     a = _args()
     if a.experiment == "selector":
@@ -653,6 +706,9 @@ def main():
         return
     if a.experiment == "orders":
         run_orders(a)
+        return
+    if a.experiment == "sweep":
+        run_sweep(a)
         return
     if a.experiment == "leapfrog":
         run_leapfrog(a)
