@@ -58,13 +58,15 @@ def _load():
             lib.orc_destroy.argtypes = [P]
             for name in ("orc_sizes", "orc_get_keys", "orc_get_cells", "orc_get_geometry",
                          "orc_get_lists", "orc_eval", "orc_pair_accel", "orc_morton",
-                         "orc_dtensor_generic", "orc_dtensor_p3", "orc_direct", "orc_balance"):
+                         "orc_dtensor_generic", "orc_dtensor_p3", "orc_direct", "orc_balance",
+                         "orc_set_lists"):
                 getattr(lib, name).restype = I
             lib.orc_sizes.argtypes = [P, P]
             lib.orc_get_keys.argtypes = [P, P, P, P, P]
             lib.orc_get_cells.argtypes = [P, P, P, P, P, P, P]
             lib.orc_get_geometry.argtypes = [P, P, P, P, P]
             lib.orc_get_lists.argtypes = [P, P, P, P]
+            lib.orc_set_lists.argtypes = [P, P, I, P, I, P, I]
             lib.orc_eval.argtypes = [P, I, I, I, P, P, P, P]
             lib.orc_pair_accel.argtypes = [P, I, I, I, I, P, P, P]
             lib.orc_morton.argtypes = [I, P, P, P, P, P, P]
@@ -157,6 +159,18 @@ class Oracle:
         slf = np.zeros(self.n_self, dtype=np.int32)
         _load().orc_get_lists(self._h, _ptr(m2l), _ptr(p2p), _ptr(slf))
         return m2l, p2p, slf
+
+    def set_lists(self, m2l, p2p, slf):
+        """Replaces the interaction lists (another pair selection over the same
+        tree); ``accel`` then sums those pairs."""
+        m2l = np.ascontiguousarray(np.asarray(m2l, dtype=np.int32).reshape(-1, 2))
+        p2p = np.ascontiguousarray(np.asarray(p2p, dtype=np.int32).reshape(-1, 2))
+        slf = np.ascontiguousarray(np.asarray(slf, dtype=np.int32).reshape(-1))
+        rc = _load().orc_set_lists(self._h, _ptr(m2l), m2l.shape[0], _ptr(p2p), p2p.shape[0], _ptr(slf),
+                                   slf.shape[0])
+        if rc != 0:
+            raise OracleError(f"orc_set_lists failed ({rc})")
+        self.n_m2l, self.n_p2p, self.n_self = m2l.shape[0], p2p.shape[0], slf.shape[0]
 
     # ---- forces ----------------------------------------------------------
     def accel(self, variant="TC", generic=False, parts=PART_FAR | PART_NEAR, targets=None) -> np.ndarray:

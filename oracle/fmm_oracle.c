@@ -887,6 +887,32 @@ int orc_get_lists(const orc_t *t, int *m2l, int *p2p, int *self) {
   return ORC_OK;
 }
 
+/* Replaces the interaction lists with caller-given ones (pairs as (A, B),
+ * stored as (min, max)).  Used to evaluate the forces of a pair selection
+ * other than the plain criterion's (the learned selector of the GPU path is
+ * judged this way).  Every index must name a cell; P2P pairs and self
+ * entries must name leaves. */
+int orc_set_lists(orc_t *t, const int *m2l, int n_m2l, const int *p2p, int n_p2p, const int *self,
+                  int n_self) {
+  if (n_m2l < 0 || n_p2p < 0 || n_self < 0) return ORC_EINVAL;
+  for (int k = 0; k < 2 * n_m2l; ++k)
+    if (m2l[k] < 0 || m2l[k] >= t->ncell) return ORC_EINVAL;
+  for (int k = 0; k < 2 * n_p2p; ++k)
+    if (p2p[k] < 0 || p2p[k] >= t->ncell || !is_leaf(t, p2p[k])) return ORC_EINVAL;
+  for (int k = 0; k < n_self; ++k)
+    if (self[k] < 0 || self[k] >= t->ncell || !is_leaf(t, self[k])) return ORC_EINVAL;
+  t->n_m2l = t->n_p2p = t->n_self = 0;
+  for (int k = 0; k < n_m2l; ++k) push_pair(&t->m2l, &t->n_m2l, &t->cap_m2l, m2l[2 * k], m2l[2 * k + 1]);
+  for (int k = 0; k < n_p2p; ++k) push_pair(&t->p2p, &t->n_p2p, &t->cap_p2p, p2p[2 * k], p2p[2 * k + 1]);
+  int *ns = (int *)realloc(t->self, sizeof(int) * (size_t)(n_self > 0 ? n_self : 1));
+  if (!ns) abort();
+  t->self = ns;
+  t->cap_self = n_self > 0 ? n_self : 1;
+  memcpy(t->self, self, sizeof(int) * (size_t)n_self);
+  t->n_self = n_self;
+  return ORC_OK;
+}
+
 static void unpermute(const orc_t *t, double *acc[3], double *ax, double *ay, double *az) {
   for (int i = 0; i < t->n; ++i) {
     ax[t->order[i]] = acc[0][i];

@@ -38,6 +38,10 @@ int orc_get_cells(const orc_t *t, int *begin, int *count, int *level, int *paren
 /* Z is [ncell][3]; mom is [ncell][nmom] by multi-index (a,b,c) */
 int orc_get_geometry(const orc_t *t, double *M, double *Z, double *Rmax, double *mom);
 int orc_get_lists(const orc_t *t, int *m2l, int *p2p, int *self);
+/* Replaces the lists (e.g. by those of another pair selection); indices are
+ * validated (P2P and self entries must be leaves). */
+int orc_set_lists(orc_t *t, const int *m2l, int n_m2l, const int *p2p, int n_p2p, const int *self,
+                  int n_self);
 
 /* Accelerations in the caller's body order.  generic=0: order 3, Eqs. (3),
  * (4), (7), (8); generic=1: App. A at the order given to orc_create.

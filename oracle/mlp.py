@@ -1,4 +1,5 @@
-"""Reference of the pair-selector network (test infrastructure only).
+"""Reference of the pair-selector network and its Adam optimiser (test
+infrastructure only).
 
 The network maps 8 normalised pair features through three hidden layers of
 64 SiLU units to one output; the loss is the mean squared error.  Two forms:
@@ -97,3 +98,21 @@ def loss_and_grad(params, feat, label, mode="bf16"):
     flat = np.concatenate([g["W1"].ravel(), g["b1"], g["W2"].ravel(), g["b2"], g["W3"].ravel(), g["b3"],
                            g["w4"], g["b4"]])
     return loss, flat
+
+
+def adam_step(params, m, v, grad, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step (Kingma & Ba 2015, Algorithm 1) on the first NW
+    parameters, in float64: the moment estimates decay by beta1 and beta2
+    and take the gradient and its square, each estimate is divided by one
+    minus its decay rate to the power of the step count (bias correction),
+    and every weight moves by lr times the corrected first moment over
+    (square root of the corrected second moment + eps).  The normalisation
+    entries after the weights are left alone.  Returns new (params, m, v)."""
+    p = np.array(params, dtype=np.float64)
+    g = np.asarray(grad, dtype=np.float64)[:NW]
+    m = beta1 * np.asarray(m, dtype=np.float64)[:NW] + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64)[:NW] + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** step)
+    v_hat = v / (1.0 - beta2 ** step)
+    p[:NW] = p[:NW] - lr * m_hat / (np.sqrt(v_hat) + eps)
+    return p, m, v

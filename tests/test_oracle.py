@@ -425,10 +425,24 @@ def test_generic_order3_equals_explicit(plummer2000):
     for v in ("UC", "TC", "TCO"):
         g = o.accel(v, generic=True)
         e = o.accel(v)
-        # TCO differs by design at P = 3 only in the force component along r
         if v == "TCO":
             continue
         assert np.abs(g - e).max() <= 1e-13 * np.abs(e).max()
+
+
+def test_order3_tco_forms_differ_only_along_r():
+    """At P = 3 the two D' definitions (Eq. 8 keeps the terms of D_ijkl without
+    a factor r_i; App. A projects D onto the plane normal to r) give
+    corrective forces that differ only by a component along r."""
+    b, o, pairs = _tco_pairs(3)
+    M, Z, _, _ = o.geometry()
+    for A, B in pairs:
+        r = Z[A] - Z[B]
+        ia = o.cell_bodies(A)
+        d = (o.pair_accel(A, B, "TCO", generic=True) - o.pair_accel(A, B, "TCO"))[ia] * M[A]
+        F, _, _ = _pair_corrections(o, A, B)
+        scale = np.linalg.norm(F, axis=1).max() * np.linalg.norm(r)
+        assert np.abs(np.cross(d, r)).max() <= 1e-10 * scale
 
 
 @pytest.mark.parametrize("P", [4, 5])
@@ -451,6 +465,45 @@ def test_generic_order_torque_cancellation(P):
                 assert np.abs(t).max() > 1e-10 * sc
             else:
                 assert np.abs(t).max() <= 1e-13 * sc
+
+
+def _tco_pairs(P):
+    b = ics.plummer(600, seed=12)
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.6, 16, P=P)
+    m2l, _, _ = o.lists()
+    c = o.cells()
+    sel = [k for k in range(len(m2l)) if c.count[m2l[k, 0]] >= 3 and c.count[m2l[k, 1]] >= 3][:4]
+    return b, o, [tuple(m2l[k]) for k in sel]
+
+
+def _pair_corrections(o, A, B):
+    """(F_c, F'_c, r) of one accepted pair at general order: the corrective
+    force is what TC (resp. TCO) adds to UC, times M_A, at every body of A."""
+    M, Z, _, _ = o.geometry()
+    uc = o.pair_accel(A, B, "UC", generic=True)
+    ia = o.cell_bodies(A)
+    F = (o.pair_accel(A, B, "TC", generic=True) - uc)[ia] * M[A]
+    Fp = (o.pair_accel(A, B, "TCO", generic=True) - uc)[ia] * M[A]
+    return F, Fp, Z[A] - Z[B]
+
+
+@pytest.mark.parametrize("P", [3, 4, 5])
+def test_generic_tco_projection_is_perpendicular_to_r(P):
+    """App. A's projected D' = (delta - r r / r^2) D makes the TCO corrective
+    force the part of F_c perpendicular to r: r . F'_c = 0 and F_c - F'_c is
+    parallel to r, the same force on every body of A.  (A flipped projection
+    F_c + r (r.F_c)/r^2 still cancels the torque and balances the force, so
+    only this pin sees it.)"""
+    _, o, pairs = _tco_pairs(P)
+    for A, B in pairs:
+        F, Fp, r = _pair_corrections(o, A, B)
+        scale = np.linalg.norm(F, axis=1).max() * np.linalg.norm(r)
+        assert np.abs(Fp @ r).max() <= 1e-10 * scale
+        assert np.abs(F - F[0]).max() <= 1e-10 * np.abs(F).max()
+        par = np.cross(F - Fp, r)
+        assert np.abs(par).max() <= 1e-10 * scale
+        # the projection removes a component that is really there
+        assert np.abs(F @ r).max() > 1e-3 * scale
 
 
 def test_higher_order_is_more_accurate():
@@ -481,6 +534,31 @@ def test_planted_half_coefficient_breaks_torque_pin():
     assert np.allclose(t, -2.0 * t_uc, rtol=1e-6)
     sc = (b.m[:, None] * np.abs(np.cross(p, wrong))).sum(0).max()
     assert np.abs(t).max() > 1e-10 * sc
+
+
+@pytest.mark.parametrize("P", [4, 5])
+def test_planted_projection_sign_flip_breaks_perpendicular_pin(P):
+    """A TCO projection with the wrong sign, F_c + r (r.F_c)/r^2, cancels the
+    torque like the right one (it differs by a force along r) but leaves
+    r . F'_c = 2 r . F_c: the perpendicularity pin above fails on it."""
+    b, o, pairs = _tco_pairs(P)
+    p = b.pos()
+    M, _, _, _ = o.geometry()
+    for A, B in pairs[:2]:
+        F, _, r = _pair_corrections(o, A, B)
+        flipped = F + np.outer(F @ r, r) / (r @ r)
+        scale = np.linalg.norm(F, axis=1).max() * np.linalg.norm(r)
+        assert np.abs(flipped @ r).max() > 1e-6 * scale
+        # ... while the torque pin alone cannot tell: the flipped force, put
+        # back into the pair's accelerations, still cancels the torque
+        uc = o.pair_accel(A, B, "UC", generic=True)
+        a = uc.copy()
+        ia, ib = o.cell_bodies(A), o.cell_bodies(B)
+        a[ia] += flipped[0] / M[A]
+        a[ib] -= flipped[0] / M[B]
+        t = (b.m[:, None] * np.cross(p, a)).sum(0)
+        sc = (b.m[:, None] * np.abs(np.cross(p, a))).sum(0).max()
+        assert np.abs(t).max() <= 1e-12 * sc
 
 
 def test_planted_sign_flip_breaks_brute_force_pin(plummer2000):
