@@ -261,6 +261,54 @@ def test_mixed_precision_against_oracle(variant):
     assert fb <= 1e-6 and tb <= 1e-6, (fb, tb)
 
 
+@pytest.mark.slow
+def test_mixed_precision_1m_against_oracle():
+    """The mixed form at the benchmark size (Plummer N = 1,048,576, theta =
+    0.5, TC): tree and lists bit-exact, rms relative deviation from the FP64
+    oracle <= 1e-6 on 4,096 sampled bodies, balances <= 1e-6."""
+    b = ics.plummer(1 << 20, seed=0)
+    s, got = _solve(b, theta=0.5, precision="mixed")
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25)
+    _compare_tree(s, o)
+    _compare_lists(s, o)
+    t = ics.error_subset(b.n, 4096, seed=1)
+    rel = _rel_dev(got[t], o.accel("TC", targets=t))
+    assert np.sqrt(np.mean(rel ** 2)) <= 1e-6, np.sqrt(np.mean(rel ** 2))
+    fb, tb = oracle.balance(b.x, b.y, b.z, b.m, got)
+    assert fb <= 1e-6 and tb <= 1e-6, (fb, tb)
+
+
+@pytest.mark.slow
+def test_mixed_precision_depth_capped_binary():
+    """The longest FP32 sums: a binary of two dense Plummer spheres (the
+    leapfrog workload's cores, N = 2,097,152) with 64 bodies thrown out to
+    ~3,000 scale radii, as close encounters do.  The cube grows ~1,000-fold,
+    the tree reaches the level-21 key limit and the cores' leaves hold
+    hundreds of bodies, so leaf pairs and column streams are far longer than
+    in a Plummer sphere.  Mixed form: rms deviation from the FP64 oracle
+    <= 1e-6 on 4,096 bodies, half of them in the densest leaves."""
+    b = ics.binary_plummer(1 << 21, seed=3)
+    rng = np.random.default_rng(4)
+    far = rng.choice(b.n, 64, replace=False)
+    d = rng.normal(size=(64, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    b.x[far], b.y[far], b.z[far] = (3000.0 * d[:, k] for k in range(3))
+    s, got = _solve(b, theta=0.5, precision="mixed")
+    st = s.stats()
+    assert st.depth == 21
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25)
+    c = o.cells()
+    leaves = np.nonzero(c.nchild == 0)[0]
+    big = leaves[np.argsort(c.count[leaves])[::-1][:64]]
+    assert c.count[big[0]] > 100
+    dense = np.concatenate([o.cell_bodies(L) for L in big])
+    rng2 = np.random.default_rng(5)
+    t = np.unique(np.concatenate([rng2.choice(dense, min(2048, dense.size), replace=False),
+                                  ics.error_subset(b.n, 2048, seed=6)]))
+    rel = _rel_dev(got[t], o.accel("TC", targets=t))
+    assert np.sqrt(np.mean(rel ** 2)) <= 1e-6, np.sqrt(np.mean(rel ** 2))
+
+
 def test_mixed_precision_small_exact_cases():
     b = ics.plummer(2000, seed=0)
     s, got = _solve(b, theta=0.5, precision="mixed")
