@@ -59,7 +59,7 @@ def _load():
             for name in ("orc_sizes", "orc_get_keys", "orc_get_cells", "orc_get_geometry",
                          "orc_get_lists", "orc_eval", "orc_pair_accel", "orc_morton",
                          "orc_dtensor_generic", "orc_dtensor_p3", "orc_direct", "orc_balance",
-                         "orc_set_lists"):
+                         "orc_set_lists", "orc_set_softening"):
                 getattr(lib, name).restype = I
             lib.orc_sizes.argtypes = [P, P]
             lib.orc_get_keys.argtypes = [P, P, P, P, P]
@@ -70,9 +70,10 @@ def _load():
             lib.orc_eval.argtypes = [P, I, I, I, P, P, P, P]
             lib.orc_pair_accel.argtypes = [P, I, I, I, I, P, P, P]
             lib.orc_morton.argtypes = [I, P, P, P, P, P, P]
-            lib.orc_dtensor_generic.argtypes = [P, I, P]
-            lib.orc_dtensor_p3.argtypes = [P, P, P, P, P, P, P]
-            lib.orc_direct.argtypes = [I, P, P, P, P, I, P, P, P, P]
+            lib.orc_dtensor_generic.argtypes = [P, D, I, P]
+            lib.orc_dtensor_p3.argtypes = [P, D, P, P, P, P, P, P]
+            lib.orc_direct.argtypes = [I, P, P, P, P, I, P, D, P, P, P]
+            lib.orc_set_softening.argtypes = [P, D]
             lib.orc_balance.argtypes = [I, P, P, P, P, P, P, P, P]
             _lib = lib
     return _lib
@@ -107,7 +108,7 @@ class Oracle:
     computes Z, R_max and the moments to order P, and walks the tree.
     """
 
-    def __init__(self, x, y, z, m, theta: float, n_crit: int = 25, P: int = 3):
+    def __init__(self, x, y, z, m, theta: float, n_crit: int = 25, P: int = 3, softening: float = 0.0):
         lib = _load()
         self.x, self.y, self.z, self.m = (_f64(a) for a in (x, y, z, m))
         self.n = int(self.x.shape[0])
@@ -121,6 +122,16 @@ class Oracle:
         sz = np.zeros(6, dtype=np.int32)
         lib.orc_sizes(self._h, _ptr(sz))
         (_, self.ncell, self.n_m2l, self.n_p2p, self.n_self, self.nmom) = (int(v) for v in sz)
+        self.softening = 0.0
+        if softening:
+            self.set_softening(softening)
+
+    def set_softening(self, eps: float):
+        """Plummer softening of the forces (G = -1/sqrt(R^2 + eps^2)); the
+        tree and the lists do not depend on it."""
+        if _load().orc_set_softening(self._h, float(eps)) != 0:
+            raise OracleError("softening must be finite and >= 0")
+        self.softening = float(eps)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -222,21 +233,22 @@ def morton(x, y, z):
     return keys, lo, float(scale[0])
 
 
-def dtensor_generic(r, n: int) -> np.ndarray:
-    """Symmetric components of the n-th derivative of -1/R, multi-index order."""
+def dtensor_generic(r, n: int, eps: float = 0.0) -> np.ndarray:
+    """Symmetric components of the n-th derivative of -1/sqrt(R^2 + eps^2),
+    multi-index order."""
     r = _f64(r)
     out = np.zeros((n + 1) * (n + 2) // 2)
-    _load().orc_dtensor_generic(_ptr(r), int(n), _ptr(out))
+    _load().orc_dtensor_generic(_ptr(r), float(eps), int(n), _ptr(out))
     return out
 
 
-def dtensor_p3(r):
-    """(D, D_i, D_ij, D_ijk, D_ijkl, D'_ijkl) as full arrays."""
+def dtensor_p3(r, eps: float = 0.0):
+    """(D, D_i, D_ij, D_ijk, D_ijkl, D'_ijkl) of -1/sqrt(R^2 + eps^2) as full arrays."""
     r = _f64(r)
     d0 = np.zeros(1)
     d1, d2, d3 = np.zeros(3), np.zeros((3, 3)), np.zeros((3, 3, 3))
     d4, d4p = np.zeros((3, 3, 3, 3)), np.zeros((3, 3, 3, 3))
-    _load().orc_dtensor_p3(_ptr(r), _ptr(d0), _ptr(d1), _ptr(d2), _ptr(d3), _ptr(d4), _ptr(d4p))
+    _load().orc_dtensor_p3(_ptr(r), float(eps), _ptr(d0), _ptr(d1), _ptr(d2), _ptr(d3), _ptr(d4), _ptr(d4p))
     return float(d0[0]), d1, d2, d3, d4, d4p
 
 
@@ -245,13 +257,14 @@ def multi_indices(n: int):
     return [(a, b, n - a - b) for a in range(n, -1, -1) for b in range(n - a, -1, -1)]
 
 
-def direct(x, y, z, m, targets=None) -> np.ndarray:
-    """Exact accelerations by Neumaier-compensated direct summation [nt,3]."""
+def direct(x, y, z, m, targets=None, eps: float = 0.0) -> np.ndarray:
+    """Exact accelerations by Neumaier-compensated direct summation [nt,3]
+    (softened by eps when eps > 0)."""
     x, y, z, m = (_f64(a) for a in (x, y, z, m))
     n = x.shape[0]
     t = np.arange(n, dtype=np.int32) if targets is None else np.ascontiguousarray(targets, dtype=np.int32)
     a = [np.zeros(t.shape[0]) for _ in range(3)]
-    rc = _load().orc_direct(n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), int(t.shape[0]), _ptr(t),
+    rc = _load().orc_direct(n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), int(t.shape[0]), _ptr(t), float(eps),
                             *(_ptr(c) for c in a))
     if rc != 0:
         raise OracleError("orc_direct failed")

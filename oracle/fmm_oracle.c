@@ -61,6 +61,7 @@
 struct orc {
   int n, n_crit, P;
   double theta;
+  double eps2; /* Plummer softening length squared (0: the unsoftened 1/R) */
   /* Morton keys: bounding cube origin and scale */
   double lo[3], scale;
   uint64_t *key; /* sorted keys */
@@ -418,8 +419,8 @@ typedef struct {
   double D0, D1[3], D2[3][3], D3[3][3][3], D4[3][3][3][3];
 } dtens;
 
-static void dtensors(const double r[3], dtens *T) {
-  double R2 = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
+static void dtensors(const double r[3], double eps2, dtens *T) {
+  double R2 = ((r[0] * r[0] + r[1] * r[1]) + r[2] * r[2]) + eps2;
   double R = sqrt(R2);
   double R3 = R2 * R, R5 = R3 * R2, R7 = R5 * R2, R9 = R7 * R2;
   T->D0 = -1.0 / R;
@@ -444,8 +445,8 @@ static void dtensors(const double r[3], dtens *T) {
 
 /* D'_ijkl of Eq. (8): D_ijkl with every term that carries the factor r_i
  * removed (i is the direction of the corrective force). */
-static void dprime4(const double r[3], double Dp[3][3][3][3]) {
-  double R2 = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
+static void dprime4(const double r[3], double eps2, double Dp[3][3][3][3]) {
+  double R2 = ((r[0] * r[0] + r[1] * r[1]) + r[2] * r[2]) + eps2;
   double R = sqrt(R2);
   double R5 = R2 * R2 * R, R7 = R5 * R2;
   for (int i = 0; i < 3; ++i)
@@ -482,10 +483,10 @@ static double pairings(const int *l, int n, int used, const double r[3], int npa
   return acc;
 }
 
-int orc_dtensor_generic(const double *r, int n, double *out) {
+static int dtensor_generic_e2(const double *r, double eps2, int n, double *out) {
   /* out[mi_index(a,b,c) - mi_offset(n)] for every (a,b,c) of order n */
   if (n < 0 || n > 12) return ORC_EINVAL;
-  double R = sqrt((r[0] * r[0] + r[1] * r[1]) + r[2] * r[2]);
+  double R = sqrt(((r[0] * r[0] + r[1] * r[1]) + r[2] * r[2]) + eps2);
   for (int a = n; a >= 0; --a)
     for (int b = n - a; b >= 0; --b) {
       int c = n - a - b, l[16], s = 0;
@@ -497,17 +498,21 @@ int orc_dtensor_generic(const double *r, int n, double *out) {
   return ORC_OK;
 }
 
-int orc_dtensor_p3(const double *r, double *d0, double *d1, double *d2, double *d3, double *d4,
+int orc_dtensor_generic(const double *r, double eps, int n, double *out) {
+  return dtensor_generic_e2(r, eps * eps, n, out);
+}
+
+int orc_dtensor_p3(const double *r, double eps, double *d0, double *d1, double *d2, double *d3, double *d4,
                    double *d4prime) {
   dtens T;
-  dtensors(r, &T);
+  dtensors(r, eps * eps, &T);
   *d0 = T.D0;
   memcpy(d1, T.D1, sizeof T.D1);
   memcpy(d2, T.D2, sizeof T.D2);
   memcpy(d3, T.D3, sizeof T.D3);
   memcpy(d4, T.D4, sizeof T.D4);
   double Dp[3][3][3][3];
-  dprime4(r, Dp);
+  dprime4(r, eps * eps, Dp);
   memcpy(d4prime, Dp, sizeof Dp);
   return ORC_OK;
 }
@@ -532,7 +537,7 @@ static void m2l_p3_pair(const struct orc *t, int A, int B, int variant, double *
   double r[3] = {t->Z[0][A] - t->Z[0][B], t->Z[1][A] - t->Z[1][B], t->Z[2][A] - t->Z[2][B]};
   if ((r[0] * r[0] + r[1] * r[1]) + r[2] * r[2] == 0.0) return;
   dtens T;
-  dtensors(r, &T);
+  dtensors(r, t->eps2, &T);
   const double MA = t->M[A], MB = t->M[B];
   double QA[3][3], OA[3][3][3], QB[3][3], OB[3][3][3];
   cell_q_o(t, A, QA, OA);
@@ -555,7 +560,7 @@ static void m2l_p3_pair(const struct orc *t, int A, int B, int variant, double *
   double F[3] = {0.0, 0.0, 0.0};
   if (variant != ORC_UC) {
     double Dp[3][3][3][3];
-    if (variant == ORC_TCO) dprime4(r, Dp);
+    if (variant == ORC_TCO) dprime4(r, t->eps2, Dp);
     for (int i = 0; i < 3; ++i) {
       double f = 0.0;
       for (int j = 0; j < 3; ++j)
@@ -604,9 +609,9 @@ static void m2l_p3_pair(const struct orc *t, int A, int B, int variant, double *
 /* ------------------------------------------------------------------------ */
 
 /* Derivatives of order 0..P+1 at r, by symmetric component. */
-static double *dtab_generic(const double r[3], int P) {
+static double *dtab_generic(const double r[3], double eps2, int P) {
   double *tab = (double *)xmalloc(sizeof(double) * mi_count(P + 1));
-  for (int n = 0; n <= P + 1; ++n) orc_dtensor_generic(r, n, tab + mi_offset(n));
+  for (int n = 0; n <= P + 1; ++n) dtensor_generic_e2(r, eps2, n, tab + mi_offset(n));
   return tab;
 }
 
@@ -645,7 +650,7 @@ static void m2l_generic_pair(const struct orc *t, int A, int B, int variant, dou
   double r[3] = {t->Z[0][A] - t->Z[0][B], t->Z[1][A] - t->Z[1][B], t->Z[2][A] - t->Z[2][B]};
   double r2 = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
   if (r2 == 0.0) return;
-  double *tab = dtab_generic(r, P);
+  double *tab = dtab_generic(r, t->eps2, P);
   const int nm = P; /* local orders m = 0..P-1 */
   /* Local coefficients: the acceleration on a body of A at x is
    *   g_k = - sum_{m} 1/m! x_{l1..lm} LA[m][k][L],
@@ -750,8 +755,9 @@ static void m2l_generic_pair(const struct orc *t, int A, int B, int variant, dou
 static void p2p_bodies(const struct orc *t, int i, int j, double *acc[3], const unsigned char *want) {
   if (want && !want[i] && !want[j]) return;
   double d[3] = {t->X[0][j] - t->X[0][i], t->X[1][j] - t->X[1][i], t->X[2][j] - t->X[2][i]};
-  double r2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
-  if (r2 == 0.0) return;
+  double d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+  if (d2 == 0.0) return;
+  double r2 = d2 + t->eps2; /* Plummer softening: G = -1/sqrt(R^2 + eps^2) */
   double inv3 = 1.0 / (r2 * sqrt(r2));
   for (int k = 0; k < 3; ++k) {
     acc[k][i] += t->mu[j] * d[k] * inv3;
@@ -838,6 +844,16 @@ void orc_destroy(orc_t *t) {
   free(t->p2p);
   free(t->self);
   free(t);
+}
+
+/* Plummer softening for the evaluation: every derivative tensor and every
+ * direct pair then uses G(R) = -1/sqrt(R^2 + eps^2) (the paper's Sec. 4
+ * remarks that the correction holds for any G that depends only on the
+ * distance).  The tree and the walk do not change.  eps = 0: unsoftened. */
+int orc_set_softening(orc_t *t, double eps) {
+  if (!(eps >= 0.0) || !isfinite(eps)) return ORC_EINVAL;
+  t->eps2 = eps * eps;
+  return ORC_OK;
 }
 
 int orc_sizes(const orc_t *t, int *out) {
@@ -984,7 +1000,7 @@ int orc_pair_accel(const orc_t *t, int A, int B, int variant, int generic, doubl
 }
 
 /* ------------------------------------------------------------------------ */
-/* exact direct summation (Sec. 3: "the exact, directly computed force")     */
+/* exact direct summation (Sec. 3: the reference of the error metric)       */
 /* ------------------------------------------------------------------------ */
 
 /* Neumaier's compensated summation */
@@ -996,15 +1012,17 @@ static void neumaier_add(double *sum, double *comp, double v) {
 }
 
 int orc_direct(int n, const double *x, const double *y, const double *z, const double *m, int nt,
-               const int *targets, double *ax, double *ay, double *az) {
+               const int *targets, double eps, double *ax, double *ay, double *az) {
+  const double eps2 = eps * eps;
   for (int t = 0; t < nt; ++t) {
     const int i = targets[t];
     if (i < 0 || i >= n) return ORC_EINVAL;
     double s[3] = {0, 0, 0}, c[3] = {0, 0, 0};
     for (int j = 0; j < n; ++j) {
       double d[3] = {x[j] - x[i], y[j] - y[i], z[j] - z[i]};
-      double r2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
-      if (r2 == 0.0) continue;
+      double d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+      if (d2 == 0.0) continue;
+      double r2 = d2 + eps2;
       double inv3 = 1.0 / (r2 * sqrt(r2));
       for (int k = 0; k < 3; ++k) neumaier_add(&s[k], &c[k], m[j] * d[k] * inv3);
     }

@@ -53,12 +53,16 @@ int orc_eval(const orc_t *t, int variant, int generic, int parts, const unsigned
 int orc_pair_accel(const orc_t *t, int A, int B, int variant, int generic, double *ax,
                    double *ay, double *az);
 
-int orc_dtensor_generic(const double *r, int n, double *out);
-int orc_dtensor_p3(const double *r, double *d0, double *d1, double *d2, double *d3, double *d4,
+/* derivatives of G = -1/sqrt(R^2 + eps^2) (eps = 0: the paper's -1/R) */
+int orc_dtensor_generic(const double *r, double eps, int n, double *out);
+int orc_dtensor_p3(const double *r, double eps, double *d0, double *d1, double *d2, double *d3, double *d4,
                    double *d4prime);
+/* Plummer softening of the evaluation (orc_eval, orc_pair_accel) */
+int orc_set_softening(orc_t *t, double eps);
 
+/* direct sums of G = -1/sqrt(R^2 + eps^2), Neumaier-compensated */
 int orc_direct(int n, const double *x, const double *y, const double *z, const double *m, int nt,
-               const int *targets, double *ax, double *ay, double *az);
+               const int *targets, double eps, double *ax, double *ay, double *az);
 int orc_balance(int n, const double *x, const double *y, const double *z, const double *m,
                 const double *ax, const double *ay, const double *az, double *out);
 #endif

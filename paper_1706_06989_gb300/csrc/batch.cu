@@ -27,14 +27,18 @@ extern "C" int fmm_autotune_ncrit(fmm_ctx *c, const double *x, const double *y, 
     rc = fmm_solve_batch(c, x, y, z, m, offsets, nsys, ax, ay, az);  // warm-up and buffer growth
     float tot = 0.f;
     for (int r = 0; r < reps && rc == FMM_OK; ++r) {
-      cudaEventRecord(e0, c->stream);
-      rc = fmm_solve_batch(c, x, y, z, m, offsets, nsys, ax, ay, az);
-      cudaEventRecord(e1, c->stream);
-      if (rc == FMM_OK && cudaEventSynchronize(e1) == cudaSuccess) {
-        float t = 0.f;
-        cudaEventElapsedTime(&t, e0, e1);
-        tot += t;
-      }
+      cudaError_t ce = cudaEventRecord(e0, c->stream);
+      if (ce == cudaSuccess) rc = fmm_solve_batch(c, x, y, z, m, offsets, nsys, ax, ay, az);
+      if (rc != FMM_OK) break;
+      if (ce == cudaSuccess) ce = cudaEventRecord(e1, c->stream);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+      float t = 0.f;
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+      // a repetition that cannot be timed fails the call: counting it as
+      // zero would make the candidate look fast
+      if (ce != cudaSuccess) rc = set_error(c, FMM_ECUDA, "timing candidate n_crit %d: %s", candidates[k],
+                                            cudaGetErrorString(ce));
+      tot += t;
     }
     const float ms = tot / reps;
     if (ms_out) ms_out[k] = ms;
