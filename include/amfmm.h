@@ -102,6 +102,19 @@ const char *fmm_last_error(const fmm_ctx *ctx);
 int fmm_set_opts(fmm_ctx *ctx, const fmm_opts *opts);
 /* 1: record CUDA events around every stage (fmm_get_stats reports them). */
 int fmm_set_timing(fmm_ctx *ctx, int enable);
+/* Plummer softening of the following solves and of fmm_direct: every
+ * interaction (M2L, P2P) and the direct sums use G(R) = -1/sqrt(R^2 + eps^2)
+ * instead of the paper's -1/R.  The paper notes (Sec. 4) that the
+ * angular-momentum correction carries over to any Green's function of the
+ * distance alone; it is applied unchanged (the derivative tensors keep their
+ * form with R^2 -> R^2 + eps^2), so TC and TCO still cancel every pair's
+ * torque.  The tree, the opening criterion and the lists do not depend on
+ * eps.  eps = 0 (the default) is the unsoftened method.  Built at order
+ * P = 3 (FP64 and mixed); a softened solve at P = 4, 5 returns
+ * FMM_EUNSUPPORTED from fmm_interact.  FMM_EINVAL for eps < 0 or not finite.
+ * The learned selector's training labels stay those of the unsoftened
+ * expansion. */
+int fmm_set_softening(fmm_ctx *ctx, double eps);
 
 /* a1-a3 (Sec. 2, first paragraph): bounding cube, 63-bit Morton keys, stable
  * radix sort by (key, index), octree whose leaves hold at most n_crit bodies
@@ -257,8 +270,8 @@ int fmm_debug_walk_wait_timeout(fmm_ctx *ctx);
 /* ---- a10 diagnostics (Sec. 3) ---------------------------------------------- */
 
 /* Exact accelerations of nt target bodies by direct summation over all n
- * bodies (Sec. 3: the error of the method is measured against "the exact,
- * directly computed force"), FP64 with Neumaier-compensated sums in a fixed
+ * bodies (Sec. 3: the reference of the error metric), softened as set by
+ * fmm_set_softening, FP64 with Neumaier-compensated sums in a fixed
  * order (reproducible).  x, y, z, m: device, n doubles, any body order;
  * targets: device, nt int32 indices into them; ax, ay, az: device, nt
  * doubles (G = 1; the context's G is not applied).  A body at zero

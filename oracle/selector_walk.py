@@ -31,8 +31,9 @@ set depends only on the decision taken for each pair.
 Features of a pair (the pair is first ordered by R_max rounded to FP32,
 descending, then by cell id, so that (A, B) and (B, A) agree): log10 |r|,
 log10 R_A/|r| and log10 R_B/|r| (each floored at -12), log10 M_A,
-log10 M_B, log10 of (|Q - tr(Q)/3 I|_F / (M R_max^2) + 1e-12) of A and of B,
-and log10 (N_A + N_B).
+log10 M_B, log10 of (|Q - tr(Q)/3 I|_F / (M R_max^2) + 1e-12) of A and of B
+(the norm taken as 0 for a cell of one body or of zero extent), and
+log10 (N_A + N_B).
 
 The field estimate of the relative rule: the monopoles of one coarse level
 of the tree (the deepest level before the first level with more than 2,048
@@ -66,8 +67,9 @@ def cell_parts(o):
     n2 = ((Q[:, 0] - tr) ** 2 + (Q[:, 3] - tr) ** 2 + (Q[:, 5] - tr) ** 2
           + 2.0 * (Q[:, 1] ** 2 + Q[:, 2] ** 2 + Q[:, 4] ** 2))
     den = M * R * R
+    ok = (den > 0) & (cnt > 1)  # a cell of one body has no quadrupole
     with np.errstate(divide="ignore", invalid="ignore"):
-        qn = np.where(den > 0, np.sqrt(n2) / np.where(den > 0, den, 1.0), 0.0)
+        qn = np.where(ok, np.sqrt(n2) / np.where(ok, den, 1.0), 0.0)
         lgR = np.log10(R)
     return lgR, np.log10(M), np.log10(qn + 1e-12), cnt
 

@@ -176,6 +176,14 @@ int fmm_set_opts(fmm_ctx *c, const fmm_opts *opts) {
   return FMM_OK;
 }
 
+int fmm_set_softening(fmm_ctx *c, double eps) {
+  if (!c) return FMM_EINVAL;
+  if (!(eps >= 0.0) || !(eps < 1e300)) return set_error(c, FMM_EINVAL, "softening must be finite and >= 0 (got %g)", eps);
+  c->eps2 = eps * eps;
+  c->stage = kNone;
+  return FMM_OK;
+}
+
 int fmm_set_timing(fmm_ctx *c, int enable) {
   if (!c) return FMM_EINVAL;
   c->timing = enable != 0;
@@ -275,6 +283,8 @@ int fmm_upward(fmm_ctx *c) {
 int fmm_interact(fmm_ctx *c) {
   if (!c) return FMM_EINVAL;
   AMFMM_TRY(need_stage(c, kUp, "fmm_interact"));
+  if (c->eps2 > 0.0 && c->opts.order_P != 3)
+    return set_error(c, FMM_EUNSUPPORTED, "softening is built at order 3 only (order_P = %d)", c->opts.order_P);
   timer(c, kWalkBeg);
   AMFMM_TRY(walk(c));
   AMFMM_TRY(m2l_prepare(c));

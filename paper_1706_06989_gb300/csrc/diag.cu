@@ -65,15 +65,16 @@ __device__ void block_reduce(Comp (&v)[NV]) {
 __global__ void __launch_bounds__(kBlock) k_direct(int64_t n, const double *__restrict__ x,
                                                    const double *__restrict__ y, const double *__restrict__ z,
                                                    const double *__restrict__ m, const int32_t *__restrict__ tg,
-                                                   double *__restrict__ ax, double *__restrict__ ay,
+                                                   double eps2, double *__restrict__ ax, double *__restrict__ ay,
                                                    double *__restrict__ az) {
   const int i = tg[blockIdx.x];
   const double xi = x[i], yi = y[i], zi = z[i];
   Comp a[3] = {{0, 0}, {0, 0}, {0, 0}};
   for (int64_t j = threadIdx.x; j < n; j += kBlock) {
     const double dx = x[j] - xi, dy = y[j] - yi, dz = z[j] - zi;
-    const double r2 = (dx * dx + dy * dy) + dz * dz;
-    if (r2 > 0.0) {
+    const double d2 = (dx * dx + dy * dy) + dz * dz;
+    if (d2 > 0.0) {
+      const double r2 = d2 + eps2;
       const double inv3 = 1.0 / (r2 * sqrt(r2));
       const double s = m[j] * inv3;
       nadd(a[0], s * dx);
@@ -155,7 +156,7 @@ int fmm_direct(fmm_ctx *c, const double *x, const double *y, const double *z, co
   if (n < 1 || nt < 0 || nt > 0x7fffffffLL) return set_error(c, FMM_EINVAL, "bad sizes for fmm_direct");
   if (nt == 0) return FMM_OK;
   if (!x || !y || !z || !m || !targets || !ax || !ay || !az) return set_error(c, FMM_EINVAL, "NULL array");
-  k_direct<<<static_cast<unsigned>(nt), kBlock, 0, c->stream>>>(n, x, y, z, m, targets, ax, ay, az);
+  k_direct<<<static_cast<unsigned>(nt), kBlock, 0, c->stream>>>(n, x, y, z, m, targets, c->eps2, ax, ay, az);
   return launched(c, "direct");
 }
 

@@ -65,6 +65,7 @@ struct fmm_ctx {
   // solve inputs (caller-owned device memory)
   const double *x = nullptr, *y = nullptr, *z = nullptr, *m = nullptr;
   double theta = 0.5;
+  double eps2 = 0.0;  // Plummer softening length squared (0: the paper's unsoftened 1/R)
   amfmm::Sizes sz;
   int m2l_which = 0;  // which of the ekey/eval buffers holds the sorted M2L entries
 

@@ -26,6 +26,13 @@
 // The variant of Eq. (8) keeps only the terms of D'_ijkl (those without a
 // factor r_i):  D'_ijkl S_jkl = 45 u_i/R^7 - 9 t_i/R^5.
 //
+// Softening (optional): with G = -1/sqrt(R^2 + eps^2) every derivative keeps
+// the same form with R^2 -> R^2 + eps^2 (the derivatives act through
+// u = r.r + eps^2 only), so the formulas below take R^2 + eps^2 and leave the
+// components r_i alone; n = r/R is then no longer a unit vector, and nothing
+// below assumes that it is.  The torque correction still cancels the pair's
+// torque (the G is still a function of the distance only).
+//
 // Each pair writes its two local contributions into slots whose positions
 // were fixed by a stable sort of (cell, 2k + side); every cell then sums its
 // slots in that order.  No floating-point atomics: the result is
@@ -60,14 +67,14 @@ __device__ __forceinline__ float min_r2<float>() { return 1e-30f; }
 // large power of 1/R is formed on its own (this keeps the FP32 form in range).
 template <class T, int VARIANT>
 __device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, T iMA, T iMB, const T *QA,
-                                         const T *QB, const T *OA, const T *OB, T *CA, T *CB) {
-  const T R2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-  if (!(R2 > min_r2<T>())) {
+                                         const T *QB, const T *OA, const T *OB, T eps2, T *CA, T *CB) {
+  const T r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  if (!(r2 > min_r2<T>())) {
 #pragma unroll
     for (int q = 0; q < 19; ++q) CA[q] = CB[q] = T(0);
     return;
   }
-  const T Ri = rsqrt_t(R2);
+  const T Ri = rsqrt_t(r2 + eps2);
   const T x = r[0] * Ri, y = r[1] * Ri, z = r[2] * Ri;
   const T xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
   // unit parts of D_ij and D_ijk
@@ -158,7 +165,8 @@ __global__ void __launch_bounds__(kBlock) k_m2l64(int64_t K, const int2 *__restr
                                                    const double *__restrict__ M,
                                                    const double *__restrict__ invM,
                                                    const double *__restrict__ mom,
-                                                   const int32_t *__restrict__ pos, double *__restrict__ slots) {
+                                                   const int32_t *__restrict__ pos, double eps2,
+                                                   double *__restrict__ slots) {
   const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (k >= K) return;
   const int A = pairs[k].x, B = pairs[k].y;
@@ -166,7 +174,7 @@ __global__ void __launch_bounds__(kBlock) k_m2l64(int64_t K, const int2 *__restr
   const double r[3] = {Z[3 * A] - Z[3 * B], Z[3 * A + 1] - Z[3 * B + 1], Z[3 * A + 2] - Z[3 * B + 2]};
   const double *mA = mom + static_cast<int64_t>(A) * kMomStride;
   const double *mB = mom + static_cast<int64_t>(B) * kMomStride;
-  m2l_pair<double, VARIANT>(r, M[A], M[B], invM[A], invM[B], mA + 4, mB + 4, mA + 10, mB + 10, CA, CB);
+  m2l_pair<double, VARIANT>(r, M[A], M[B], invM[A], invM[B], mA + 4, mB + 4, mA + 10, mB + 10, eps2, CA, CB);
   CA[19] = CB[19] = 0.0;
   double *sa = slots + static_cast<int64_t>(pos[2 * k]) * kLocStride;
   double *sb = slots + static_cast<int64_t>(pos[2 * k + 1]) * kLocStride;
@@ -186,14 +194,14 @@ __global__ void __launch_bounds__(kBlock) k_m2l64(int64_t K, const int2 *__restr
 // cell's partners evaluates the mutual interaction once from each side.
 template <class T, int VARIANT>
 __device__ __forceinline__ void m2l_one(const T r[3], T MT, T iMT, T MS, const T *QS, const T *OT, const T *OS,
-                                        T *C) {
-  const T R2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-  if (!(R2 > min_r2<T>())) {
+                                        T eps2, T *C) {
+  const T r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  if (!(r2 > min_r2<T>())) {
 #pragma unroll
     for (int q = 0; q < 19; ++q) C[q] = T(0);
     return;
   }
-  const T Ri = rsqrt_t(R2);
+  const T Ri = rsqrt_t(r2 + eps2);
   const T x = r[0] * Ri, y = r[1] * Ri, z = r[2] * Ri;
   const T xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
   const T fxx = T(15) * xx, fyy = T(15) * yy, fzz = T(15) * zz;
@@ -265,7 +273,7 @@ template <int VARIANT>
 __global__ void __launch_bounds__(kGatherWarps * 32) k_m2l32_gather(int32_t ncell, const int32_t *__restrict__ off,
                                                                     const uint32_t *__restrict__ partner,
                                                                     const float *__restrict__ cell32,
-                                                                    double *__restrict__ loc,
+                                                                    double *__restrict__ loc, float eps2,
                                                                     int *__restrict__ queue) {
   // per warp, per coefficient, per lane: the lane's sum and (negated) error
   __shared__ float sh[kGatherWarps][19][33];
@@ -300,7 +308,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_m2l32_gather(int32_t ncel
     }
     const float r[3] = {(thx - b[0]) + (tlx - b[3]), (thy - b[1]) + (tly - b[4]), (thz - b[2]) + (tlz - b[5])};
     float C[19];
-    m2l_one<float, VARIANT>(r, MT, iMT, b[6], b + 8, OT, b + 14, C);
+    m2l_one<float, VARIANT>(r, MT, iMT, b[6], b + 8, OT, b + 14, eps2, C);
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
       const float yq = C[q] - cmp[q];
@@ -364,7 +372,8 @@ __global__ void k_pair_locals(int64_t K, const int2 *__restrict__ pairs, const d
   const double r[3] = {Z[3 * A] - Z[3 * B], Z[3 * A + 1] - Z[3 * B + 1], Z[3 * A + 2] - Z[3 * B + 2]};
   const double *mA = mom + static_cast<int64_t>(A) * kMomStride;
   const double *mB = mom + static_cast<int64_t>(B) * kMomStride;
-  m2l_pair<double, FMM_TC>(r, M[A], M[B], invM[A], invM[B], mA + 4, mB + 4, mA + 10, mB + 10, CA, CB);
+  // the labels are errors of the unsoftened expansion
+  m2l_pair<double, FMM_TC>(r, M[A], M[B], invM[A], invM[B], mA + 4, mB + 4, mA + 10, mB + 10, 0.0, CA, CB);
   CA[19] = CB[19] = 0.0;
 #pragma unroll
   for (int q = 0; q < kLocStride; ++q) {
@@ -478,9 +487,9 @@ int launch_m2l64(fmm_ctx *c, int64_t K) {
   double *slots = ptr<double>(c->m2l_slots);
   cudaStream_t st = c->stream;
   switch (c->opts.variant) {
-    case FMM_UC: k_m2l64<FMM_UC><<<g, kBlock, 0, st>>>(K, pairs, Z, M, iM, mom, pos, slots); break;
-    case FMM_TC: k_m2l64<FMM_TC><<<g, kBlock, 0, st>>>(K, pairs, Z, M, iM, mom, pos, slots); break;
-    default: k_m2l64<FMM_TCO><<<g, kBlock, 0, st>>>(K, pairs, Z, M, iM, mom, pos, slots); break;
+    case FMM_UC: k_m2l64<FMM_UC><<<g, kBlock, 0, st>>>(K, pairs, Z, M, iM, mom, pos, c->eps2, slots); break;
+    case FMM_TC: k_m2l64<FMM_TC><<<g, kBlock, 0, st>>>(K, pairs, Z, M, iM, mom, pos, c->eps2, slots); break;
+    default: k_m2l64<FMM_TCO><<<g, kBlock, 0, st>>>(K, pairs, Z, M, iM, mom, pos, c->eps2, slots); break;
   }
   return launched(c, "m2l");
 }
@@ -502,7 +511,7 @@ int launch_m2l32_gather(fmm_ctx *c) {
   const int64_t resident = static_cast<int64_t>(std::max(1, per_sm)) * std::max(1, c->num_sms);
   const unsigned g =
       static_cast<unsigned>(std::min<int64_t>(grid_for(static_cast<int64_t>(nc) * 32, kGatherWarps * 32), resident));
-  kern<<<g, kGatherWarps * 32, 0, st>>>(nc, off, partner, c32, loc, queue);
+  kern<<<g, kGatherWarps * 32, 0, st>>>(nc, off, partner, c32, loc, static_cast<float>(c->eps2), queue);
   return launched(c, "m2l");
 }
 

@@ -5,7 +5,7 @@
 // once: with d = X_j - X_i and s = 1/|d|^3,
 //     a_i += m_j s d,    a_j -= m_i s d,
 // so the two contributions are equal and opposite (linear momentum is
-// conserved pair by pair).  A leaf with itself sums every ordered pair i != j
+// conserved pair by pair).  With Plummer softening, s = 1/(|d|^2 + eps^2)^(3/2).  A leaf with itself sums every ordered pair i != j
 // once on the side of i.  A pair at zero separation contributes nothing.
 //
 // Work layout: one warp per leaf A.  Its columns are A's own bodies (summed
@@ -80,7 +80,8 @@ __device__ __forceinline__ bool p2p_apart(float r2) { return r2 > p2p_min_r2<flo
 // in row order, then the A-side partials.
 template <int R>
 __device__ __forceinline__ void rows32(P2PSmem<float> &sm, int i, int l, bool valid, bool mutual, float xj,
-                                       float yj, float zj, float mj, float &bx, float &by, float &bz) {
+                                       float yj, float zj, float mj, float eps2, float &bx, float &by,
+                                       float &bz) {
   float dx[R], dy[R], dz[R], r3[R];
 #pragma unroll
   for (int u = 0; u < R; ++u) {
@@ -88,7 +89,7 @@ __device__ __forceinline__ void rows32(P2PSmem<float> &sm, int i, int l, bool va
     dx[u] = rw.x - xj;
     dy[u] = rw.y - yj;
     dz[u] = rw.z - zj;
-    const float r2 = dx[u] * dx[u] + dy[u] * dy[u] + dz[u] * dz[u];
+    const float r2 = fmaf(dz[u], dz[u], fmaf(dy[u], dy[u], fmaf(dx[u], dx[u], eps2)));
     const bool ok = valid && r2 > p2p_min_r2<float>();
     const float ri = ok ? rsqrtf(r2) : 0.f;
     r3[u] = ri * ri * ri;
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
     const int32_t *__restrict__ count, const double *__restrict__ Zc, const double *__restrict__ X,
     const double *__restrict__ Y, const double *__restrict__ Zb, const double *__restrict__ Mb,
     const int2 *__restrict__ cols, double *__restrict__ near, double *__restrict__ extra,
-    T *__restrict__ slots, const BodyF *__restrict__ bodyf, int *__restrict__ queue) {
+    T *__restrict__ slots, const BodyF *__restrict__ bodyf, T eps2, int *__restrict__ queue) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   P2PSmem<T> &sm = reinterpret_cast<P2PSmem<T> *>(smem_raw)[w];
@@ -259,13 +260,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
       // its pipe and runs faster one row at a time)
       int i = 0;
       if constexpr (sizeof(T) == sizeof(float)) {
-        for (; i + 7 < nr; i += 8) rows32<8>(sm, i, l, valid, mutual, xj, yj, zj, mj, bx, by, bz);
-        for (; i + 3 < nr; i += 4) rows32<4>(sm, i, l, valid, mutual, xj, yj, zj, mj, bx, by, bz);
-        for (; i + 1 < nr; i += 2) rows32<2>(sm, i, l, valid, mutual, xj, yj, zj, mj, bx, by, bz);
+        for (; i + 7 < nr; i += 8) rows32<8>(sm, i, l, valid, mutual, xj, yj, zj, mj, eps2, bx, by, bz);
+        for (; i + 3 < nr; i += 4) rows32<4>(sm, i, l, valid, mutual, xj, yj, zj, mj, eps2, bx, by, bz);
+        for (; i + 1 < nr; i += 2) rows32<2>(sm, i, l, valid, mutual, xj, yj, zj, mj, eps2, bx, by, bz);
       }
       for (; i < nr; ++i) {
         const T dx = sm.row[i][0] - xj, dy = sm.row[i][1] - yj, dz = sm.row[i][2] - zj;
-        const T r2 = dx * dx + dy * dy + dz * dz;
+        // softening enters as the addend of the first product (no extra
+        // operation; eps2 = 0 gives the unsoftened sum)
+        const T r2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps2)));
         if (valid && p2p_apart(r2)) {
           const T ri = rsqrt_t(r2);
           const T r3 = ri * ri * ri;
@@ -570,7 +573,8 @@ int launch_p2p(fmm_ctx *c) {
       nitem, n, ptr<int4>(c->p2p_items), ptr<int32_t>(c->begin), ptr<int32_t>(c->count),
       ptr<double>(c->Z), ptr<double>(c->X), ptr<double>(c->Y), ptr<double>(c->Zb), ptr<double>(c->Mb),
       ptr<int2>(c->p2p_cols), ptr<double>(c->near), ptr<double>(c->p2p_extra),
-      static_cast<T *>(c->p2p_slots.p), sizeof(T) == sizeof(float) ? ptr<BodyF>(c->p2p_bodyf) : nullptr, queue);
+      static_cast<T *>(c->p2p_slots.p), sizeof(T) == sizeof(float) ? ptr<BodyF>(c->p2p_bodyf) : nullptr,
+      static_cast<T>(c->eps2), queue);
   AMFMM_TRY(launched(c, "p2p"));
   if (nitem > nleaf) {
     k_p2p_chunks<<<grid_for(static_cast<int64_t>(nleaf) * 32, 256), 256, 0, c->stream>>>(

@@ -46,9 +46,11 @@ namespace {
 // features and labels
 // ---------------------------------------------------------------------------
 // Per-cell parts of the features, once per tree: log10 R_max, log10 M,
-// log10 of the trace-free quadrupole norm |Q - tr(Q)/3 I| / (M R_max^2), and
-// the body count.  The squared norm is formed in FP64 (the trace removal
-// cancels); everything per pair is FP32 (FP64 costs 64 FP32 operations on
+// log10 of the trace-free quadrupole norm |Q - tr(Q)/3 I| / (M R_max^2) (plus
+// 1e-12), and the body count.  A cell of one body, or of zero extent, has no
+// quadrupole: its norm is 0.  The norm and its ratio are formed in FP64 (the
+// trace removal cancels, and the squared norm of a small cell leaves the
+// FP32 range); everything per pair is FP32 (FP64 costs 64 FP32 operations on
 // this GPU, and the features only need BF16 accuracy).
 __device__ __forceinline__ float lg(float v) { return __log2f(v) * 0.30102999566f; }
 
@@ -61,8 +63,9 @@ __global__ void k_cell_features(int32_t ncell, const double *__restrict__ Rmax, 
   const double tr = (q[0] + q[3] + q[5]) / 3.0;
   const double a = q[0] - tr, d = q[3] - tr, f = q[5] - tr;
   const double n2 = a * a + d * d + f * f + 2.0 * (q[1] * q[1] + q[2] * q[2] + q[4] * q[4]);
+  const double den = M[c] * Rmax[c] * Rmax[c];
+  const float qn = (count[c] > 1 && den > 0.0) ? static_cast<float>(sqrt(n2) / den) : 0.f;
   const float R = static_cast<float>(Rmax[c]), m = static_cast<float>(M[c]);
-  const float qn = sqrtf(static_cast<float>(n2)) / (m * R * R + 1e-30f);
   cf[c] = make_float4(lg(R), lg(m), lg(qn + 1e-12f), static_cast<float>(count[c]));
 }
 

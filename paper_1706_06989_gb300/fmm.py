@@ -64,6 +64,7 @@ def load() -> ctypes.CDLL:
                 "fmm_create": [ctypes.POINTER(P), ctypes.POINTER(_Opts), P],
                 "fmm_set_opts": [P, ctypes.POINTER(_Opts)],
                 "fmm_set_timing": [P, I],
+                "fmm_set_softening": [P, D],
                 "fmm_build_tree": [P, P, P, P, P, I64, D],
                 "fmm_upward": [P],
                 "fmm_interact": [P],
@@ -179,6 +180,11 @@ class FMM:
         if G is not None:
             o.G = float(G)
         self._check(self.lib.fmm_set_opts(self._h, ctypes.byref(o)), "fmm_set_opts")
+
+    def set_softening(self, eps: float):
+        """Plummer softening G = -1/sqrt(R^2 + eps^2) of the following solves
+        and of direct(); 0 restores the unsoftened method."""
+        self._check(self.lib.fmm_set_softening(self._h, float(eps)), "fmm_set_softening")
 
     def set_timing(self, on: bool = True):
         self._check(self.lib.fmm_set_timing(self._h, int(bool(on))), "fmm_set_timing")

@@ -163,7 +163,7 @@ def test_pair_features_by_definition(plummer3000):
             rmax = np.linalg.norm(x, axis=1).max()
             Q = np.einsum("n,ni,nj->ij", b.m[ii], x, x)
             Qt = Q - np.trace(Q) / 3 * np.eye(3)
-            qn = np.linalg.norm(Qt) / (mc * rmax ** 2) if rmax > 0 else 0.0
+            qn = np.linalg.norm(Qt) / (mc * rmax ** 2) if (rmax > 0 and len(ii) > 1) else 0.0
             props.append((mc, zc, rmax, qn, len(ii)))
         (ma, za, ra, qa, na), (mb, zb, rb, qb, nb) = props
         r = np.linalg.norm(za - zb)
