@@ -66,6 +66,8 @@ def _args():
     p.add_argument("--experiment", choices=["none", "leapfrog", "ensemble", "selector", "orders", "sweep"],
                    default="none",
                    help="leapfrog: two-Plummer binary, uniform KDK steps, momentum drift per step")
+    p.add_argument("--ics", choices=["plummer", "dwd"], default="plummer",
+                   help="sweep inputs: Plummer sphere, or the double white dwarf of Sec. 3")
     p.add_argument("--lf-steps", type=int, default=200)
     p.add_argument("--sel-steps", type=int, default=3000)
     p.add_argument("--lf-variants", default="TC:mixed,UC:mixed,TC:fp64")
@@ -658,7 +660,9 @@ def torque_errors(x, g, g_ref):
 
 
 def run_sweep(a):
-    """The experiment grid of Sec. 3 on a Plummer sphere (FP64, n_crit = 25):
+    """The experiment grid of Sec. 3 on a Plummer sphere, or on the paper's own
+    test problem (--ics dwd: two Lane-Emden white dwarfs, the donor filling
+    its Roche lobe), FP64, n_crit = 25:
     theta = 0.2 ... 1.0 for the variants UC, TC and TCO.  Per point: time per
     solve, mean and rms relative force error and mean relative torque error
     over 4,096 bodies against exact direct sums, and the net force and torque
@@ -666,7 +670,7 @@ def run_sweep(a):
     import torch
     from paper_1706_06989_gb300 import fmm, ics
     dev = torch.device("cuda", 0)
-    b = ics.plummer(a.n, seed=0)
+    b = ics.dwd(a.n, seed=0) if a.ics == "dwd" else ics.plummer(a.n, seed=0)
     x, y, z, m = (torch.from_numpy(v).to(dev) for v in (b.x, b.y, b.z, b.m))
     tg = torch.as_tensor(ics.error_subset(b.n, 4096, seed=1), device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -694,7 +698,7 @@ def run_sweep(a):
     for th in sorted({r["theta"] for r in rows}):
         t = {r["variant"]: r["ms"] for r in rows if r["theta"] == th}
         cost[str(th)] = {"TC/UC": t["TC"] / t["UC"], "TCO/UC": t["TCO"] / t["UC"]}
-    print(json.dumps({"experiment": "sweep", "workload": f"plummer_n{b.n}_ncrit{a.n_crit}_{a.precision}",
+    print(json.dumps({"experiment": "sweep", "workload": f"{a.ics}_n{b.n}_ncrit{a.n_crit}_{a.precision}",
                       "subset": "4096 bodies drawn without replacement, seed 1; exact FP64 direct sums",
                       "results": rows, "time_ratio": cost}), flush=True)
 

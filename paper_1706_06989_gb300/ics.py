@@ -12,6 +12,7 @@ spheres of log-uniform size.
 """
 from __future__ import annotations
 
+import functools
 from dataclasses import dataclass
 
 import numpy as np
@@ -149,6 +150,113 @@ def hernquist_disc(n: int, seed: int = 0, a: float = 1.0, disc_frac: float = 0.3
     z = np.concatenate([ph[:, 2], zd])
     m = np.full(n, 1.0 / n)
     return Bodies(x, y, z, m)
+
+
+@functools.lru_cache(maxsize=16)
+def lane_emden(n_index: float, h: float = 1e-3):
+    """Lane-Emden polytrope of index n: theta'' + (2/xi) theta' + theta^n = 0,
+    theta(0) = 1, theta'(0) = 0, integrated by classical fourth-order
+    Runge-Kutta in xi from a series start (theta = 1 - xi^2/6 + n xi^4/120)
+    to the first zero xi_1 (the stellar surface), which is located by a final
+    step to the zero of the cubic Hermite interpolant.  Returns (xi, theta,
+    mass) on the grid, mass = -xi^2 theta' (the mass inside xi in units of
+    4 pi rho_c alpha^3), with xi[-1] = xi_1.  For n >= 5 there is no zero;
+    the integration then stops at xi = 50."""
+    def rhs(x, y):
+        t, dt = y
+        # theta^n with theta clipped at the surface (the stages of the last
+        # step may step past the zero)
+        return np.array([dt, -max(t, 0.0) ** n_index - 2.0 * dt / x])
+
+    x0 = 1e-3
+    xs = [0.0, x0]
+    ts = [1.0, 1.0 - x0 ** 2 / 6 + n_index * x0 ** 4 / 120]
+    ds = [0.0, -x0 / 3 + n_index * x0 ** 3 / 30]
+    y = np.array([ts[-1], ds[-1]])
+    x = x0
+    while x < 50.0:
+        k1 = rhs(x, y)
+        k2 = rhs(x + h / 2, y + h / 2 * k1)
+        k3 = rhs(x + h / 2, y + h / 2 * k2)
+        k4 = rhs(x + h, y + h * k3)
+        yn = y + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+        if yn[0] <= 0.0:
+            # zero of the cubic Hermite interpolant on [x, x + h]
+            lo, hi = 0.0, 1.0
+            for _ in range(60):
+                mid = 0.5 * (lo + hi)
+                s2, s3 = mid * mid, mid * mid * mid
+                val = ((2 * s3 - 3 * s2 + 1) * y[0] + (s3 - 2 * s2 + mid) * h * y[1]
+                       + (-2 * s3 + 3 * s2) * yn[0] + (s3 - s2) * h * yn[1])
+                lo, hi = (mid, hi) if val > 0 else (lo, mid)
+            tz = 0.5 * (lo + hi)
+            xz = x + tz * h
+            dz = y[1] + tz * (yn[1] - y[1])  # theta' varies slowly over one step
+            xs.append(xz)
+            ts.append(0.0)
+            ds.append(dz)
+            break
+        x += h
+        y = yn
+        xs.append(x)
+        ts.append(y[0])
+        ds.append(y[1])
+    xi, th, dth = np.array(xs), np.array(ts), np.array(ds)
+    return xi, th, -xi * xi * dth
+
+
+def _polytrope_radii(rng: np.random.Generator, n: int, n_index: float, radius: float) -> np.ndarray:
+    """Radii of n bodies sampling a Lane-Emden polytrope of the given index
+    and surface radius: the inverse of the normalised enclosed mass."""
+    xi, _, mass = lane_emden(n_index)
+    cdf = mass / mass[-1]
+    cdf, keep = np.unique(cdf, return_index=True)
+    u = rng.uniform(0.0, 1.0, n)
+    return radius * np.interp(u, cdf, xi[keep]) / xi[-1]
+
+
+def eggleton_roche_radius(q: float) -> float:
+    """Volume-equivalent Roche-lobe radius over the separation for a star of
+    mass ratio q = M_star / M_companion (Eggleton 1983)."""
+    q23 = q ** (2.0 / 3.0)
+    return 0.49 * q23 / (0.6 * q23 + np.log1p(q ** (1.0 / 3.0)))
+
+
+def wd_radius_ratio(m1: float, m2: float, m_ch: float = 1.44) -> float:
+    """R(m1) / R(m2) of cold white dwarfs by the Nauenberg (1972) mass-radius
+    relation R ~ [(M/M_ch)^(-2/3) - (M/M_ch)^(2/3)]^(1/2)."""
+    f = lambda m: np.sqrt((m / m_ch) ** (-2.0 / 3.0) - (m / m_ch) ** (2.0 / 3.0))
+    return float(f(m1) / f(m2))
+
+
+def dwd(n: int, seed: int = 0, m_acc: float = 1.0, m_don: float = 0.2, n_acc: float = 3.0,
+        n_don: float = 1.5, sep: float = 1.0) -> Bodies:
+    """The test problem of Sec. 3 as synthetic bodies: a double white dwarf of
+    an accretor (mass 1, Lane-Emden index 3) and a donor (mass 0.2, index 1.5)
+    that fills its Roche lobe, each star spherical, n equal-mass bodies split
+    by mass and sampled from the polytropes' densities.  Readings of what the
+    paper leaves open: the separation is the unit of length (sep = 1); the
+    donor's radius is the volume-equivalent Roche-lobe radius (Eggleton 1983)
+    at q = m_don / m_acc; the accretor's radius follows from the donor's by
+    the cold white-dwarf mass-radius relation (Nauenberg 1972).  Masses in
+    solar masses with G = 1.  The stars sit on the x axis about the common
+    centre of mass and rotate rigidly with the orbit (velocities
+    Omega z x X, Omega = sqrt(M / sep^3))."""
+    rng = _rng(seed)
+    mt = m_acc + m_don
+    n_a = int(round(n * m_acc / mt))
+    n_d = n - n_a
+    r_don = eggleton_roche_radius(m_don / m_acc) * sep
+    r_acc = r_don * wd_radius_ratio(m_acc, m_don)
+    pa = _polytrope_radii(rng, n_a, n_acc, r_acc)[:, None] * _directions(rng, n_a)
+    pd = _polytrope_radii(rng, n_d, n_don, r_don)[:, None] * _directions(rng, n_d)
+    pa[:, 0] += -sep * m_don / mt
+    pd[:, 0] += sep * m_acc / mt
+    p = np.concatenate([pa, pd])
+    omega = np.sqrt(mt / sep ** 3)
+    m = np.full(n, mt / n)
+    return Bodies(p[:, 0].copy(), p[:, 1].copy(), p[:, 2].copy(), m,
+                  -omega * p[:, 1], omega * p[:, 0], np.zeros(n))
 
 
 def ensemble_sizes(nsys: int = 512, seed: int = 0, nmin: int = 1024, nmax: int = 65536) -> np.ndarray:

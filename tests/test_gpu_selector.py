@@ -106,7 +106,12 @@ def test_adam_step_matches_oracle():
         rc = s.lib.fmm_mlp_adam(s._h, ctypes.c_void_p(pd.data_ptr()), ctypes.c_void_p(md.data_ptr()),
                                 ctypes.c_void_p(vd.data_ptr()), ctypes.c_void_p(gd.data_ptr()), 3e-3, step)
         assert rc == 0
-        rp, rm, rv = M.adam_step(p.astype(np.float64), m0, v0, g, 3e-3, step)
+        # the device holds beta1, beta2, eps and lr as FP32 constants: the
+        # oracle takes those same values (1 - float32(0.999) differs from
+        # 0.001 by 1.3e-5 of itself)
+        f32 = lambda v: float(np.float32(v))
+        rp, rm, rv = M.adam_step(p.astype(np.float64), m0, v0, g, f32(3e-3), step, beta1=f32(0.9),
+                                 beta2=f32(0.999), eps=f32(1e-8))
         gp, gm, gv = pd.cpu().numpy(), md.cpu().numpy(), vd.cpu().numpy()
         # FP32 rounding relative to the size of the terms (the two terms of a
         # moment can cancel, so the bound follows the terms, not the result)
