@@ -10,7 +10,10 @@ written to flush the 129 MB L2.  The e2e figure is the same solve through
 fmm_solve_host from pinned host buffers (copies inside the timed region).
 
 --impl reference times the CPU oracle (the paper's serial method, plain C,
-FP64) on the host cores on a bounded sample of the same workload.
+FP64) on all host cores on a bounded sample of the same workload: the tree
+and the walk run serially, the far and near field of the bodies in one
+thread per core, each thread on a contiguous slice of the Morton order (the
+oracle's arithmetic is unchanged; only the bodies are divided).
 """
 from __future__ import annotations
 
@@ -37,16 +40,19 @@ SM_MAX_MHZ = 2070.0
 # FP64: 2 DFMA per clock per SM (4 flop); FP32: 128 FFMA per clock per SM (256 flop)
 FP64_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 4
 FP32_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 256
-# algorithmic flops (FMA = 2, rsqrt = 1) per unit of work; derivation in the design doc
+# algorithmic flops (FMA = 2, rsqrt = 1) per unit of work, counted from the
+# kernels' expressions: an accepted M2L pair of each variant, a body pair
 M2L_FLOPS = {"UC": 174, "TC": 295, "TCO": 276}
 # DRAM traffic of the dominant kernel per unit it processes, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum) of a launch at the
-# bench workload (Plummer N = 1,048,576, theta = 0.5, TC): k_p2p<double>
-# read 468,709,376 B and wrote 939,030,528 B for 421,686,939 body pairs
-# (profiles/p2p_fp64_plummer1m.md).  Scaled by the units of the launch timed.
-TRAFFIC_PER_UNIT = {("p2p", "fp64"): (468709376 + 939030528) / 421686939}
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of k_p2p<double> on a
+# Plummer sphere of N = 262,144 (theta = 0.5, TC): 117,100,000 B read and
+# 204,200,000 B written for 115,126,406 body pairs.  Scaled by the body pairs
+# of the launch timed (the traffic grows with them: column stream, B-side
+# partial slots and near-field sums are all per pair or per body).
+TRAFFIC_PER_UNIT = {("p2p", "fp64"): (117.1e6 + 204.2e6) / 115126406}
 P2P_FLOPS_PER_BODY_PAIR = 25
-ORACLE_SAMPLE_N = 131072
+ORACLE_SAMPLE_N = 131072      # single-core oracle sample (bodies)
+REFERENCE_N = 262144          # bodies per step of the reference arm (all cores)
 
 
 def _args():
@@ -63,7 +69,10 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-other", action="store_true", help="skip timing the other precision form")
-    p.add_argument("--experiment", choices=["none", "leapfrog", "ensemble", "selector", "orders", "sweep"],
+    p.add_argument("--no-targets", action="store_true",
+                   help="skip the 4M-body comparison of the FP64 and mixed forms")
+    p.add_argument("--experiment", choices=["none", "leapfrog", "ensemble", "selector", "orders", "sweep",
+                                            "peaks"],
                    default="none",
                    help="leapfrog: two-Plummer binary, uniform KDK steps, momentum drift per step")
     p.add_argument("--ics", choices=["plummer", "dwd"], default="plummer",
@@ -163,49 +172,81 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle (reported baseline; also the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(a, n_sample: int):
-    """One oracle solve of a Plummer sphere of n_sample bodies (same recipe)."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_solve(b, a, threads: int = 1):
+    """One oracle solve (tree, walk, far and near field at every body) of the
+    bodies b; with threads > 1 the evaluation is divided into contiguous
+    slices of the Morton order, one per thread (the C oracle releases the
+    interpreter lock, and its evaluation only reads the tree).  Returns
+    (seconds, tree seconds, thread count)."""
+    import concurrent.futures as cf
+
     import oracle
-    from paper_1706_06989_gb300 import ics
-    b = ics.plummer(n_sample, seed=0)
     t0 = time.perf_counter()
     o = oracle.Oracle(b.x, b.y, b.z, b.m, a.theta, a.n_crit)
-    o.accel(a.variant)
-    dt = time.perf_counter() - t0
-    return n_sample / dt, dt
+    t_tree = time.perf_counter() - t0
+    if threads <= 1:
+        o.accel(a.variant)
+    else:
+        order = o.keys()[1]
+        cuts = np.linspace(0, b.n, threads + 1).astype(np.int64)
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(lambda k: o.accel(a.variant, targets=order[cuts[k]:cuts[k + 1]]), range(threads)))
+    return time.perf_counter() - t0, t_tree, threads
 
 
 def cpu_baseline(a) -> dict:
-    v, dt = oracle_sample(a, ORACLE_SAMPLE_N)
-    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"one serial FP64 oracle solve of a Plummer sphere N={ORACLE_SAMPLE_N} (seed 0), "
-                       f"theta={a.theta}, n_crit={a.n_crit}, {a.variant}: tree, walk, order-3 far field "
-                       f"evaluated at every body, near field; {dt:.1f} s"),
-            "seconds": dt}
+    """The oracle on this host: the full workload on all cores, and a serial
+    solve of a smaller Plummer sphere on one core."""
+    from paper_1706_06989_gb300 import ics
+    cores = host_cores()
+    b = ics.plummer(a.n, seed=0)
+    dt, t_tree, _ = oracle_solve(b, a, threads=cores)
+    s = ics.plummer(ORACLE_SAMPLE_N, seed=0)
+    dt1, _, _ = oracle_solve(s, a, threads=1)
+    return {"value": a.n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"one FP64 oracle solve of the workload itself (Plummer N={a.n}, seed 0, theta={a.theta}, "
+                       f"n_crit={a.n_crit}, {a.variant}): tree and walk serial ({t_tree:.1f} s), far and near "
+                       f"field of every body on {cores} threads, one contiguous Morton slice each; {dt:.1f} s"),
+            "seconds": dt,
+            "single_core": {"value": ORACLE_SAMPLE_N / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"one serial oracle solve of a Plummer sphere N={ORACLE_SAMPLE_N} (seed 0); "
+                                      f"{dt1:.1f} s", "seconds": dt1}}
 
 
 def run_reference(a):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    n_sample = 32768
-    times = []
+    from paper_1706_06989_gb300 import ics
+    cores = host_cores()
+    n_ref = min(a.n, REFERENCE_N)
+    b = ics.plummer(n_ref, seed=0)
     for _ in range(a.warmup):
-        oracle_sample(a, n_sample)
+        oracle_solve(b, a, threads=cores)
+    times = []
     for _ in range(a.steps):
-        v, dt = oracle_sample(a, n_sample)
+        dt, _, _ = oracle_solve(b, a, threads=cores)
         times.append(dt)
-    value = n_sample * len(times) / sum(times)
+    value = n_ref * len(times) / sum(times)
+    sample = (f"each step one FP64 oracle solve of a Plummer sphere N={n_ref} (seed 0; the workload's recipe at "
+              f"a quarter of its size), theta={a.theta}, n_crit={a.n_crit}, {a.variant}: tree and walk serial, "
+              f"far and near field on {cores} threads, one contiguous Morton slice each")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": _workload(a), "n": a.n, "theta": a.theta,
+            "data": "synthetic", "config": {"workload": f"plummer_n{n_ref}_theta{a.theta}_ncrit{a.n_crit}_"
+                                                        f"{a.variant.lower()}_fp64",
+                                            "n": n_ref, "sample_of": _workload(a), "theta": a.theta,
                                             "n_crit": a.n_crit, "variant": a.variant,
                                             "precision": "fp64", "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": (f"each step one serial FP64 oracle solve of a Plummer sphere "
-                                        f"N={n_sample} (seed 0), theta={a.theta}, n_crit={a.n_crit}, "
-                                        f"{a.variant}")},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -232,6 +273,8 @@ def run_ours(a):
                      stream=stream)
     solver.set_timing(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    # measured peak of the FMA pipe that bounds the interaction kernels
+    peak_measured = fmm.alu_peak(a.precision, reps=5)
 
     for _ in range(max(3, a.warmup)):
         solver.solve(x, y, z, m, out)
@@ -279,6 +322,9 @@ def run_ours(a):
                 "traffic_unit": "bytes per launch (ncu capture scaled by units)" if traffic else None,
                 "peak_source": ("derived: 152 SMs x 2070 MHz x %s flop/clk/SM (FMA = 2)"
                                 % ("4 FP64" if a.precision == "fp64" else "256 FP32")),
+                "peak_measured": peak_measured, "frac_of_measured": achieved / peak_measured,
+                "peak_measured_source": "fmm_alu_peak: independent FMA chains on every SM, best of 5 launches, "
+                                        "CUDA events, in this run",
                 "other": {"m2l": {"ms": m2l_ms, "tflops": m2l_flops / (m2l_ms * 1e-3) / 1e12 if m2l_ms > 0 else None},
                           "p2p": {"ms": p2p_ms, "tflops": p2p_flops / (p2p_ms * 1e-3) / 1e12 if p2p_ms > 0 else None}}}
 
@@ -351,6 +397,10 @@ def run_ours(a):
                          "frac": p2p_flops / (p2p2 * 1e-3) / pk2}}
         s2.close()
 
+    targets = None
+    if rank == 0 and ws == 1 and not a.no_targets:
+        targets = run_targets(a, flush)
+
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
         cpu = cpu_baseline(a)
@@ -366,7 +416,7 @@ def run_ours(a):
                            "l2": "flushed (256 MiB write between timed steps)",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "accuracy": accuracy,
-                "other_form": other,
+                "other_form": other, "targets": targets,
                 "gpu_launches": int(st.launches) * a.steps, "clocks": clocks,
                 "counts": {"ncell": st.ncell, "nleaf": st.nleaf, "depth": st.depth, "n_m2l": st.n_m2l,
                            "n_p2p": st.n_p2p, "p2p_body_pairs": st.p2p_body_pairs},
@@ -376,6 +426,60 @@ def run_ours(a):
     solver.close()
     if dist:
         dist.destroy_process_group()
+
+
+def run_targets(a, flush, n: int = 4194304) -> dict:
+    """The 4M-body comparison: a Plummer sphere of N = 4,194,304 (seed 0,
+    theta = 0.5, n_crit = 25, TC) solved by the plain FP64 form, the mixed
+    form, and the mixed form with the learned selector when its trained
+    parameters are present; median of 3 timed solves after 2 warm-ups (L2
+    flushed between them); rms relative force error against exact FP64
+    direct sums on 4,096 bodies (seed 1)."""
+    import torch
+    from paper_1706_06989_gb300 import fmm, ics, selector
+    dev = torch.device("cuda", 0)
+    b = ics.plummer(n, seed=0)
+    x, y, z, m = (torch.from_numpy(v).to(dev) for v in (b.x, b.y, b.z, b.m))
+    out = tuple(torch.empty(n, dtype=torch.float64, device=dev) for _ in range(3))
+    tg = torch.as_tensor(ics.error_subset(n, 4096, seed=1), device=dev)
+    forms = [("fp64", None), ("mixed", None)]
+    params = selector.trained_params()
+    if params is not None:
+        forms.append(("mixed", params))
+    res, ref = {}, None
+    for prec, p in forms:
+        s = fmm.FMM(theta=p["theta_lo"] if p is not None else 0.5, n_crit=25, variant="TC", precision=prec)
+        if p is not None:
+            s.selector_set(p["params"], log10_target=p["log10_target"], theta_max=p["theta_max"],
+                           min_work=p["min_work"], rule=p["rule"])
+        if ref is None:
+            ref = torch.stack(s.direct(x, y, z, m, tg), 1)
+        for _ in range(2):
+            s.solve(x, y, z, m, out)
+        ms = _time_solves(s, x, y, z, m, out, flush, reps=3)
+        key = prec + ("_selector" if p is not None else "")
+        res[key] = {"ms": ms, "bodies_per_s": n / (ms / 1e3), "rms_force_err": _rms_err(s, x, y, z, m, out, tg, ref)}
+        s.close()
+    for k in res:
+        if k != "fp64":
+            res[k]["speedup_vs_fp64"] = res["fp64"]["ms"] / res[k]["ms"]
+            res[k]["err_ratio_vs_fp64"] = res[k]["rms_force_err"] / res["fp64"]["rms_force_err"]
+    return {"workload": f"plummer_n{n}_theta0.5_ncrit25_tc", "results": res,
+            "target": "mixed (+ learned selector) >= 3x the FP64 form at equal or lower rms force error",
+            "error_reference": "exact FP64 direct sums on 4,096 bodies (seed 1)"}
+
+
+def run_peaks(a):
+    """Measured FMA-pipe peaks (FP64 DFMA, FP32 FFMA) and the clocks they ran at."""
+    from paper_1706_06989_gb300 import fmm
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    r = {p: fmm.alu_peak(p, reps=20) for p in ("fp64", "mixed")}
+    clocks = sampler.stop()
+    print(json.dumps({"experiment": "peaks", "fp64_tflops": r["fp64"], "fp32_tflops": r["mixed"],
+                      "derived_fp64_tflops": FP64_PEAK / 1e12, "derived_fp32_tflops": FP32_PEAK / 1e12,
+                      "clocks": clocks}), flush=True)
 
 
 def run_leapfrog(a):
@@ -713,6 +817,9 @@ def main():
         return
     if a.experiment == "sweep":
         run_sweep(a)
+        return
+    if a.experiment == "peaks":
+        run_peaks(a)
         return
     if a.experiment == "leapfrog":
         run_leapfrog(a)

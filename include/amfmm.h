@@ -310,6 +310,16 @@ int fmm_balance_noalloc(const double *x, const double *y, const double *z, const
                         const double *ax, const double *ay, const double *az, int64_t n, double *out,
                         void *cuda_stream);
 
+/* Measured arithmetic peak of the GPU's plain FMA pipe (the pipe that bounds
+ * the P2P and M2L kernels; no tensor cores), for the roofline of those
+ * kernels: independent FMA chains on every SM of the current device, timed
+ * with CUDA events on the legacy default stream; the best of `reps` timed
+ * launches after one warm-up.  precision FMM_FP64: DFMA; FMM_MIXED: FFMA.
+ * *tflops (HOST) receives TFLOP/s with an FMA counted as 2.  No context;
+ * allocates nothing; synchronises the device's default stream.  (A
+ * measurement aid; the paper has no counterpart.) */
+int fmm_alu_peak(int precision, int reps, double *tflops);
+
 /* Counts (and stage timings) of the last solve; synchronises the stream. */
 int fmm_get_stats(fmm_ctx *ctx, fmm_stats *out);
 

@@ -61,6 +61,33 @@ __device__ void block_reduce(Comp (&v)[NV]) {
   __syncthreads();
 }
 
+// Arithmetic peak of the plain (non-tensor) FMA pipe: every thread runs
+// kPeakChains independent chains a = a * b + c, kPeakUnroll steps per
+// iteration, on a grid of kPeakBlocksPerSM blocks per SM.  The chains' sum is
+// written only if it equals a value it cannot reach, which keeps them live
+// without a store per thread.  The roofline of the interaction kernels
+// (bound by this pipe, not by memory) is taken against what it measures.
+constexpr int kPeakBlock = 256, kPeakBlocksPerSM = 8, kPeakChains = 8, kPeakUnroll = 16;
+
+template <class T>
+__global__ void __launch_bounds__(kPeakBlock) k_fma_peak(int iters, T *__restrict__ sink) {
+  T a[kPeakChains];
+#pragma unroll
+  for (int k = 0; k < kPeakChains; ++k) a[k] = T(threadIdx.x + k) * T(1e-3);
+  const T b = T(0.9999), c = T(1e-4);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < kPeakUnroll; ++u) {
+#pragma unroll
+      for (int k = 0; k < kPeakChains; ++k) a[k] = fma(a[k], b, c);
+    }
+  }
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < kPeakChains; ++k) s += a[k];
+  if (s == T(-12345.0) && sink) *sink = s;
+}
+
 // one block per target body
 __global__ void __launch_bounds__(kBlock) k_direct(int64_t n, const double *__restrict__ x,
                                                    const double *__restrict__ y, const double *__restrict__ z,
@@ -158,6 +185,43 @@ int fmm_direct(fmm_ctx *c, const double *x, const double *y, const double *z, co
   if (!x || !y || !z || !m || !targets || !ax || !ay || !az) return set_error(c, FMM_EINVAL, "NULL array");
   k_direct<<<static_cast<unsigned>(nt), kBlock, 0, c->stream>>>(n, x, y, z, m, targets, c->eps2, ax, ay, az);
   return launched(c, "direct");
+}
+
+int fmm_alu_peak(int precision, int reps, double *tflops) {
+  if (!tflops || reps < 1 || (precision != FMM_FP64 && precision != FMM_MIXED)) return FMM_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return FMM_ECUDA;
+  }
+  // FP64 runs at 1/64 of the FP32 rate: fewer iterations keep both launches
+  // in the millisecond range
+  const int iters = precision == FMM_FP64 ? 64 : 4096;
+  const unsigned grid = static_cast<unsigned>(sms * kPeakBlocksPerSM);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double best = 0.0;
+  int rc = FMM_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = FMM_ECUDA;
+  for (int r = 0; r <= reps && rc == FMM_OK; ++r) {  // the first launch warms up
+    cudaEventRecord(e0, 0);
+    if (precision == FMM_FP64) k_fma_peak<double><<<grid, kPeakBlock>>>(iters, nullptr);
+    else k_fma_peak<float><<<grid, kPeakBlock>>>(iters, nullptr);
+    cudaEventRecord(e1, 0);
+    float ms = 0.f;
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || !(ms > 0.f)) {
+      rc = FMM_ECUDA;
+      break;
+    }
+    const double flops = 2.0 * kPeakChains * kPeakUnroll * static_cast<double>(iters) * grid * kPeakBlock;
+    if (r > 0) best = std::max(best, flops / (ms * 1e-3) / 1e12);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaGetLastError();
+  if (rc == FMM_OK) *tflops = best;
+  return rc;
 }
 
 int fmm_balance(fmm_ctx *c, const double *x, const double *y, const double *z, const double *m,

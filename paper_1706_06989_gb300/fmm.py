@@ -95,6 +95,8 @@ def load() -> ctypes.CDLL:
                 f = getattr(lib, name)
                 f.argtypes = args
                 f.restype = I
+            lib.fmm_alu_peak.argtypes = [I, I, ctypes.POINTER(ctypes.c_double)]
+            lib.fmm_alu_peak.restype = I
             lib.fmm_selector_nparams.argtypes = []
             lib.fmm_selector_nparams.restype = I
             lib.fmm_destroy.argtypes = [P]
@@ -124,6 +126,16 @@ class Stats:
     scale: float
     ms: dict
     n_scored: int = 0
+
+
+def alu_peak(precision: str = "fp64", reps: int = 5) -> float:
+    """Measured TFLOP/s of the plain FMA pipe (FP64 or FP32) on the current
+    device (fmm_alu_peak)."""
+    out = ctypes.c_double(0.0)
+    rc = load().fmm_alu_peak(PRECISIONS[precision], int(reps), ctypes.byref(out))
+    if rc != FMM_OK:
+        raise FMMError(rc, "fmm_alu_peak failed")
+    return float(out.value)
 
 
 class FMM:

@@ -21,10 +21,28 @@ shifted by another (same label): the network learns the invariance.
 """
 from __future__ import annotations
 
+import json
+import os
+
 import numpy as np
 
 NPARAMS = 8977
 H, F = 64, 8
+PARAMS_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_params.npz")
+
+
+def trained_params(path: str = PARAMS_PATH):
+    """The committed trained network and its acceptance setting (written by
+    train_selector.py), as a dict with keys params, rule, theta_lo,
+    theta_max, min_work, log10_target; None if the file is absent."""
+    if not os.path.exists(path):
+        return None
+    with np.load(path) as f:
+        params = np.asarray(f["params"], dtype=np.float32)
+        meta = json.loads(str(f["meta"]))
+    if params.shape != (NPARAMS,):
+        raise ValueError(f"{path}: expected {NPARAMS} parameters, found {params.shape}")
+    return dict(meta, params=params)
 
 
 def init_params(feat: np.ndarray, seed: int = 0) -> np.ndarray:
