@@ -725,9 +725,10 @@ def run_selector(a):
 
 
 def run_orders(a):
-    """Expansion order P = 3, 4, 5 (App. A), FP64, on a Plummer sphere of
-    N = 262,144 (theta = 0.5, TC): time per solve and rms force error against
-    exact direct sums on 2,048 bodies."""
+    """Expansion order P = 3 ... 8 (App. A), FP64, on a Plummer sphere of
+    N = 262,144 (theta = 0.5, TC) and at theta = 0.7: time per solve and rms
+    force error against exact direct sums on 2,048 bodies, with the stage
+    times and the interaction counts (the error/cost trade of the order)."""
     import torch
     from paper_1706_06989_gb300 import fmm, ics
     dev = torch.device("cuda", 0)
@@ -738,18 +739,24 @@ def run_orders(a):
     s = fmm.FMM(theta=0.5, n_crit=25, variant="TC", precision="fp64")
     ref = torch.stack(s.direct(x, y, z, m, tg), 1)
     rows = []
-    for P in (3, 4, 5):
-        sp = fmm.FMM(theta=0.5, n_crit=25, variant="TC", precision="fp64", order_P=P)
-        out = tuple(torch.empty(b.n, dtype=torch.float64, device=dev) for _ in range(3))
-        for _ in range(3):
-            sp.solve(x, y, z, m, out)
-        ms = _time_solves(sp, x, y, z, m, out, flush, reps=5)
-        g = torch.stack(out, 1)[tg]
-        rel = torch.linalg.norm(g - ref, dim=1) / torch.linalg.norm(ref, dim=1)
-        fb, tb = sp.balance(x, y, z, m, *out)
-        rows.append({"order_P": P, "ms": ms, "bodies_per_s": b.n / (ms / 1e3),
-                     "rms_err": float(torch.sqrt(torch.mean(rel * rel))), "force_balance": fb, "torque_balance": tb})
-        sp.close()
+    for theta in (0.5, 0.7):
+        for P in (3, 4, 5, 6, 7, 8):
+            sp = fmm.FMM(theta=theta, n_crit=25, variant="TC", precision="fp64", order_P=P)
+            sp.set_timing(True)
+            out = tuple(torch.empty(b.n, dtype=torch.float64, device=dev) for _ in range(3))
+            for _ in range(2):
+                sp.solve(x, y, z, m, out)
+            ms = _time_solves(sp, x, y, z, m, out, flush, reps=3)
+            st = sp.stats()
+            g = torch.stack(out, 1)[tg]
+            rel = torch.linalg.norm(g - ref, dim=1) / torch.linalg.norm(ref, dim=1)
+            fb, tb = sp.balance(x, y, z, m, *out)
+            rows.append({"order_P": P, "theta": theta, "ms": ms, "bodies_per_s": b.n / (ms / 1e3),
+                         "rms_err": float(torch.sqrt(torch.mean(rel * rel))), "force_balance": fb,
+                         "torque_balance": tb, "stage_ms": st.ms, "n_m2l": st.n_m2l,
+                         "p2p_body_pairs": st.p2p_body_pairs})
+            sp.close()
+            torch.cuda.empty_cache()
     print(json.dumps({"experiment": "orders", "workload": "plummer_n262144_theta0.5_ncrit25_tc_fp64", "results": rows}), flush=True)
 
 

@@ -88,8 +88,8 @@ int check_opts(fmm_ctx *c, const fmm_opts *o) {
   if (!(o->theta > 0.0 && o->theta <= 1.0))
     return set_error(c, FMM_EINVAL, "theta must satisfy 0 < theta <= 1 (got %g)", o->theta);
   if (o->n_crit < 1) return set_error(c, FMM_EINVAL, "n_crit must be >= 1 (got %d)", o->n_crit);
-  if (o->order_P < 3 || o->order_P > 5)
-    return set_error(c, FMM_EUNSUPPORTED, "order_P %d is not built (3, 4 and 5 are)", o->order_P);
+  if (o->order_P < 3 || o->order_P > 8)
+    return set_error(c, FMM_EUNSUPPORTED, "order_P %d is not built (3 to 8 are)", o->order_P);
   if (o->order_P != 3 && o->precision != FMM_FP64)
     return set_error(c, FMM_EUNSUPPORTED, "orders above 3 are built in FP64 only");
   if (o->variant < FMM_UC || o->variant > FMM_TCO)
@@ -156,7 +156,7 @@ void fmm_destroy(fmm_ctx *c) {
                  &c->m2l, &c->p2p, &c->self_list, &c->walk_zr, &c->walk_zf, &c->walk_nl, &c->walk_state, &c->walk_lb, &c->ekey[0], &c->ekey[1], &c->eval[0], &c->eval[1],
                  &c->m2l_pos, &c->m2l_off, &c->m2l_slots, &c->cell32, &c->pkey[0], &c->pkey[1], &c->pval[0],
                  &c->pval[1], &c->p2p_A, &c->p2p_offA, &c->p2p_offB, &c->p2p_pos, &c->p2p_poff,
-                 &c->p2p_len, &c->p2p_slots, &c->p2p_colOff, &c->p2p_cols, &c->p2p_nb, &c->p2p_pre, &c->p2p_bodyf, &c->p2p_items, &c->p2p_itemOff, &c->p2p_extraOff, &c->p2p_extra, &c->scan_tmp, &c->sort_hist, &c->totals, &c->diag, &c->sel_params, &c->sel_cellfeat, &c->sel_cand, &c->sel_lga, &c->sel_scratch, &c->sel_part, &c->sel_score, &c->sel_grad, &c->sel_perm, &c->sel_xb, &c->sel_yb, &c->hx, &c->hy,
+                 &c->p2p_len, &c->p2p_slots, &c->p2p_colOff, &c->p2p_cols, &c->p2p_nb, &c->p2p_pre, &c->p2p_bodyf, &c->p2p_items, &c->p2p_itemOff, &c->p2p_extraOff, &c->p2p_extra, &c->scan_tmp, &c->sort_hist, &c->totals, &c->diag, &c->sel_params, &c->sel_cellfeat, &c->sel_cand, &c->sel_lga, &c->sel_scratch, &c->sel_part, &c->sel_score, &c->sel_grad, &c->sel_perm, &c->sel_xb, &c->sel_yb, &c->gen_tab, &c->hx, &c->hy,
                  &c->hz, &c->hm, &c->hax, &c->hay, &c->haz};
   for (DBuf *b : all) free_buf(*b);
   for (int k = 0; k < kNumTimers; ++k)

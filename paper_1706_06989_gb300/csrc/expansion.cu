@@ -1,6 +1,7 @@
 // expansion.cu -- a7': the general-order expansion of App. A on the GPU
-// (orders P = 4 and 5, FP64), reusing the tree, walk and near field of the
-// order-3 path.  The per-order arithmetic is generated (expansion_gen.cuh);
+// (orders P = 4 and 5 from generated code, FP64; P = 6 .. 8 from the
+// table-driven kernels of expansion_table.cu), reusing the tree, walk and
+// near field of the order-3 path.  The per-order arithmetic is generated (expansion_gen.cuh);
 // this file holds the kernels and their launches:
 //   P2M   moments of order 0..P about each leaf's centre of mass
 //   M2M   shifted child moments, level by level
@@ -197,7 +198,7 @@ int upward_general(fmm_ctx *c) {
   switch (c->opts.order_P) {
     case 4: return upward_p<4>(c);
     case 5: return upward_p<5>(c);
-    default: return set_error(c, FMM_EUNSUPPORTED, "order %d is not built", c->opts.order_P);
+    default: return upward_table(c);
   }
 }
 
@@ -206,7 +207,7 @@ int m2l_general(fmm_ctx *c) {
   switch (c->opts.order_P) {
     case 4: return m2l_p<4>(c);
     case 5: return m2l_p<5>(c);
-    default: return set_error(c, FMM_EUNSUPPORTED, "order %d is not built", c->opts.order_P);
+    default: return m2l_table(c);
   }
 }
 
@@ -227,7 +228,7 @@ int downward_general(fmm_ctx *c) {
   switch (c->opts.order_P) {
     case 4: return downward_p<4>(c);
     case 5: return downward_p<5>(c);
-    default: return set_error(c, FMM_EUNSUPPORTED, "order %d is not built", c->opts.order_P);
+    default: return downward_table(c);
   }
 }
 

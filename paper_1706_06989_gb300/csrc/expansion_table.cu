@@ -1,0 +1,475 @@
+// expansion_table.cu -- a7' at orders P = 6 .. 8: the general-order
+// expansion of App. A driven by index tables instead of generated
+// straight-line code (which at these orders holds hundreds of values per
+// thread and spills).  The formulas are those of the generated orders 4 and
+// 5, in multi-index notation (alpha, beta, gamma exponent triples, |a| the
+// order, a! the product of the factorials):
+//   derivatives  D^g = d^g G(r), G = -1/R, written D^g = R^-(|g|+1) U^g(n),
+//                n = r/R, U^g the polynomial in n of the chain rule on G(u),
+//                u = r.r (every way of pairing equal indices through u's
+//                second derivative, the other indices left as components of
+//                r):  U^g = sum_{i,j,l} c_m K_a(i) K_b(j) K_c(l) nx^(a-2i) ny^(b-2j) nz^(c-2l),
+//                m = |g| - i - j - l, c_m = -(-1)^m (2m-1)!!,
+//                K_a(i) = a! / (2^i i! (a-2i)!)
+//   field of B at A:  L_A^a = sum_b (-1)^|b| D^(a+b) M_B^b / b!,   |a| + |b| <= P
+//   field of A at B:  L_B^b = (-1)^|b| sum_a D^(a+b) M_A^a / a!
+//   correction:       F_k = - sum_{|a|+|b|=P} (-1)^|b| M_A^a M_B^b D^(a+b+e_k) / (a! b!),
+//                     +F/M_A on A, -F/M_B on B; TCO: F - n (n.F)
+//   P2M: M^a = sum mu x^a;  M2M: M^a += sum_{b<=a} C(a,b) M_child^b s^(a-b)
+//   L2L: L'^a += sum_g L^(a+g) s^g / g!;  L2P: g_k = -sum_a L^(a+e_k) x^a / a!
+// Multi-indices of order n are stored from offset n (n+1) (n+2) / 6, ordered
+// a0 = n..0 and then a1 = n - a0 .. 0, so that the position of (a0, a1, a2)
+// in its order is s (s+1) / 2 + a2 with s = a1 + a2.
+//
+// Work layout: one warp per accepted pair (lanes over the output
+// coefficients, the derivatives and scaled moments of the pair staged in
+// shared memory), one warp per cell for P2M, M2M and L2L, one thread per
+// body for L2P.  FP64 throughout; every sum has a fixed order.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "internal.cuh"
+#include "geom.cuh"
+
+namespace amfmm {
+namespace {
+
+constexpr int kTabMaxP = 8;
+constexpr int kNUMax = (kTabMaxP + 2) * (kTabMaxP + 3) * (kTabMaxP + 4) / 6;  // orders 0..P+1: 220
+constexpr int kNMMax = (kTabMaxP + 1) * (kTabMaxP + 2) * (kTabMaxP + 3) / 6;  // orders 0..P: 165
+constexpr int kTabWarps = 4;
+
+__host__ __device__ constexpr int mi_off(int n) { return n * (n + 1) * (n + 2) / 6; }
+__device__ __forceinline__ int mi_idx(int a0, int a1, int a2) {
+  const int n = a0 + a1 + a2, s = a1 + a2;
+  return mi_off(n) + s * (s + 1) / 2 + a2;
+}
+
+// Index tables, built once on the host and copied to each context:
+//   expo[i]  = (a0, a1, a2, |a|) of multi-index i (orders 0..kTabMaxP+1)
+//   ifact[i] = 1 / a!
+//   uoff[g] .. uoff[g+1]: the terms of U^g, each a coefficient and the
+//   exponents of n packed as px | py << 8 | pz << 16
+struct TabHost {
+  std::vector<int4> expo;
+  std::vector<double> ifact;
+  std::vector<int> uoff;
+  std::vector<double> ucoef;
+  std::vector<int> uexp;
+};
+
+double fact(int k) {
+  double f = 1.0;
+  for (int q = 2; q <= k; ++q) f *= q;
+  return f;
+}
+
+const TabHost &tables() {
+  static TabHost t;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    for (int n = 0; n <= kTabMaxP + 1; ++n)
+      for (int a0 = n; a0 >= 0; --a0)
+        for (int a1 = n - a0; a1 >= 0; --a1) {
+          const int a2 = n - a0 - a1;
+          t.expo.push_back(make_int4(a0, a1, a2, n));
+          t.ifact.push_back(1.0 / (fact(a0) * fact(a1) * fact(a2)));
+        }
+    t.uoff.push_back(0);
+    for (const int4 &g : t.expo) {
+      const int a = g.x, b = g.y, c = g.z, n = g.w;
+      for (int i = 0; 2 * i <= a; ++i)
+        for (int j = 0; 2 * j <= b; ++j)
+          for (int l = 0; 2 * l <= c; ++l) {
+            const int m = n - i - j - l;
+            double dfm = 1.0;  // (2m - 1)!!
+            for (int k = 2 * m - 1; k > 1; k -= 2) dfm *= k;
+            const double cm = (m % 2 == 0 ? -1.0 : 1.0) * dfm;
+            const double ka = fact(a) / (std::pow(2.0, i) * fact(i) * fact(a - 2 * i));
+            const double kb = fact(b) / (std::pow(2.0, j) * fact(j) * fact(b - 2 * j));
+            const double kc = fact(c) / (std::pow(2.0, l) * fact(l) * fact(c - 2 * l));
+            t.ucoef.push_back(cm * ka * kb * kc);
+            t.uexp.push_back((a - 2 * i) | ((b - 2 * j) << 8) | ((c - 2 * l) << 16));
+          }
+      t.uoff.push_back(static_cast<int>(t.ucoef.size()));
+    }
+  });
+  return t;
+}
+
+struct TabDev {
+  const int4 *expo;
+  const double *ifact;
+  const int *uoff;
+  const double *ucoef;
+  const int *uexp;
+};
+
+// the device copy of the tables, in one context-owned buffer
+int device_tables(fmm_ctx *c, TabDev *out) {
+  const TabHost &t = tables();
+  const size_t b_expo = t.expo.size() * sizeof(int4), b_if = t.ifact.size() * sizeof(double),
+               b_uoff = t.uoff.size() * sizeof(int), b_uc = t.ucoef.size() * sizeof(double),
+               b_ue = t.uexp.size() * sizeof(int);
+  auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+  const size_t o_if = up(b_expo), o_uoff = o_if + up(b_if), o_uc = o_uoff + up(b_uoff), o_ue = o_uc + up(b_uc),
+               total = o_ue + up(b_ue);
+  if (c->gen_tab.cap < total) {
+    AMFMM_TRY(ensure_bytes(c, c->gen_tab, total));
+    std::vector<char> h(total, 0);
+    memcpy(h.data(), t.expo.data(), b_expo);
+    memcpy(h.data() + o_if, t.ifact.data(), b_if);
+    memcpy(h.data() + o_uoff, t.uoff.data(), b_uoff);
+    memcpy(h.data() + o_uc, t.ucoef.data(), b_uc);
+    memcpy(h.data() + o_ue, t.uexp.data(), b_ue);
+    // synchronous: the host vector goes out of scope afterwards
+    AMFMM_CUDA(c, cudaMemcpy(c->gen_tab.p, h.data(), total, cudaMemcpyHostToDevice));
+  }
+  char *base = static_cast<char *>(c->gen_tab.p);
+  out->expo = reinterpret_cast<const int4 *>(base);
+  out->ifact = reinterpret_cast<const double *>(base + o_if);
+  out->uoff = reinterpret_cast<const int *>(base + o_uoff);
+  out->ucoef = reinterpret_cast<const double *>(base + o_uc);
+  out->uexp = reinterpret_cast<const int *>(base + o_ue);
+  return FMM_OK;
+}
+
+__device__ __forceinline__ double binom(int n, int k) {
+  double r = 1.0;
+  for (int q = 1; q <= k; ++q) r = r * (n - k + q) / q;
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// M2L: one warp per accepted pair
+// ---------------------------------------------------------------------------
+struct PairSmem {
+  double U[kNUMax];
+  double sA[kNMMax], sB[kNMMax];
+  double F[3][32];
+};
+
+template <int VARIANT>
+__global__ void __launch_bounds__(kTabWarps * 32) k_m2l_tab(int P, int64_t K, const int2 *__restrict__ pairs,
+                                                            const double *__restrict__ Z,
+                                                            const double *__restrict__ invM,
+                                                            const double *__restrict__ mom,
+                                                            const int32_t *__restrict__ pos, TabDev tab,
+                                                            double *__restrict__ slots) {
+  __shared__ PairSmem sm_all[kTabWarps];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  PairSmem &sm = sm_all[w];
+  const int NM = mi_off(P + 1), NU = mi_off(P + 2), NL = NM - 1;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(kTabWarps) + w; k < K;
+       k += static_cast<int64_t>(gridDim.x) * kTabWarps) {
+    const int A = pairs[k].x, B = pairs[k].y;
+    double *LA = slots + static_cast<int64_t>(pos[2 * k]) * NL;
+    double *LB = slots + static_cast<int64_t>(pos[2 * k + 1]) * NL;
+    const double r0 = Z[3 * A] - Z[3 * B], r1 = Z[3 * A + 1] - Z[3 * B + 1], r2 = Z[3 * A + 2] - Z[3 * B + 2];
+    const double R2 = r0 * r0 + r1 * r1 + r2 * r2;
+    if (!(R2 > 0.0)) {
+      for (int q = lane; q < NL; q += 32) LA[q] = LB[q] = 0.0;
+      continue;
+    }
+    const double Ri = rsqrt(R2);
+    const double nx = r0 * Ri, ny = r1 * Ri, nz = r2 * Ri;
+    double ri[kTabMaxP + 3];
+    ri[0] = 1.0;
+#pragma unroll
+    for (int q = 1; q < kTabMaxP + 3; ++q) ri[q] = ri[q - 1] * Ri;
+    double px[kTabMaxP + 2], py[kTabMaxP + 2], pz[kTabMaxP + 2];
+    px[0] = py[0] = pz[0] = 1.0;
+#pragma unroll
+    for (int q = 1; q < kTabMaxP + 2; ++q) {
+      px[q] = px[q - 1] * nx;
+      py[q] = py[q - 1] * ny;
+      pz[q] = pz[q - 1] * nz;
+    }
+    // U^g(n) for |g| <= P + 1
+    for (int g = lane; g < NU; g += 32) {
+      double u = 0.0;
+      for (int t = tab.uoff[g]; t < tab.uoff[g + 1]; ++t) {
+        const int e = tab.uexp[t];
+        u += tab.ucoef[t] * (px[e & 255] * py[(e >> 8) & 255] * pz[e >> 16]);
+      }
+      sm.U[g] = u;
+    }
+    // moments scaled by R^-|b|
+    const double *mA = mom + static_cast<int64_t>(A) * NM, *mB = mom + static_cast<int64_t>(B) * NM;
+    for (int i = lane; i < NM; i += 32) {
+      const int o = tab.expo[i].w;
+      sm.sA[i] = mA[i] * ri[o];
+      sm.sB[i] = mB[i] * ri[o];
+    }
+    __syncwarp();
+    // corrective force: lanes over a, b over the order P - |a|
+    double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+    if (VARIANT != FMM_UC) {
+      for (int ia = lane; ia < NM; ia += 32) {
+        const int4 a = tab.expo[ia];
+        const int nb = P - a.w;
+        const double ca = -sm.sA[ia] * tab.ifact[ia];
+        for (int ib = mi_off(nb); ib < mi_off(nb + 1); ++ib) {
+          const int4 b = tab.expo[ib];
+          const double cb = (nb % 2 == 0 ? ca : -ca) * sm.sB[ib] * tab.ifact[ib];
+          const int x0 = a.x + b.x, x1 = a.y + b.y, x2 = a.z + b.z;
+          f0 += cb * sm.U[mi_idx(x0 + 1, x1, x2)];
+          f1 += cb * sm.U[mi_idx(x0, x1 + 1, x2)];
+          f2 += cb * sm.U[mi_idx(x0, x1, x2 + 1)];
+        }
+      }
+      // lane sums in a fixed order
+      sm.F[0][lane] = f0;
+      sm.F[1][lane] = f1;
+      sm.F[2][lane] = f2;
+      __syncwarp();
+      if (lane < 3) {
+        double s = 0.0;
+        for (int q = 0; q < 32; ++q) s += sm.F[lane][q];
+        sm.F[lane][0] = s;
+      }
+      __syncwarp();
+      f0 = sm.F[0][0] * ri[2];
+      f1 = sm.F[1][0] * ri[2];
+      f2 = sm.F[2][0] * ri[2];
+      if (VARIANT == FMM_TCO) {
+        const double nf = nx * f0 + ny * f1 + nz * f2;
+        f0 -= nx * nf;
+        f1 -= ny * nf;
+        f2 -= nz * nf;
+      }
+    }
+    // locals of order 1..P on both sides: lanes over the output index
+    for (int o = lane; o < NL; o += 32) {
+      const int iq = o + 1;
+      const int4 q = tab.expo[iq];
+      double accA = 0.0, accB = 0.0;
+      const int top = mi_off(P - q.w + 1);
+      for (int is = 0; is < top; ++is) {
+        const int4 s = tab.expo[is];
+        const double u = sm.U[mi_idx(q.x + s.x, q.y + s.y, q.z + s.z)] * tab.ifact[is];
+        accA += (s.w % 2 == 0 ? u : -u) * sm.sB[is];
+        accB += u * sm.sA[is];
+      }
+      double la = ri[q.w + 1] * accA;
+      double lb = (q.w % 2 == 0 ? 1.0 : -1.0) * ri[q.w + 1] * accB;
+      if (VARIANT != FMM_UC && o < 3) {
+        const double f = o == 0 ? f0 : (o == 1 ? f1 : f2);
+        la -= f * invM[A];
+        lb += f * invM[B];
+      }
+      LA[o] = la;
+      LB[o] = lb;
+    }
+    __syncwarp();  // the staged values are written again by the next pair
+  }
+}
+
+// ---------------------------------------------------------------------------
+// P2M (leaves), M2M (one level), L2L (one level), L2P
+// ---------------------------------------------------------------------------
+// one warp per leaf: centre of mass as at order 3, then lanes over the
+// multi-indices, each summing mu x^a over the leaf's bodies in sorted order
+__global__ void k_leaf_upward_tab(int P, int32_t nleaf, const int32_t *__restrict__ leaves,
+                                  const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+                                  const double *__restrict__ X, const double *__restrict__ Y,
+                                  const double *__restrict__ Zb, const double *__restrict__ Mb,
+                                  double *__restrict__ S, double *__restrict__ M, double *__restrict__ Z,
+                                  double *__restrict__ invM, double *__restrict__ mom, TabDev tab) {
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q >= nleaf) return;
+  const int c = leaves[q];
+  const int b = begin[c], e = b + count[c];
+  double z[3];
+  if (lane == 0) leaf_com(c, b, e, X, Y, Zb, Mb, S, M, Z, invM, z);
+  z[0] = __shfl_sync(0xffffffffu, z[0], 0);
+  z[1] = __shfl_sync(0xffffffffu, z[1], 0);
+  z[2] = __shfl_sync(0xffffffffu, z[2], 0);
+  const int NM = mi_off(P + 1);
+  double *out = mom + static_cast<int64_t>(c) * NM;
+  for (int i = lane; i < NM; i += 32) {
+    const int4 a = tab.expo[i];
+    double acc = 0.0;
+    for (int j = b; j < e; ++j) {
+      const double x = X[j] - z[0], y = Y[j] - z[1], zz = Zb[j] - z[2];
+      double v = Mb[j];
+      for (int t = 0; t < a.x; ++t) v *= x;
+      for (int t = 0; t < a.y; ++t) v *= y;
+      for (int t = 0; t < a.z; ++t) v *= zz;
+      acc += v;
+    }
+    out[i] = acc;
+  }
+  __syncwarp();
+  if (lane == 0) out[0] = M[c];
+}
+
+// one warp per cell of a level: centre of mass from the children (as at
+// order 3), then lanes over a: M^a = sum over children in order of
+// sum_{b <= a} C(a, b) M_child^b s^(a-b)
+__global__ void k_internal_upward_tab(int P, int32_t c0, int32_t c1, const int32_t *__restrict__ first_child,
+                                      const int32_t *__restrict__ nchild, double *__restrict__ S,
+                                      double *__restrict__ M, double *__restrict__ Z, double *__restrict__ invM,
+                                      double *__restrict__ mom, TabDev tab) {
+  const int c = c0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= c1) return;
+  const int nch = nchild[c];
+  if (nch == 0) return;
+  const int f = first_child[c];
+  double z[3];
+  if (lane == 0) parent_com(c, f, nch, S, M, Z, invM, z);
+  z[0] = __shfl_sync(0xffffffffu, z[0], 0);
+  z[1] = __shfl_sync(0xffffffffu, z[1], 0);
+  z[2] = __shfl_sync(0xffffffffu, z[2], 0);
+  const int NM = mi_off(P + 1);
+  double *out = mom + static_cast<int64_t>(c) * NM;
+  for (int i = lane; i < NM; i += 32) {
+    const int4 a = tab.expo[i];
+    double acc = 0.0;
+    for (int k = f; k < f + nch; ++k) {
+      const double s0 = Z[3 * k] - z[0], s1 = Z[3 * k + 1] - z[1], s2 = Z[3 * k + 2] - z[2];
+      const double *mc = mom + static_cast<int64_t>(k) * NM;
+      for (int b0 = 0; b0 <= a.x; ++b0)
+        for (int b1 = 0; b1 <= a.y; ++b1)
+          for (int b2 = 0; b2 <= a.z; ++b2) {
+            double v = binom(a.x, b0) * binom(a.y, b1) * binom(a.z, b2) * mc[mi_idx(b0, b1, b2)];
+            for (int t = b0; t < a.x; ++t) v *= s0;
+            for (int t = b1; t < a.y; ++t) v *= s1;
+            for (int t = b2; t < a.z; ++t) v *= s2;
+            acc += v;
+          }
+    }
+    out[i] = acc;
+  }
+  __syncwarp();
+  if (lane == 0) out[0] = M[c];
+}
+
+// one warp per cell of a level: L^a(cell) += sum_g L^(a+g)(parent) s^g / g!
+__global__ void k_l2l_tab(int P, int32_t c0, int32_t c1, const int32_t *__restrict__ parent,
+                          const double *__restrict__ Z, double *__restrict__ loc, TabDev tab) {
+  const int c = c0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= c1) return;
+  const int p = parent[c];
+  const double s0 = Z[3 * c] - Z[3 * p], s1 = Z[3 * c + 1] - Z[3 * p + 1], s2 = Z[3 * c + 2] - Z[3 * p + 2];
+  const int NL = mi_off(P + 1) - 1;
+  const double *Lp = loc + static_cast<int64_t>(p) * NL;
+  double *Lc = loc + static_cast<int64_t>(c) * NL;
+  for (int o = lane; o < NL; o += 32) {
+    const int4 a = tab.expo[o + 1];
+    double acc = 0.0;
+    const int top = mi_off(P - a.w + 1);
+    for (int ig = 0; ig < top; ++ig) {
+      const int4 g = tab.expo[ig];
+      double v = Lp[mi_idx(a.x + g.x, a.y + g.y, a.z + g.z) - 1] * tab.ifact[ig];
+      for (int t = 0; t < g.x; ++t) v *= s0;
+      for (int t = 0; t < g.y; ++t) v *= s1;
+      for (int t = 0; t < g.z; ++t) v *= s2;
+      acc += v;
+    }
+    Lc[o] += acc;
+  }
+}
+
+// one thread per body: g_k = -sum_{|a| <= P-1} L^(a+e_k) x^a / a!
+__global__ void k_l2p_tab(int P, int64_t n, const int32_t *__restrict__ leaf_of, const double *__restrict__ Z,
+                          const double *__restrict__ loc, const double *__restrict__ X,
+                          const double *__restrict__ Y, const double *__restrict__ Zb,
+                          const double *__restrict__ near, double *__restrict__ acc, TabDev tab) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const int L = leaf_of[i];
+  const double x = X[i] - Z[3 * L], y = Y[i] - Z[3 * L + 1], z = Zb[i] - Z[3 * L + 2];
+  const int NL = mi_off(P + 1) - 1;
+  const double *Lc = loc + static_cast<int64_t>(L) * NL;
+  double px[kTabMaxP], py[kTabMaxP], pz[kTabMaxP];
+  px[0] = py[0] = pz[0] = 1.0;
+#pragma unroll
+  for (int q = 1; q < kTabMaxP; ++q) {
+    px[q] = px[q - 1] * x;
+    py[q] = py[q - 1] * y;
+    pz[q] = pz[q - 1] * z;
+  }
+  double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+  for (int ia = 0; ia < mi_off(P); ++ia) {
+    const int4 a = tab.expo[ia];
+    const double w = tab.ifact[ia] * (px[a.x] * py[a.y] * pz[a.z]);
+    g0 += w * Lc[mi_idx(a.x + 1, a.y, a.z) - 1];
+    g1 += w * Lc[mi_idx(a.x, a.y + 1, a.z) - 1];
+    g2 += w * Lc[mi_idx(a.x, a.y, a.z + 1) - 1];
+  }
+  acc[i] = near[i] - g0;
+  acc[n + i] = near[n + i] - g1;
+  acc[2 * n + i] = near[2 * n + i] - g2;
+}
+
+}  // namespace
+
+int upward_table(fmm_ctx *c) {
+  TabDev tab;
+  AMFMM_TRY(device_tables(c, &tab));
+  cudaStream_t st = c->stream;
+  const int P = c->opts.order_P;
+  k_leaf_upward_tab<<<grid_for(c->sz.nleaf * 32, 128), 128, 0, st>>>(
+      P, static_cast<int32_t>(c->sz.nleaf), ptr<int32_t>(c->leaves), ptr<int32_t>(c->begin), ptr<int32_t>(c->count),
+      ptr<double>(c->X), ptr<double>(c->Y), ptr<double>(c->Zb), ptr<double>(c->Mb), ptr<double>(c->S),
+      ptr<double>(c->M), ptr<double>(c->Z), ptr<double>(c->invM), ptr<double>(c->mom), tab);
+  AMFMM_TRY(launched(c, "leaf_upward_tab"));
+  for (int lev = c->sz.depth - 1; lev >= 0; --lev) {
+    const int64_t c0 = c->sz.lvl_off[lev], c1 = c->sz.lvl_off[lev + 1];
+    if (c1 <= c0) continue;
+    k_internal_upward_tab<<<grid_for((c1 - c0) * 32, 128), 128, 0, st>>>(
+        P, static_cast<int32_t>(c0), static_cast<int32_t>(c1), ptr<int32_t>(c->first_child), ptr<int32_t>(c->nchild),
+        ptr<double>(c->S), ptr<double>(c->M), ptr<double>(c->Z), ptr<double>(c->invM), ptr<double>(c->mom), tab);
+    AMFMM_TRY(launched(c, "internal_upward_tab"));
+  }
+  return FMM_OK;
+}
+
+int m2l_table(fmm_ctx *c) {
+  const int64_t K = c->sz.n_m2l;
+  if (K == 0) return FMM_OK;
+  TabDev tab;
+  AMFMM_TRY(device_tables(c, &tab));
+  const int P = c->opts.order_P;
+  const unsigned g = static_cast<unsigned>(std::min<int64_t>((K + kTabWarps - 1) / kTabWarps,
+                                                             static_cast<int64_t>(c->num_sms) * 16));
+  const int2 *pairs = ptr<int2>(c->m2l);
+  const double *Z = ptr<double>(c->Z), *iM = ptr<double>(c->invM), *mom = ptr<double>(c->mom);
+  const int32_t *pos = ptr<int32_t>(c->m2l_pos);
+  double *slots = ptr<double>(c->m2l_slots);
+  cudaStream_t st = c->stream;
+  switch (c->opts.variant) {
+    case FMM_UC: k_m2l_tab<FMM_UC><<<g, kTabWarps * 32, 0, st>>>(P, K, pairs, Z, iM, mom, pos, tab, slots); break;
+    case FMM_TC: k_m2l_tab<FMM_TC><<<g, kTabWarps * 32, 0, st>>>(P, K, pairs, Z, iM, mom, pos, tab, slots); break;
+    default: k_m2l_tab<FMM_TCO><<<g, kTabWarps * 32, 0, st>>>(P, K, pairs, Z, iM, mom, pos, tab, slots); break;
+  }
+  return launched(c, "m2l_tab");
+}
+
+int downward_table(fmm_ctx *c) {
+  TabDev tab;
+  AMFMM_TRY(device_tables(c, &tab));
+  cudaStream_t st = c->stream;
+  const int P = c->opts.order_P;
+  const int64_t n = c->sz.n;
+  for (int lev = 1; lev <= c->sz.depth; ++lev) {
+    const int64_t c0 = c->sz.lvl_off[lev], c1 = c->sz.lvl_off[lev + 1];
+    if (c1 <= c0) continue;
+    k_l2l_tab<<<grid_for((c1 - c0) * 32, 128), 128, 0, st>>>(P, static_cast<int32_t>(c0), static_cast<int32_t>(c1),
+                                                             ptr<int32_t>(c->parent), ptr<double>(c->Z),
+                                                             ptr<double>(c->loc), tab);
+    AMFMM_TRY(launched(c, "l2l_tab"));
+  }
+  k_l2p_tab<<<grid_for(n, 128), 128, 0, st>>>(P, n, ptr<int32_t>(c->leaf_of), ptr<double>(c->Z), ptr<double>(c->loc),
+                                              ptr<double>(c->X), ptr<double>(c->Y), ptr<double>(c->Zb),
+                                              ptr<double>(c->near), ptr<double>(c->acc), tab);
+  return launched(c, "l2p_tab");
+}
+
+}  // namespace amfmm

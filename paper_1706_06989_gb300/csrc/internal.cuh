@@ -100,6 +100,8 @@ struct fmm_ctx {
   double sel_theta_max = 1.0;  // upper edge of the band the network decides
   int64_t sel_min_work = 256;  // pairs with n_A n_B below this are left to the floor
   int sel_rule = FMM_SEL_RELATIVE;  // acceptance rule of the learned selector
+  // index tables of the table-driven general order (P = 6 .. 8)
+  amfmm::DBuf gen_tab;
   // host-solve staging
   amfmm::DBuf hx, hy, hz, hm, hax, hay, haz;
 };
@@ -182,6 +184,10 @@ int upward_general(fmm_ctx *c);
 int m2l_general(fmm_ctx *c);
 int reduce_general(fmm_ctx *c);
 int downward_general(fmm_ctx *c);
+// the same stages at P = 6 .. 8, table-driven (expansion_table.cu)
+int upward_table(fmm_ctx *c);
+int m2l_table(fmm_ctx *c);
+int downward_table(fmm_ctx *c);
 
 // learned selector (selector.cu, m2l.cu)
 int cell_features(fmm_ctx *c);  // per-cell parts of the selector's features

@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(kGenBlock, kGenBlocksPerSM) k_walk_gen(
     int4 *__restrict__ inc) {
   __shared__ unsigned s_place;
   __shared__ int4 s_warp[kGenBlock / 32];
-  __shared__ int4 s_prefix;
+  __shared__ int4 s_red[kGenBlock / 32];
+  __shared__ int s_stop[kGenBlock / 32];
   const float th2f = static_cast<float>(theta) * static_cast<float>(theta);
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   GenState &G = gs[g];
@@ -220,73 +221,79 @@ __global__ void __launch_bounds__(kGenBlock, kGenBlocksPerSM) k_walk_gen(
     block_total = add4(block_total, s_warp[q]);
   }
   // look-back: the sum of the totals of all earlier places, read by the
-  // first warp 32 places at a time (lane k looks at place - 1 - k)
-  if (w == 0) {
-    const int ep = static_cast<int>(epoch & 0x3fffffffu) << 2;
-    if (lane == 0) {
-      if (place == 0) st_volatile4(&inc[0], block_total);
-      else st_volatile4(&agg[place], block_total);
+  // whole block kGenBlock places at a time (thread k looks at place - 1 - k).
+  // Every thread of the block would otherwise wait at the next barrier, so a
+  // window as wide as the block costs nothing extra and lets the inclusive
+  // prefixes travel kGenBlock places per round instead of one warp's 32.
+  const int ep = static_cast<int>(epoch & 0x3fffffffu) << 2;
+  if (t == 0) {
+    if (place == 0) st_volatile4(&inc[0], block_total);
+    else st_volatile4(&agg[place], block_total);
+    __threadfence();
+    atomicExch(&flag[place], ep | (place == 0 ? 2 : 1));
+  }
+  int4 pre = make_int4(0, 0, 0, 0);
+  bool failed = false;
+  if (place > 0) {
+    int top = static_cast<int>(place) - 1;  // highest place not yet summed
+    long long spins = 0;                     // the same in every thread: the loops below are block-uniform
+    while (top >= 0) {
+      const int j = top - t;
+      int f = j >= 0 ? *reinterpret_cast<volatile int *>(&flag[j]) : (ep | 2);
+      bool ready = (f & ~3) == ep && (f & 3) != 0;
+      // wait until every place of the window has published something
+      while (!__syncthreads_and(ready)) {
+        if (++spins > kSpinLimit) break;
+        __nanosleep(32);
+        if (!ready) {
+          f = *reinterpret_cast<volatile int *>(&flag[j]);
+          ready = (f & ~3) == ep && (f & 3) != 0;
+        }
+      }
+      if (!__syncthreads_and(ready)) {
+        failed = true;
+        break;
+      }
       __threadfence();
-      atomicExch(&flag[place], ep | (place == 0 ? 2 : 1));
-    }
-    int4 pre = make_int4(0, 0, 0, 0);
-    bool failed = false;
-    if (place > 0) {
-      int top = static_cast<int>(place) - 1;  // highest place not yet summed
-      long long spins = 0;
-      while (top >= 0) {
-        const int j = top - lane;
-        int f = j >= 0 ? *reinterpret_cast<volatile int *>(&flag[j]) : (ep | 2);
-        bool ready = (f & ~3) == ep && (f & 3) != 0;
-        // wait until every place of the window has published something
-        while (!__all_sync(0xffffffffu, ready)) {
-          if (++spins > kSpinLimit) break;
-          __nanosleep(32);
-          if (!ready) {
-            f = *reinterpret_cast<volatile int *>(&flag[j]);
-            ready = (f & ~3) == ep && (f & 3) != 0;
-          }
-        }
-        if (!__all_sync(0xffffffffu, ready)) {
-          failed = true;
-          break;
-        }
-        __threadfence();
-        // nearest place in the window that holds an inclusive prefix
-        const unsigned incl_mask = __ballot_sync(0xffffffffu, j >= 0 && (f & 3) == 2);
-        const int stop = incl_mask ? __ffs(incl_mask) - 1 : 32;  // lanes [0, stop) add aggregates
-        int4 v = make_int4(0, 0, 0, 0);
-        if (j >= 0 && lane < stop) v = ld_volatile4(&agg[j]);
-        if (j >= 0 && lane == stop) v = ld_volatile4(&inc[j]);
+      // nearest place in the window that holds an inclusive prefix: threads
+      // [0, stop) add aggregates, thread stop the inclusive prefix
+      const unsigned incl_mask = __ballot_sync(0xffffffffu, j >= 0 && (f & 3) == 2);
+      if (lane == 0) s_stop[w] = incl_mask ? w * 32 + __ffs(incl_mask) - 1 : kGenBlock;
+      __syncthreads();
+      int stop = kGenBlock;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-          v = add4(v, make_int4(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o),
-                                __shfl_xor_sync(0xffffffffu, v.z, o), __shfl_xor_sync(0xffffffffu, v.w, o)));
-        pre = add4(pre, v);
-        if (incl_mask) break;
-        top -= 32;
-      }
-      if (lane == 0) {
-        if (failed) atomicOr(&G.status, 2);
-        st_volatile4(&inc[place], add4(pre, block_total));
-        __threadfence();
-        atomicExch(&flag[place], ep | 2);
-      }
+      for (int q = 0; q < kGenBlock / 32; ++q) stop = min(stop, s_stop[q]);
+      int4 v = make_int4(0, 0, 0, 0);
+      if (j >= 0 && t < stop) v = ld_volatile4(&agg[j]);
+      if (j >= 0 && t == stop) v = ld_volatile4(&inc[j]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        v = add4(v, make_int4(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o),
+                              __shfl_xor_sync(0xffffffffu, v.z, o), __shfl_xor_sync(0xffffffffu, v.w, o)));
+      if (lane == 0) s_red[w] = v;
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < kGenBlock / 32; ++q) pre = add4(pre, s_red[q]);
+      __syncthreads();  // s_stop and s_red are written again by the next round
+      if (stop < kGenBlock) break;
+      top -= kGenBlock;
     }
-    if (lane == 0) {
-      if (place == nb - 1) {
-        const int4 tot = add4(pre, block_total);
-        G.total = tot;
-        const bool over = tot.x > cap_next || m2l_base + tot.y > cap_m2l || p2p_base + tot.z > cap_p2p ||
-                          self_base + tot.w > cap_self;
-        if (over) atomicOr(&G.status, 1);
-        gs[g + 1].in = GenIn{over ? 0 : tot.x, m2l_base + tot.y, p2p_base + tot.z, self_base + tot.w};
-      }
-      s_prefix = pre;
+    if (t == 0) {
+      if (failed) atomicOr(&G.status, 2);
+      st_volatile4(&inc[place], add4(pre, block_total));
+      __threadfence();
+      atomicExch(&flag[place], ep | 2);
     }
   }
-  __syncthreads();
-  const int4 base = add4(s_prefix, before);
+  if (t == 0 && place == nb - 1) {
+    const int4 tot = add4(pre, block_total);
+    G.total = tot;
+    const bool over = tot.x > cap_next || m2l_base + tot.y > cap_m2l || p2p_base + tot.z > cap_p2p ||
+                      self_base + tot.w > cap_self;
+    if (over) atomicOr(&G.status, 1);
+    gs[g + 1].in = GenIn{over ? 0 : tot.x, m2l_base + tot.y, p2p_base + tot.z, self_base + tot.w};
+  }
+  const int4 base = add4(pre, before);
   int64_t ox = base.x, oy = m2l_base + base.y, oz = p2p_base + base.z, ow = self_base + base.w;
   bool over = false;
 #pragma unroll
