@@ -136,20 +136,31 @@ int device_tables(fmm_ctx *c, TabDev *out) {
   return FMM_OK;
 }
 
-__device__ __forceinline__ double binom(int n, int k) {
-  double r = 1.0;
-  for (int q = 1; q <= k; ++q) r = r * (n - k + q) / q;
-  return r;
-}
-
 // ---------------------------------------------------------------------------
 // M2L: one warp per accepted pair
 // ---------------------------------------------------------------------------
 struct PairSmem {
   double U[kNUMax];
+  // scaled moments with the 1/b! of the sums folded in: sA[b] = M_A^b R^-|b| / b!,
+  // sB[b] = (-1)^|b| M_B^b R^-|b| / b!
   double sA[kNMMax], sB[kNMMax];
+  double pw[3][kTabMaxP + 2];  // powers of the unit vector's components
   double F[3][32];
 };
+
+// per-block copy of the multi-index table: exponents packed a0 | a1 << 8 |
+// a2 << 16 | |a| << 24 (orders 0 .. kTabMaxP + 1)
+__device__ __forceinline__ void load_expo(int *dst, const int4 *__restrict__ expo) {
+  for (int i = threadIdx.x; i < kNUMax; i += blockDim.x) {
+    const int4 e = expo[i];
+    dst[i] = e.x | (e.y << 8) | (e.z << 16) | (e.w << 24);
+  }
+}
+__device__ __forceinline__ int mi_idx_sum(int pa, int pb) {
+  // index of the multi-index a + b from the packed exponents of a and b
+  const int s = pa + pb;  // no field exceeds 255
+  return mi_idx(s & 255, (s >> 8) & 255, (s >> 16) & 255);
+}
 
 template <int VARIANT>
 __global__ void __launch_bounds__(kTabWarps * 32) k_m2l_tab(int P, int64_t K, const int2 *__restrict__ pairs,
@@ -159,6 +170,11 @@ __global__ void __launch_bounds__(kTabWarps * 32) k_m2l_tab(int P, int64_t K, co
                                                             const int32_t *__restrict__ pos, TabDev tab,
                                                             double *__restrict__ slots) {
   __shared__ PairSmem sm_all[kTabWarps];
+  __shared__ int ex[kNUMax];
+  __shared__ double ifa[kNUMax];
+  load_expo(ex, tab.expo);
+  for (int i = threadIdx.x; i < kNUMax; i += blockDim.x) ifa[i] = tab.ifact[i];
+  __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   PairSmem &sm = sm_all[w];
   const int NM = mi_off(P + 1), NU = mi_off(P + 2), NL = NM - 1;
@@ -179,45 +195,46 @@ __global__ void __launch_bounds__(kTabWarps * 32) k_m2l_tab(int P, int64_t K, co
     ri[0] = 1.0;
 #pragma unroll
     for (int q = 1; q < kTabMaxP + 3; ++q) ri[q] = ri[q - 1] * Ri;
-    double px[kTabMaxP + 2], py[kTabMaxP + 2], pz[kTabMaxP + 2];
-    px[0] = py[0] = pz[0] = 1.0;
-#pragma unroll
-    for (int q = 1; q < kTabMaxP + 2; ++q) {
-      px[q] = px[q - 1] * nx;
-      py[q] = py[q - 1] * ny;
-      pz[q] = pz[q - 1] * nz;
+    if (lane < 3) {
+      const double v = lane == 0 ? nx : (lane == 1 ? ny : nz);
+      double p = 1.0;
+      for (int q = 0; q < kTabMaxP + 2; ++q) {
+        sm.pw[lane][q] = p;
+        p *= v;
+      }
     }
+    // moments scaled by R^-|b| and divided by b!
+    const double *mA = mom + static_cast<int64_t>(A) * NM, *mB = mom + static_cast<int64_t>(B) * NM;
+    for (int i = lane; i < NM; i += 32) {
+      const int o = ex[i] >> 24;
+      const double f = ri[o] * ifa[i];
+      sm.sA[i] = mA[i] * f;
+      sm.sB[i] = (o % 2 == 0 ? f : -f) * mB[i];
+    }
+    __syncwarp();
     // U^g(n) for |g| <= P + 1
     for (int g = lane; g < NU; g += 32) {
       double u = 0.0;
       for (int t = tab.uoff[g]; t < tab.uoff[g + 1]; ++t) {
         const int e = tab.uexp[t];
-        u += tab.ucoef[t] * (px[e & 255] * py[(e >> 8) & 255] * pz[e >> 16]);
+        u += tab.ucoef[t] * (sm.pw[0][e & 255] * sm.pw[1][(e >> 8) & 255] * sm.pw[2][e >> 16]);
       }
       sm.U[g] = u;
-    }
-    // moments scaled by R^-|b|
-    const double *mA = mom + static_cast<int64_t>(A) * NM, *mB = mom + static_cast<int64_t>(B) * NM;
-    for (int i = lane; i < NM; i += 32) {
-      const int o = tab.expo[i].w;
-      sm.sA[i] = mA[i] * ri[o];
-      sm.sB[i] = mB[i] * ri[o];
     }
     __syncwarp();
     // corrective force: lanes over a, b over the order P - |a|
     double f0 = 0.0, f1 = 0.0, f2 = 0.0;
     if (VARIANT != FMM_UC) {
       for (int ia = lane; ia < NM; ia += 32) {
-        const int4 a = tab.expo[ia];
-        const int nb = P - a.w;
-        const double ca = -sm.sA[ia] * tab.ifact[ia];
+        const int pa = ex[ia];
+        const int nb = P - (pa >> 24);
+        const double ca = -sm.sA[ia];
         for (int ib = mi_off(nb); ib < mi_off(nb + 1); ++ib) {
-          const int4 b = tab.expo[ib];
-          const double cb = (nb % 2 == 0 ? ca : -ca) * sm.sB[ib] * tab.ifact[ib];
-          const int x0 = a.x + b.x, x1 = a.y + b.y, x2 = a.z + b.z;
-          f0 += cb * sm.U[mi_idx(x0 + 1, x1, x2)];
-          f1 += cb * sm.U[mi_idx(x0, x1 + 1, x2)];
-          f2 += cb * sm.U[mi_idx(x0, x1, x2 + 1)];
+          const double cb = ca * sm.sB[ib];  // (-1)^|b| / (a! b!) folded in
+          const int ab = (pa + ex[ib]) & 0xffffff;
+          f0 += cb * sm.U[mi_idx_sum(ab, 1)];
+          f1 += cb * sm.U[mi_idx_sum(ab, 1 << 8)];
+          f2 += cb * sm.U[mi_idx_sum(ab, 1 << 16)];
         }
       }
       // lane sums in a fixed order
@@ -243,18 +260,17 @@ __global__ void __launch_bounds__(kTabWarps * 32) k_m2l_tab(int P, int64_t K, co
     }
     // locals of order 1..P on both sides: lanes over the output index
     for (int o = lane; o < NL; o += 32) {
-      const int iq = o + 1;
-      const int4 q = tab.expo[iq];
+      const int pq = ex[o + 1] & 0xffffff;
+      const int nq = ex[o + 1] >> 24;
       double accA = 0.0, accB = 0.0;
-      const int top = mi_off(P - q.w + 1);
+      const int top = mi_off(P - nq + 1);
       for (int is = 0; is < top; ++is) {
-        const int4 s = tab.expo[is];
-        const double u = sm.U[mi_idx(q.x + s.x, q.y + s.y, q.z + s.z)] * tab.ifact[is];
-        accA += (s.w % 2 == 0 ? u : -u) * sm.sB[is];
+        const double u = sm.U[mi_idx_sum(pq, ex[is] & 0xffffff)];
+        accA += u * sm.sB[is];
         accB += u * sm.sA[is];
       }
-      double la = ri[q.w + 1] * accA;
-      double lb = (q.w % 2 == 0 ? 1.0 : -1.0) * ri[q.w + 1] * accB;
+      double la = ri[nq + 1] * accA;
+      double lb = (nq % 2 == 0 ? 1.0 : -1.0) * ri[nq + 1] * accB;
       if (VARIANT != FMM_UC && o < 3) {
         const double f = o == 0 ? f0 : (o == 1 ? f1 : f2);
         la -= f * invM[A];
@@ -309,13 +325,30 @@ __global__ void k_leaf_upward_tab(int P, int32_t nleaf, const int32_t *__restric
 
 // one warp per cell of a level: centre of mass from the children (as at
 // order 3), then lanes over a: M^a = sum over children in order of
-// sum_{b <= a} C(a, b) M_child^b s^(a-b)
-__global__ void k_internal_upward_tab(int P, int32_t c0, int32_t c1, const int32_t *__restrict__ first_child,
-                                      const int32_t *__restrict__ nchild, double *__restrict__ S,
-                                      double *__restrict__ M, double *__restrict__ Z, double *__restrict__ invM,
-                                      double *__restrict__ mom, TabDev tab) {
-  const int c = c0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
+// sum_{b <= a} C(a, b) M_child^b s^(a-b); binomials and the powers of each
+// child's shift s from shared memory
+constexpr int kTabLevelWarps = 4;
+
+__global__ void __launch_bounds__(kTabLevelWarps * 32) k_internal_upward_tab(
+    int P, int32_t c0, int32_t c1, const int32_t *__restrict__ first_child, const int32_t *__restrict__ nchild,
+    double *__restrict__ S, double *__restrict__ M, double *__restrict__ Z, double *__restrict__ invM,
+    double *__restrict__ mom, TabDev tab) {
+  __shared__ double binom_t[kTabMaxP + 1][kTabMaxP + 1];
+  __shared__ double pw[kTabLevelWarps][3][kTabMaxP + 1];
+  __shared__ int ex[kNUMax];
+  for (int q = threadIdx.x; q < (kTabMaxP + 1) * (kTabMaxP + 1); q += blockDim.x) {
+    const int n = q / (kTabMaxP + 1), k = q % (kTabMaxP + 1);
+    double r = 0.0;
+    if (k <= n) {
+      r = 1.0;
+      for (int t = 1; t <= k; ++t) r = r * (n - k + t) / t;
+    }
+    binom_t[n][k] = r;
+  }
+  load_expo(ex, tab.expo);
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = c0 + blockIdx.x * kTabLevelWarps + w;
   if (c >= c1) return;
   const int nch = nchild[c];
   if (nch == 0) return;
@@ -326,51 +359,83 @@ __global__ void k_internal_upward_tab(int P, int32_t c0, int32_t c1, const int32
   z[1] = __shfl_sync(0xffffffffu, z[1], 0);
   z[2] = __shfl_sync(0xffffffffu, z[2], 0);
   const int NM = mi_off(P + 1);
-  double *out = mom + static_cast<int64_t>(c) * NM;
-  for (int i = lane; i < NM; i += 32) {
-    const int4 a = tab.expo[i];
-    double acc = 0.0;
-    for (int k = f; k < f + nch; ++k) {
-      const double s0 = Z[3 * k] - z[0], s1 = Z[3 * k + 1] - z[1], s2 = Z[3 * k + 2] - z[2];
-      const double *mc = mom + static_cast<int64_t>(k) * NM;
-      for (int b0 = 0; b0 <= a.x; ++b0)
-        for (int b1 = 0; b1 <= a.y; ++b1)
-          for (int b2 = 0; b2 <= a.z; ++b2) {
-            double v = binom(a.x, b0) * binom(a.y, b1) * binom(a.z, b2) * mc[mi_idx(b0, b1, b2)];
-            for (int t = b0; t < a.x; ++t) v *= s0;
-            for (int t = b1; t < a.y; ++t) v *= s1;
-            for (int t = b2; t < a.z; ++t) v *= s2;
-            acc += v;
-          }
+  double acc[(kNMMax + 31) / 32];
+#pragma unroll
+  for (int u = 0; u < (kNMMax + 31) / 32; ++u) acc[u] = 0.0;
+  for (int k = f; k < f + nch; ++k) {
+    __syncwarp();
+    if (lane < 3) {
+      const double sv = Z[3 * k + lane] - z[lane];
+      double p = 1.0;
+      for (int q = 0; q <= kTabMaxP; ++q) {
+        pw[w][lane][q] = p;
+        p *= sv;
+      }
     }
-    out[i] = acc;
+    __syncwarp();
+    const double *mc = mom + static_cast<int64_t>(k) * NM;
+#pragma unroll
+    for (int u = 0; u < (kNMMax + 31) / 32; ++u) {
+      const int i = lane + 32 * u;
+      if (i >= NM) continue;
+      const int e = ex[i];
+      const int a0 = e & 255, a1 = (e >> 8) & 255, a2 = (e >> 16) & 255;
+      double v = 0.0;
+      for (int b0 = 0; b0 <= a0; ++b0) {
+        const double f0 = binom_t[a0][b0] * pw[w][0][a0 - b0];
+        for (int b1 = 0; b1 <= a1; ++b1) {
+          const double f1 = f0 * binom_t[a1][b1] * pw[w][1][a1 - b1];
+          for (int b2 = 0; b2 <= a2; ++b2)
+            v += f1 * binom_t[a2][b2] * pw[w][2][a2 - b2] * mc[mi_idx(b0, b1, b2)];
+        }
+      }
+      acc[u] += v;
+    }
   }
-  __syncwarp();
-  if (lane == 0) out[0] = M[c];
+  double *out = mom + static_cast<int64_t>(c) * NM;
+#pragma unroll
+  for (int u = 0; u < (kNMMax + 31) / 32; ++u) {
+    const int i = lane + 32 * u;
+    if (i < NM) out[i] = i == 0 ? M[c] : acc[u];
+  }
 }
 
 // one warp per cell of a level: L^a(cell) += sum_g L^(a+g)(parent) s^g / g!
-__global__ void k_l2l_tab(int P, int32_t c0, int32_t c1, const int32_t *__restrict__ parent,
-                          const double *__restrict__ Z, double *__restrict__ loc, TabDev tab) {
-  const int c = c0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kTabLevelWarps * 32) k_l2l_tab(int P, int32_t c0, int32_t c1,
+                                                                 const int32_t *__restrict__ parent,
+                                                                 const double *__restrict__ Z,
+                                                                 double *__restrict__ loc, TabDev tab) {
+  __shared__ double pw[kTabLevelWarps][3][kTabMaxP + 1];
+  __shared__ int ex[kNUMax];
+  __shared__ double ifa[kNUMax];
+  load_expo(ex, tab.expo);
+  for (int i = threadIdx.x; i < kNUMax; i += blockDim.x) ifa[i] = tab.ifact[i];
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = c0 + blockIdx.x * kTabLevelWarps + w;
   if (c >= c1) return;
   const int p = parent[c];
-  const double s0 = Z[3 * c] - Z[3 * p], s1 = Z[3 * c + 1] - Z[3 * p + 1], s2 = Z[3 * c + 2] - Z[3 * p + 2];
+  if (lane < 3) {
+    const double sv = Z[3 * c + lane] - Z[3 * p + lane];
+    double q = 1.0;
+    for (int t = 0; t <= kTabMaxP; ++t) {
+      pw[w][lane][t] = q;
+      q *= sv;
+    }
+  }
+  __syncwarp();
   const int NL = mi_off(P + 1) - 1;
   const double *Lp = loc + static_cast<int64_t>(p) * NL;
   double *Lc = loc + static_cast<int64_t>(c) * NL;
   for (int o = lane; o < NL; o += 32) {
-    const int4 a = tab.expo[o + 1];
+    const int pa = ex[o + 1] & 0xffffff;
+    const int na = ex[o + 1] >> 24;
     double acc = 0.0;
-    const int top = mi_off(P - a.w + 1);
+    const int top = mi_off(P - na + 1);
     for (int ig = 0; ig < top; ++ig) {
-      const int4 g = tab.expo[ig];
-      double v = Lp[mi_idx(a.x + g.x, a.y + g.y, a.z + g.z) - 1] * tab.ifact[ig];
-      for (int t = 0; t < g.x; ++t) v *= s0;
-      for (int t = 0; t < g.y; ++t) v *= s1;
-      for (int t = 0; t < g.z; ++t) v *= s2;
-      acc += v;
+      const int eg = ex[ig];
+      const double mono = pw[w][0][eg & 255] * pw[w][1][(eg >> 8) & 255] * pw[w][2][(eg >> 16) & 255];
+      acc += Lp[mi_idx_sum(pa, eg & 0xffffff) - 1] * (ifa[ig] * mono);
     }
     Lc[o] += acc;
   }
@@ -423,7 +488,7 @@ int upward_table(fmm_ctx *c) {
   for (int lev = c->sz.depth - 1; lev >= 0; --lev) {
     const int64_t c0 = c->sz.lvl_off[lev], c1 = c->sz.lvl_off[lev + 1];
     if (c1 <= c0) continue;
-    k_internal_upward_tab<<<grid_for((c1 - c0) * 32, 128), 128, 0, st>>>(
+    k_internal_upward_tab<<<grid_for(c1 - c0, kTabLevelWarps), kTabLevelWarps * 32, 0, st>>>(
         P, static_cast<int32_t>(c0), static_cast<int32_t>(c1), ptr<int32_t>(c->first_child), ptr<int32_t>(c->nchild),
         ptr<double>(c->S), ptr<double>(c->M), ptr<double>(c->Z), ptr<double>(c->invM), ptr<double>(c->mom), tab);
     AMFMM_TRY(launched(c, "internal_upward_tab"));
@@ -461,7 +526,7 @@ int downward_table(fmm_ctx *c) {
   for (int lev = 1; lev <= c->sz.depth; ++lev) {
     const int64_t c0 = c->sz.lvl_off[lev], c1 = c->sz.lvl_off[lev + 1];
     if (c1 <= c0) continue;
-    k_l2l_tab<<<grid_for((c1 - c0) * 32, 128), 128, 0, st>>>(P, static_cast<int32_t>(c0), static_cast<int32_t>(c1),
+    k_l2l_tab<<<grid_for(c1 - c0, kTabLevelWarps), kTabLevelWarps * 32, 0, st>>>(P, static_cast<int32_t>(c0), static_cast<int32_t>(c1),
                                                              ptr<int32_t>(c->parent), ptr<double>(c->Z),
                                                              ptr<double>(c->loc), tab);
     AMFMM_TRY(launched(c, "l2l_tab"));

@@ -182,6 +182,10 @@ __global__ void __launch_bounds__(kGenBlock, kGenBlocksPerSM) k_walk_gen(
     return;
   }
   const int64_t m2l_base = in.m2l, p2p_base = in.p2p, self_base = in.self;
+  // a generation of few tiles needs few blocks: blocks beyond the tile count
+  // leave without drawing a ticket (the others take every tile; a block
+  // still waits only for tiles that blocks already running have taken)
+  if (static_cast<int64_t>(blockIdx.x) >= nb) return;
   for (;;) {
   if (t == 0) s_place = atomicAdd(&G.ticket, 1u);
   __syncthreads();

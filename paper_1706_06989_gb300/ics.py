@@ -121,11 +121,24 @@ def binary_plummer(n: int, seed: int = 0, m1: float = 0.6, a1: float = 0.05, m2:
     return Bodies(x, y, z, m, vx, vy, vz)
 
 
+def power_law_masses(rng: np.random.Generator, n: int, total: float, slope: float = 2.35,
+                     ratio: float = 100.0) -> np.ndarray:
+    """n masses drawn from dN/dm ~ m^-slope on [1, ratio] (inverse cumulative
+    distribution; slope 2.35 is Salpeter's), scaled to sum to total."""
+    u = rng.uniform(0.0, 1.0, n)
+    e = 1.0 - slope
+    m = (1.0 + u * (ratio ** e - 1.0)) ** (1.0 / e)
+    return m * (total / m.sum())
+
+
 def hernquist_disc(n: int, seed: int = 0, a: float = 1.0, disc_frac: float = 0.3,
-                   h_r: float = 0.1, h_z: float = 0.01, rcut: float = 100.0) -> Bodies:
+                   h_r: float = 0.1, h_z: float = 0.01, rcut: float = 100.0,
+                   mass_spectrum: bool = False) -> Bodies:
     """Hernquist halo (scale a, truncated at rcut * a) holding 1 - disc_frac of
     the mass, plus an exponential disc (surface density ~ exp(-R/h_r),
-    sech^2 vertical profile of height h_z) holding disc_frac; equal masses."""
+    sech^2 vertical profile of height h_z) holding disc_frac; equal masses,
+    or (mass_spectrum) masses over two decades from a Salpeter power law,
+    each component keeping its share of the mass."""
     rng = _rng(seed)
     nd = int(round(n * disc_frac))
     nh = n - nd
@@ -148,7 +161,10 @@ def hernquist_disc(n: int, seed: int = 0, a: float = 1.0, disc_frac: float = 0.3
     x = np.concatenate([ph[:, 0], R * np.cos(phi)])
     y = np.concatenate([ph[:, 1], R * np.sin(phi)])
     z = np.concatenate([ph[:, 2], zd])
-    m = np.full(n, 1.0 / n)
+    if mass_spectrum:
+        m = np.concatenate([power_law_masses(rng, nh, 1.0 - disc_frac), power_law_masses(rng, nd, disc_frac)])
+    else:
+        m = np.full(n, 1.0 / n)
     return Bodies(x, y, z, m)
 
 
