@@ -304,7 +304,10 @@ int fmm_balance(fmm_ctx *ctx, const double *x, const double *y, const double *z,
  * that loads the library until the process exits.  All calls share it: two
  * calls whose kernels overlap on the GPU race; issue them on one stream, or
  * order them.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process, so make
+ * that first call before any stream capture, pass a stream of the current
+ * device, and do not call cudaDeviceReset between calls (that releases the
+ * library's device memory, and the kept address would be stale).
  * Returns FMM_EINVAL for n < 1 or a NULL pointer, FMM_ECUDA if a launch fails. */
 int fmm_balance_noalloc(const double *x, const double *y, const double *z, const double *m,
                         const double *ax, const double *ay, const double *az, int64_t n, double *out,

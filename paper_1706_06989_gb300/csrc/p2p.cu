@@ -743,13 +743,15 @@ int p2p_prepare(fmm_ctx *c) {
   AMFMM_CUDA(c, cudaStreamSynchronize(st));
   const int64_t nslot = h[0], ncol = hc[0];
   const int64_t nitem = hc[1], nextra = hc[2];
+  // the slots are addressed with int32 offsets: refuse before anything is
+  // sized or launched from these totals
+  if (nslot + 3 > 0x7fffffffLL) return set_error(c, FMM_EUNSUPPORTED, "too many near-field slots (%lld)", (long long)nslot);
   c->sz.p2p_items = nitem;
   AMFMM_TRY(ensure<int4>(c, c->p2p_items, nitem + 1));
   AMFMM_TRY(ensure<double>(c, c->p2p_extra, nextra + 1));
   k_item_fill<<<grid_for(nleaf, 256), 256, 0, st>>>(nleaf, ptr<int32_t>(c->leaves), ptr<int32_t>(c->count), colOff,
                                                     itemOff, extraOff, ptr<int4>(c->p2p_items));
   AMFMM_TRY(launched(c, "p2p_item_fill"));
-  if (nslot + 3 > 0x7fffffffLL) return set_error(c, FMM_EUNSUPPORTED, "too many near-field slots (%lld)", (long long)nslot);
   AMFMM_TRY(ensure_bytes(c, c->p2p_slots, static_cast<size_t>(nslot + 3) * (fp32 ? sizeof(float) : sizeof(double))));
   AMFMM_TRY(ensure<int2>(c, c->p2p_cols, ncol + 1));
   k_cols_self<<<grid_for(nleaf, 256), 256, 0, st>>>(nleaf, ptr<int32_t>(c->leaves), ptr<int32_t>(c->begin),
