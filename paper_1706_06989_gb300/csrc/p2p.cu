@@ -76,6 +76,34 @@ __device__ __forceinline__ float p2p_min_r2<float>() { return 1e-30f; }
 __device__ __forceinline__ bool p2p_apart(double r2) { return __double_as_longlong(r2) != 0; }
 __device__ __forceinline__ bool p2p_apart(float r2) { return r2 > p2p_min_r2<float>(); }
 
+// R consecutive rows i.. against one column body (FP32 form): the B-side sum
+// in row order, then the A-side partials.
+template <int R>
+__device__ __forceinline__ void rows32(P2PSmem<float> &sm, int i, int l, bool valid, bool mutual, float xj,
+                                       float yj, float zj, float mj, float eps2, float &bx, float &by,
+                                       float &bz) {
+  float dx[R], dy[R], dz[R], r3[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const float4 rw = *reinterpret_cast<const float4 *>(sm.row[i + u]);
+    dx[u] = rw.x - xj;
+    dy[u] = rw.y - yj;
+    dz[u] = rw.z - zj;
+    const float r2 = fmaf(dz[u], dz[u], fmaf(dy[u], dy[u], fmaf(dx[u], dx[u], eps2)));
+    const bool ok = valid && r2 > p2p_min_r2<float>();
+    const float ri = ok ? rsqrtf(r2) : 0.f;
+    r3[u] = ri * ri * ri;
+    const float si = rw.w * r3[u];
+    bx += si * dx[u];
+    by += si * dy[u];
+    bz += si * dz[u];
+  }
+  if (mutual) {
+#pragma unroll
+    for (int u = 0; u < R; ++u) acc_sub(sm, i + u, l, mj * r3[u], dx[u], dy[u], dz[u]);
+  }
+}
+
 template <class T>
 __device__ __forceinline__ T coord(double v, double z);
 template <>
@@ -132,91 +160,6 @@ __device__ __forceinline__ RawBody<T> load_body(int j, bool valid, const BodyF *
     }
   }
   return r;
-}
-
-// One row pass of the FP32 form: rows [0, R) of the staged rows (those from
-// nr up padded with massless bodies far away) against every column of the
-// work item.  Each lane keeps, in registers, the A-side sums of all R rows for
-// its columns and the B-side sum of its current column; the rows are read
-// from shared memory as broadcasts.  So a body pair costs its arithmetic and
-// one broadcast load, with no shared-memory update per pair; the A-side sums
-// go to shared memory once per pass (for the fixed-order sum over lanes).
-// The B-side sum of a column runs over the rows in order.
-template <int R>
-__device__ __forceinline__ void pass32(P2PSmem<float> &sm, int l, int nr, int r0, int cb, int ce,
-                                       const int2 *__restrict__ cols, const BodyF *__restrict__ bodyf, float4 zh,
-                                       float4 zl, float eps2, float *__restrict__ slots, double *__restrict__ near,
-                                       int64_t n) {
-  if (l >= nr && l < R) {
-    sm.row[l][0] = 1e18f;
-    sm.row[l][1] = 1e18f;
-    sm.row[l][2] = 1e18f;
-    sm.row[l][3] = 0.f;
-  }
-  __syncwarp();
-  float ax[R], ay[R], az[R];
-#pragma unroll
-  for (int u = 0; u < R; ++u) ax[u] = ay[u] = az[u] = 0.f;
-  int2 colN = cb + l < ce ? cols[cb + l] : make_int2(0, -2);
-  BodyF rbN{};
-  if (cb + l < ce) rbN = bodyf[colN.x];
-  int2 colNN = cb + 32 + l < ce ? cols[cb + 32 + l] : make_int2(0, -2);
-  for (int c0 = cb; c0 < ce; c0 += 32) {
-    const bool valid = c0 + l < ce;
-    const int2 col = colN;
-    const BodyF rb = rbN;
-    colN = colNN;
-    if (c0 + 32 + l < ce) rbN = bodyf[colN.x];
-    colNN = c0 + 64 + l < ce ? cols[c0 + 64 + l] : make_int2(0, -2);
-    const float3 o = offset32(rb, zh, zl);
-    const float xj = o.x, yj = o.y, zj = o.z;
-    // A-side weight: the column's mass for a partner leaf's body, 0 for A's
-    // own bodies (one-sided) and for lanes without a column
-    const float wj = (valid && col.y >= 0) ? rb.h.w : 0.f;
-    float bx = 0.f, by = 0.f, bz = 0.f;
-#pragma unroll
-    for (int u = 0; u < R; ++u) {
-      const float4 rw = *reinterpret_cast<const float4 *>(sm.row[u]);
-      const float dx = rw.x - xj, dy = rw.y - yj, dz = rw.z - zj;
-      const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-      const float ri = r2 > p2p_min_r2<float>() ? rsqrtf(r2) : 0.f;
-      const float r3 = ri * ri * ri;
-      const float si = rw.w * r3;
-      bx = fmaf(si, dx, bx);
-      by = fmaf(si, dy, by);
-      bz = fmaf(si, dz, bz);
-      const float sj = wj * r3;
-      ax[u] = fmaf(-sj, dx, ax[u]);
-      ay[u] = fmaf(-sj, dy, ay[u]);
-      az[u] = fmaf(-sj, dz, az[u]);
-    }
-    if (valid) {
-      if (col.y >= 0) {
-        float *op = slots + col.y;
-        if (r0 == 0) {
-          op[0] = bx;
-          op[1] = by;
-          op[2] = bz;
-        } else {
-          op[0] += bx;
-          op[1] += by;
-          op[2] += bz;
-        }
-      } else {
-        near[col.x] += static_cast<double>(bx);
-        near[n + col.x] += static_cast<double>(by);
-        near[2 * n + col.x] += static_cast<double>(bz);
-      }
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < R; ++u) {
-    if (u < nr) {
-      sm.acc[3 * u][l] = ax[u];
-      sm.acc[3 * u + 1][l] = ay[u];
-      sm.acc[3 * u + 2][l] = az[u];
-    }
-  }
 }
 
 template <class T>
@@ -280,12 +223,6 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
         sm.row[l][3] = T(Mb[i]);
       }
     }
-    if constexpr (sizeof(T) == sizeof(float)) {
-      __syncwarp();
-      if (nr > 8) pass32<16>(sm, l, nr, r0, cb, ce, cols, bodyf, zh, zl, eps2, slots, near, n);
-      else if (nr > 4) pass32<8>(sm, l, nr, r0, cb, ce, cols, bodyf, zh, zl, eps2, slots, near, n);
-      else pass32<4>(sm, l, nr, r0, cb, ce, cols, bodyf, zh, zl, eps2, slots, near, n);
-    } else {
     acc_zero(sm, nr, l);
     __syncwarp();
     // columns: A's own bodies (one-sided, self) then the bodies of every
@@ -318,8 +255,16 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
       }
       const bool mutual = col.y >= 0;
       T bx = T(0), by = T(0), bz = T(0);
-      // FP64 is bound by its pipe: one row at a time
-      for (int i = 0; i < nr; ++i) {
+      // FP32: four rows per step, then two, independent dependency chains
+      // for the pipelines and less loop control per pair (FP64 is bound by
+      // its pipe and runs faster one row at a time)
+      int i = 0;
+      if constexpr (sizeof(T) == sizeof(float)) {
+        for (; i + 7 < nr; i += 8) rows32<8>(sm, i, l, valid, mutual, xj, yj, zj, mj, eps2, bx, by, bz);
+        for (; i + 3 < nr; i += 4) rows32<4>(sm, i, l, valid, mutual, xj, yj, zj, mj, eps2, bx, by, bz);
+        for (; i + 1 < nr; i += 2) rows32<2>(sm, i, l, valid, mutual, xj, yj, zj, mj, eps2, bx, by, bz);
+      }
+      for (; i < nr; ++i) {
         const T dx = sm.row[i][0] - xj, dy = sm.row[i][1] - yj, dz = sm.row[i][2] - zj;
         // softening enters as the addend of the first product (no extra
         // operation; eps2 = 0 gives the unsoftened sum)
@@ -355,7 +300,6 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
           near[2 * n + col.x] += static_cast<double>(bz);
         }
       }
-    }
     }
     __syncwarp();
     // A-side: every row's partials summed over the lanes in a fixed order
