@@ -535,7 +535,8 @@ def run_leapfrog(a):
 def run_ensemble(a):
     """512 independent Plummer systems with N log-uniform in [1024, 65536]
     (seed per system): the forest solve of all of them in one launch sequence
-    against one solve per system, after choosing n_crit by timing."""
+    against one solve per system, after choosing n_crit and the leaf tile
+    by timing."""
     import torch
     from paper_1706_06989_gb300 import fmm, ics
     prec = a.precision
@@ -544,8 +545,10 @@ def run_ensemble(a):
     x, y, z, m = (torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (b.x, b.y, b.z, b.m))
     n = b.n
     s = fmm.FMM(theta=a.theta, n_crit=a.n_crit, variant=a.variant, precision=prec)
-    best, tune = s.autotune_ncrit(x, y, z, m, off, candidates=(16, 25, 32, 64), reps=3)
+    best, tile, table = s.autotune(x, y, z, m, off, ncrit=(16, 25, 32, 64), tiles=(8, 16, 32), reps=3)
+    tune = {f"n_crit={k[0]},tile={k[1]}": v for k, v in table.items()}
     s.set_opts(n_crit=best)
+    s.set_tile(tile)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     out = tuple(torch.empty(n, dtype=torch.float64, device=dev) for _ in range(3))
@@ -579,7 +582,7 @@ def run_ensemble(a):
     st = s.stats()
     print(json.dumps({"experiment": "ensemble", "workload": "512 Plummer systems, N log-uniform [1024, 65536], seed per system",
                       "n_total": n, "precision": prec, "variant": a.variant, "theta": a.theta,
-                      "autotune_ms": tune, "n_crit": best,
+                      "autotune_ms": tune, "n_crit": best, "tile": tile,
                       "batched": {"ms": batched_ms, "bodies_per_s": n / (batched_ms / 1e3)},
                       "one_solve_per_system": {"ms": loop_ms, "bodies_per_s": n / (loop_ms / 1e3)},
                       "speedup": loop_ms / batched_ms}), flush=True)

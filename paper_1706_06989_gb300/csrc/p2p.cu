@@ -29,39 +29,39 @@ namespace amfmm {
 namespace {
 
 constexpr int kWarps = 4;
-// rows of A held in shared memory per pass.  16 measured best in both forms
-// at N = 1M: against 32 it halves the shared memory per warp and doubles the
-// resident warps (FP32 P2P 1.68 -> 1.10 ms, FP64 19.8 -> 18.2 ms); 8 costs
-// more column passes than it gains (1.22 / 18.4 ms).
-template <class T>
-constexpr int kRowsOf = 16;
+// Rows of A held in shared memory per pass (the leaf tile): 8, 16 or 32,
+// chosen per context (fmm_set_tile, fmm_autotune).  16 measured best in both
+// forms on a Plummer sphere of N = 1M: against 32 it halves the shared memory
+// per warp and doubles the resident warps (FP32 P2P 1.68 -> 1.10 ms, FP64
+// 19.8 -> 18.2 ms); 8 costs more column passes than it gains (1.22 / 18.4
+// ms).  Ensembles of small systems may prefer another tile.
 
 __device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
 __device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
 
 // Shared memory per warp: the rows (bodies of A) and, per row and component,
 // one running partial of the A-side sum for every lane.
-template <class T>
+template <class T, int ROWS>
 struct P2PSmem {
-  alignas(16) T row[kRowsOf<T>][4];  // x, y, z, m of the current row chunk (16-byte loads)
-  T acc[kRowsOf<T> * 3][32];         // A-side partial sums, [3 i + d][lane]
+  alignas(16) T row[ROWS][4];  // x, y, z, m of the current row chunk (16-byte loads)
+  T acc[ROWS * 3][32];         // A-side partial sums, [3 i + d][lane]
 };
-template <class T>
-__device__ __forceinline__ void acc_zero(P2PSmem<T> &sm, int nr, int l) {
+template <class T, int ROWS>
+__device__ __forceinline__ void acc_zero(P2PSmem<T, ROWS> &sm, int nr, int l) {
   for (int v = 0; v < 3 * nr; ++v) sm.acc[v][l] = T(0);
 }
 // partial of row i, lane l -= s (dx, dy, dz).  (One float4 per (row, lane)
 // for the FP32 form, one 16-byte load and store per update, measured 1%
 // slower at N = 1M than these three scalar updates.)
-template <class T>
-__device__ __forceinline__ void acc_sub(P2PSmem<T> &sm, int i, int l, T s, T dx, T dy, T dz) {
+template <class T, int ROWS>
+__device__ __forceinline__ void acc_sub(P2PSmem<T, ROWS> &sm, int i, int l, T s, T dx, T dy, T dz) {
   sm.acc[3 * i][l] -= s * dx;
   sm.acc[3 * i + 1][l] -= s * dy;
   sm.acc[3 * i + 2][l] -= s * dz;
 }
 // component v % 3 of row v / 3, lane t
-template <class T>
-__device__ __forceinline__ T acc_get(const P2PSmem<T> &sm, int v, int t) { return sm.acc[v][t]; }
+template <class T, int ROWS>
+__device__ __forceinline__ T acc_get(const P2PSmem<T, ROWS> &sm, int v, int t) { return sm.acc[v][t]; }
 
 // Coordinates a lane works with: absolute in FP64; relative to Z_A (computed
 // in FP64, rounded once) in the mixed form.
@@ -78,8 +78,8 @@ __device__ __forceinline__ bool p2p_apart(float r2) { return r2 > p2p_min_r2<flo
 
 // R consecutive rows i.. against one column body (FP32 form): the B-side sum
 // in row order, then the A-side partials.
-template <int R>
-__device__ __forceinline__ void rows32(P2PSmem<float> &sm, int i, int l, bool valid, bool mutual, float xj,
+template <int R, int ROWS>
+__device__ __forceinline__ void rows32(P2PSmem<float, ROWS> &sm, int i, int l, bool valid, bool mutual, float xj,
                                        float yj, float zj, float mj, float eps2, float &bx, float &by,
                                        float &bz) {
   float dx[R], dy[R], dz[R], r3[R];
@@ -162,7 +162,7 @@ __device__ __forceinline__ RawBody<T> load_body(int j, bool valid, const BodyF *
   return r;
 }
 
-template <class T>
+template <class T, int ROWS>
 __global__ void __launch_bounds__(kWarps * 32) k_p2p(
     int32_t nitem, int64_t n, const int4 *__restrict__ items, const int32_t *__restrict__ begin,
     const int32_t *__restrict__ count, const double *__restrict__ Zc, const double *__restrict__ X,
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
     T *__restrict__ slots, const BodyF *__restrict__ bodyf, T eps2, int *__restrict__ queue) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  P2PSmem<T> &sm = reinterpret_cast<P2PSmem<T> *>(smem_raw)[w];
+  P2PSmem<T, ROWS> &sm = reinterpret_cast<P2PSmem<T, ROWS> *>(smem_raw)[w];
   // Work items differ in size by orders of magnitude, so warps draw them
   // from a queue until it is empty instead of taking a fixed one: a block's
   // warps then never wait for one another's items (the grid is as large as
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
     }
   }
   __syncwarp();
-  constexpr int kRows = kRowsOf<T>;
+  constexpr int kRows = ROWS;
   for (int r0 = 0; r0 < nA; r0 += kRows) {
     const int nr = min(kRows, nA - r0);
     if (l < nr) {
@@ -260,9 +260,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
       // its pipe and runs faster one row at a time)
       int i = 0;
       if constexpr (sizeof(T) == sizeof(float)) {
-        for (; i + 7 < nr; i += 8) rows32<8>(sm, i, l, valid, mutual, xj, yj, zj, mj, eps2, bx, by, bz);
-        for (; i + 3 < nr; i += 4) rows32<4>(sm, i, l, valid, mutual, xj, yj, zj, mj, eps2, bx, by, bz);
-        for (; i + 1 < nr; i += 2) rows32<2>(sm, i, l, valid, mutual, xj, yj, zj, mj, eps2, bx, by, bz);
+        for (; i + 7 < nr; i += 8) rows32<8, ROWS>(sm, i, l, valid, mutual, xj, yj, zj, mj, eps2, bx, by, bz);
+        for (; i + 3 < nr; i += 4) rows32<4, ROWS>(sm, i, l, valid, mutual, xj, yj, zj, mj, eps2, bx, by, bz);
+        for (; i + 1 < nr; i += 2) rows32<2, ROWS>(sm, i, l, valid, mutual, xj, yj, zj, mj, eps2, bx, by, bz);
       }
       for (; i < nr; ++i) {
         const T dx = sm.row[i][0] - xj, dy = sm.row[i][1] - yj, dz = sm.row[i][2] - zj;
@@ -555,21 +555,22 @@ __global__ void k_cols_pairs(int64_t K, const int2 *__restrict__ pairs, const in
   }
 }
 
-template <class T>
-int launch_p2p(fmm_ctx *c) {
+template <class T, int ROWS>
+int launch_p2p_rows(fmm_ctx *c) {
   const int64_t n = c->sz.n;
   const int32_t nleaf = static_cast<int32_t>(c->sz.nleaf);
-  const size_t shm = kWarps * sizeof(P2PSmem<T>);
+  const size_t shm = kWarps * sizeof(P2PSmem<T, ROWS>);
   // per function and device, so set on every launch (a host-side call)
-  AMFMM_CUDA(c, cudaFuncSetAttribute(k_p2p<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
+  AMFMM_CUDA(c, cudaFuncSetAttribute(k_p2p<T, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(shm)));
   const int32_t nitem = static_cast<int32_t>(c->sz.p2p_items);
   int per_sm = 0;
-  AMFMM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p<T>, kWarps * 32, shm));
+  AMFMM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p<T, ROWS>, kWarps * 32, shm));
   const int64_t resident = static_cast<int64_t>(std::max(1, per_sm)) * std::max(1, c->num_sms);
   const unsigned grid = static_cast<unsigned>(std::min<int64_t>(grid_for(nitem, kWarps), resident));
   int *queue = ptr<int32_t>(c->totals) + 40;
   AMFMM_CUDA(c, cudaMemsetAsync(queue, 0, sizeof(int), c->stream));
-  k_p2p<T><<<grid, kWarps * 32, shm, c->stream>>>(
+  k_p2p<T, ROWS><<<grid, kWarps * 32, shm, c->stream>>>(
       nitem, n, ptr<int4>(c->p2p_items), ptr<int32_t>(c->begin), ptr<int32_t>(c->count),
       ptr<double>(c->Z), ptr<double>(c->X), ptr<double>(c->Y), ptr<double>(c->Zb), ptr<double>(c->Mb),
       ptr<int2>(c->p2p_cols), ptr<double>(c->near), ptr<double>(c->p2p_extra),
@@ -583,6 +584,15 @@ int launch_p2p(fmm_ctx *c) {
     AMFMM_TRY(launched(c, "p2p_chunks"));
   }
   return FMM_OK;
+}
+
+template <class T>
+int launch_p2p(fmm_ctx *c) {
+  switch (c->p2p_rows) {
+    case 8: return launch_p2p_rows<T, 8>(c);
+    case 32: return launch_p2p_rows<T, 32>(c);
+    default: return launch_p2p_rows<T, 16>(c);
+  }
 }
 
 template <class T>

@@ -65,6 +65,8 @@ def load() -> ctypes.CDLL:
                 "fmm_set_opts": [P, ctypes.POINTER(_Opts)],
                 "fmm_set_timing": [P, I],
                 "fmm_set_softening": [P, D],
+                "fmm_set_tile": [P, I],
+                "fmm_autotune": [P, P, P, P, P, P, I, P, I, P, I, I, P, P, P, P, P, P],
                 "fmm_build_tree": [P, P, P, P, P, I64, D],
                 "fmm_upward": [P],
                 "fmm_interact": [P],
@@ -198,6 +200,10 @@ class FMM:
         and of direct(); 0 restores the unsoftened method."""
         self._check(self.lib.fmm_set_softening(self._h, float(eps)), "fmm_set_softening")
 
+    def set_tile(self, rows: int):
+        """Rows of a leaf staged per pass of the near field (8, 16 or 32)."""
+        self._check(self.lib.fmm_set_tile(self._h, int(rows)), "fmm_set_tile")
+
     def set_timing(self, on: bool = True):
         self._check(self.lib.fmm_set_timing(self._h, int(bool(on))), "fmm_set_timing")
 
@@ -303,6 +309,26 @@ class FMM:
                                                 *(_dptr(o) for o in out), ctypes.byref(best),
                                                 ctypes.c_void_p(ms.ctypes.data)), "fmm_autotune_ncrit")
         return int(best.value), {int(k): float(v) for k, v in zip(cand, ms)}
+
+    def autotune(self, x, y, z, m, offsets, ncrit=(16, 25, 32, 64), tiles=(8, 16, 32), reps: int = 3):
+        """Times the batched solve for every (n_crit, tile) pair; returns
+        (best n_crit, best tile, {(n_crit, tile): ms})."""
+        import numpy as np
+        t = self._torch
+        x, y, z, m = (self._as_dev(a) for a in (x, y, z, m))
+        off, offp = self._offsets(offsets)
+        nc = np.ascontiguousarray(ncrit, dtype=np.int32)
+        tl = np.ascontiguousarray(tiles, dtype=np.int32)
+        ms = np.zeros(len(nc) * len(tl), dtype=np.float32)
+        bn, bt = ctypes.c_int(0), ctypes.c_int(0)
+        out = tuple(t.empty(x.shape[0], dtype=t.float64, device=x.device) for _ in range(3))
+        self._bodies = (x, y, z, m)
+        self._check(self.lib.fmm_autotune(self._h, _dptr(x), _dptr(y), _dptr(z), _dptr(m), offp, len(off) - 1,
+                                          ctypes.c_void_p(nc.ctypes.data), len(nc), ctypes.c_void_p(tl.ctypes.data),
+                                          len(tl), int(reps), *(_dptr(o) for o in out), ctypes.byref(bn),
+                                          ctypes.byref(bt), ctypes.c_void_p(ms.ctypes.data)), "fmm_autotune")
+        table = {(int(a), int(b)): float(ms[i * len(tl) + j]) for i, a in enumerate(nc) for j, b in enumerate(tl)}
+        return int(bn.value), int(bt.value), table
 
     # ---- learned pair selector (a12) -------------------------------------------
     def selector_nparams(self) -> int:
