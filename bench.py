@@ -66,6 +66,7 @@ def _args():
     p.add_argument("--n-crit", type=int, default=25)
     p.add_argument("--variant", default="TC", choices=["UC", "TC", "TCO"])
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--order-p", type=int, default=3, help="expansion order (4 .. 8: FP64 only, App. A)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-other", action="store_true", help="skip timing the other precision form")
@@ -84,7 +85,8 @@ def _args():
 
 
 def _workload(a) -> str:
-    return (f"plummer_n{a.n}_theta{a.theta}_ncrit{a.n_crit}_{a.variant.lower()}_{a.precision}")
+    order = f"_p{a.order_p}" if getattr(a, "order_p", 3) != 3 else ""
+    return (f"plummer_n{a.n}_theta{a.theta}_ncrit{a.n_crit}_{a.variant.lower()}_{a.precision}{order}")
 
 
 def _dist():
@@ -270,7 +272,7 @@ def run_ours(a):
     out = tuple(torch.empty(a.n, dtype=torch.float64, device=dev) for _ in range(3))
     stream = torch.cuda.current_stream()
     solver = fmm.FMM(theta=a.theta, n_crit=a.n_crit, variant=a.variant, precision=a.precision,
-                     stream=stream)
+                     order_P=a.order_p, stream=stream)
     solver.set_timing(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     # measured peak of the FMA pipe that bounds the interaction kernels
@@ -310,7 +312,9 @@ def run_ours(a):
     m2l_flops = M2L_FLOPS[a.variant] * st.n_m2l
     p2p_flops = P2P_FLOPS_PER_BODY_PAIR * st.p2p_body_pairs
     peak = FP64_PEAK if a.precision == "fp64" else FP32_PEAK
-    if m2l_ms >= p2p_ms:
+    if a.order_p != 3:
+        m2l_flops = 0  # counted at order 3 only; the near field is the measured kernel
+    if m2l_ms >= p2p_ms and a.order_p == 3:
         dom, dom_ms, dom_flops = "m2l", m2l_ms, m2l_flops
     else:
         dom, dom_ms, dom_flops = "p2p", p2p_ms, p2p_flops
@@ -411,7 +415,7 @@ def run_ours(a):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f32+f64",
                 "data": "synthetic",
                 "config": {"workload": _workload(a), "n": a.n, "theta": a.theta, "n_crit": a.n_crit,
-                           "variant": a.variant, "precision": a.precision, "order_P": 3,
+                           "variant": a.variant, "precision": a.precision, "order_P": a.order_p,
                            "ics": "Plummer sphere, equal masses, G=1, M=1, a=1, seed=rank",
                            "l2": "flushed (256 MiB write between timed steps)",
                            "parallelism": f"replicas x{ws}"},
