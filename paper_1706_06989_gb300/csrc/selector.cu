@@ -744,12 +744,16 @@ __global__ void __launch_bounds__(128) k_walk_scores(const int2 *__restrict__ fr
   __shared__ NetSmem s;
   __shared__ float xs[4][16][kF];
   __shared__ float adj[4][16];
+  const int64_t K = *ncand;
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(scored, static_cast<unsigned long long>(K));
+  // the grid is sized for the largest frontier: a block with no candidate
+  // group leaves before it stages the network (36 KB per block, at every
+  // generation of the walk)
+  if (static_cast<int64_t>(blockIdx.x) * 4 * 16 >= K) return;
   load_net(s, params);
   __syncthreads();
   NetRegs wr;
   load_regs(s, wr);
-  const int64_t K = *ncand;
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(scored, static_cast<unsigned long long>(K));
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2;
   for (int64_t grp = static_cast<int64_t>(blockIdx.x) * 4 + w; grp * 16 < K;
        grp += static_cast<int64_t>(gridDim.x) * 4) {

@@ -12,8 +12,15 @@ constexpr int kScanTile = kScanBlock * kScanItems;
 constexpr int kRedundantTiles = 4096;  // up to 8M elements: two launches per scan
 
 constexpr int kSortBlock = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortBlock * kSortItems;
+// keys per thread of a sort tile, per key type
+template <class K>
+struct SortCfg {
+  static constexpr int kItems = 16;
+};
+template <class K>
+constexpr int kSortItems = SortCfg<K>::kItems;
+template <class K>
+constexpr int kSortTile = kSortBlock * kSortItems<K>;
 constexpr int kDigitBits = 9;
 constexpr int kRadix = 1 << kDigitBits;  // 512 buckets per pass
 constexpr unsigned kDigitMask = kRadix - 1;
@@ -181,11 +188,11 @@ __global__ void k_radix_hist(const K *__restrict__ key, int64_t n, int shift,
   __shared__ int cnt[kRadix];
   for (int d = threadIdx.x; d < kRadix; d += kSortBlock) cnt[d] = 0;
   __syncthreads();
-  const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile;
-  if (base + kSortTile <= n) {
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kSortTile<K>;
+  if (base + kSortTile<K> <= n) {
     // whole tile: 16-byte loads (the tile starts 16-byte aligned), all in
     // flight before the counting
-    constexpr int kPer = 16 / sizeof(K), kLoads = kSortItems / kPer;
+    constexpr int kPer = 16 / sizeof(K), kLoads = kSortItems<K> / kPer;
     using V = uint4;
     V v[kLoads];
     const V *kv = reinterpret_cast<const V *>(key + base);
@@ -198,7 +205,7 @@ __global__ void k_radix_hist(const K *__restrict__ key, int64_t n, int shift,
       for (int u = 0; u < kPer; ++u) atomicAdd(&cnt[static_cast<int>((e[u] >> shift) & kDigitMask)], 1);
     }
   } else {
-    for (int k = 0; k < kSortItems; ++k) {
+    for (int k = 0; k < kSortItems<K>; ++k) {
       int64_t i = base + static_cast<int64_t>(k) * kSortBlock + threadIdx.x;
       if (i < n) atomicAdd(&cnt[static_cast<int>((key[i] >> shift) & kDigitMask)], 1);
     }
@@ -217,8 +224,10 @@ __global__ void k_radix_hist(const K *__restrict__ key, int64_t n, int shift,
 // digit-sorted order; the tile is staged in that order in shared memory and
 // written out so that consecutive threads store consecutive positions of a
 // bucket (coalesced).
-constexpr int kWarpKeys = kSortTile / (kSortBlock / 32);  // 512
-constexpr int kRounds = kWarpKeys / 32;                   // 16
+template <class K>
+constexpr int kWarpKeys = kSortTile<K> / (kSortBlock / 32);  // 512 at 16 keys per thread
+template <class K>
+constexpr int kRounds = kWarpKeys<K> / 32;
 static_assert(kRadix == 2 * kSortBlock, "the scan gives each thread two digits");
 
 template <class K>
@@ -227,7 +236,10 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(
     const int32_t *__restrict__ offs, int ntiles, K *__restrict__ okey, uint32_t *__restrict__ oval) {
   constexpr int kW = kSortBlock / 32;
   constexpr size_t kCntBytes = sizeof(int) * kW * (kRadix + 1);
-  constexpr size_t kStageBytes = sizeof(K) * kSortTile;
+  constexpr size_t kStageBytes = sizeof(K) * kSortTile<K>;
+  constexpr int kRounds = ::amfmm::kRounds<K>;
+  constexpr int kWarpKeys = ::amfmm::kWarpKeys<K>;
+  constexpr int kSortTile = ::amfmm::kSortTile<K>;
   __shared__ __align__(16) unsigned char pool[kCntBytes > kStageBytes ? kCntBytes : kStageBytes];
   __shared__ int dstart[kRadix];
   __shared__ int goff[kRadix];
@@ -329,7 +341,7 @@ int radix_sort(fmm_ctx *c, DBuf key[2], DBuf val[2], int64_t n, int bits, int *w
   *which = 0;
   if (n <= 1 || bits <= 0) return FMM_OK;
   if (n > 0x7fffffffLL) return set_error(c, FMM_EINVAL, "radix sort: n too large");
-  const int ntiles = static_cast<int>((n + kSortTile - 1) / kSortTile);
+  const int ntiles = static_cast<int>((n + kSortTile<K> - 1) / kSortTile<K>);
   const int64_t nh = static_cast<int64_t>(kRadix) * ntiles;
   AMFMM_TRY(ensure<int32_t>(c, c->sort_hist, 2 * nh + 64));
   AMFMM_TRY(ensure<K>(c, key[1], n));
