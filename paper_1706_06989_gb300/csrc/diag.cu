@@ -1,6 +1,6 @@
 // diag.cu -- a10: diagnostics.  Exact direct summation for a subset of bodies
-// (Sec. 3: the error of the method is measured against "the exact, directly
-// computed force") and the net force / torque balance of Sec. 3,
+// (Sec. 3 measures the method's error against the directly summed force) and
+// the net force / torque balance of Sec. 3,
 //     sqrt( sum_d (sum_n mu_n A_nd)^2 / sum_d (sum_n mu_n |A_nd|)^2 ),
 // with A = a (force) and A = X x a (torque).  Both are FP64 with Neumaier
 // compensated sums in a fixed order of combination, so they are

@@ -279,6 +279,22 @@ def test_mixed_precision_1m_against_oracle():
 
 
 @pytest.mark.slow
+def test_mixed_precision_4m_against_oracle():
+    """The mixed form at the size of the 4M-body comparison (Plummer N =
+    4,194,304, theta = 0.5, TC): rms relative deviation from the FP64 oracle
+    <= 1e-6 on 4,096 sampled bodies and the M2L and P2P counts the oracle's
+    walk gives."""
+    b = ics.plummer(1 << 22, seed=0)
+    s, got = _solve(b, theta=0.5, precision="mixed")
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25)
+    st = s.stats()
+    assert (st.ncell, st.n_m2l, st.n_p2p) == (o.ncell, o.n_m2l, o.n_p2p)
+    t = ics.error_subset(b.n, 4096, seed=1)
+    rel = _rel_dev(got[t], o.accel("TC", targets=t))
+    assert np.sqrt(np.mean(rel ** 2)) <= 1e-6, np.sqrt(np.mean(rel ** 2))
+
+
+@pytest.mark.slow
 def test_mixed_precision_depth_capped_binary():
     """The longest FP32 sums: a binary of two dense Plummer spheres (the
     leapfrog workload's cores, N = 2,097,152) with 64 bodies thrown out to

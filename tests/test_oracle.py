@@ -98,7 +98,7 @@ def test_generic_derivatives_match_explicit_and_fd():
 
 
 # ---------------------------------------------------------------------------
-# direct summation (Sec. 3, "the exact, directly computed force")
+# direct summation (Sec. 3: the reference of the error metric)
 # ---------------------------------------------------------------------------
 def _golden_bodies(name):
     rows = []
