@@ -65,9 +65,15 @@ __device__ __forceinline__ float min_r2<float>() { return 1e-30f; }
 // - 9 t_i) R^-5 with u_i = S_ikl n_k n_l, t_i = S_ijj.  Powers of 1/R are
 // applied one factor at a time to the mass- or moment-scaled terms, so no
 // large power of 1/R is formed on its own (this keeps the FP32 form in range).
+// The correction is formed from the octupoles per unit mass, Oh = O / M (a
+// per-cell array): S = M_A O_B - M_B O_A = M_A M_B (Oh_B - Oh_A), and the
+// two masses fold into the scale factors F / M_A = M_B (F / (M_A M_B)) and
+// F / M_B = M_A (F / (M_A M_B)), so the pair needs 10 subtractions for S and
+// no divisions.  (The FP64 form runs at the FP64 pipe's rate: every
+// operation per pair counts.)
 template <class T, int VARIANT>
-__device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, T iMA, T iMB, const T *QA,
-                                         const T *QB, const T *OA, const T *OB, T eps2, T *CA, T *CB) {
+__device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, const T *QA, const T *QB, const T *OhA,
+                                         const T *OhB, T eps2, T *CA, T *CB) {
   const T r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
   if (!(r2 > min_r2<T>())) {
 #pragma unroll
@@ -79,24 +85,24 @@ __device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, T iMA, T iMB,
   const T xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
   // unit parts of D_ij and D_ijk
   const T U2[6] = {T(1) - T(3) * xx, T(-3) * xy, T(-3) * xz, T(1) - T(3) * yy, T(-3) * yz, T(1) - T(3) * zz};
-  const T fxx = T(15) * xx, fyy = T(15) * yy, fzz = T(15) * zz;
-  const T U3[10] = {(fxx - T(9)) * x, (fxx - T(3)) * y, (fxx - T(3)) * z, (fyy - T(3)) * x,
-                    T(15) * xy * z,   (fzz - T(3)) * x, (fyy - T(9)) * y, (fyy - T(3)) * z,
-                    (fzz - T(3)) * y, (fzz - T(9)) * z};
+  const T fx3 = T(15) * xx - T(3), fy3 = T(15) * yy - T(3), fz3 = T(15) * zz - T(3);
+  const T U3[10] = {(fx3 - T(6)) * x, fx3 * y, fx3 * z, fy3 * x, T(15) * xy * z, fz3 * x, (fy3 - T(6)) * y,
+                    fy3 * z, fz3 * y, (fz3 - T(6)) * z};
   // mass-scaled powers: M R^-2, M R^-3, M R^-4
-  const T MB2 = MB * Ri * Ri, MA2 = MA * Ri * Ri;
+  const T Ri2 = Ri * Ri;
+  const T MB2 = MB * Ri2, MA2 = MA * Ri2;
   const T MB3 = MB2 * Ri, MA3 = MA2 * Ri;
   const T MB4 = MB3 * Ri, MA4 = MA3 * Ri;
-  const T Ri2 = Ri * Ri;
+  const T Ri4 = Ri2 * Ri2;
   // h = Q_jk D_ijk / 2 = R^-4 [n_i (15 n.Q.n - 3 trQ) - 6 (Q n)_i] / 2
+  const T v = T(-3) * Ri4;
   T hA[3], hB[3];
   {
     const T *Q = QB;
     const T qx = Q[0] * x + Q[1] * y + Q[2] * z;
     const T qy = Q[1] * x + Q[3] * y + Q[4] * z;
     const T qz = Q[2] * x + Q[4] * y + Q[5] * z;
-    const T w = (T(7.5) * (x * qx + y * qy + z * qz) - T(1.5) * (Q[0] + Q[3] + Q[5])) * Ri2 * Ri2;
-    const T v = T(-3) * Ri2 * Ri2;
+    const T w = (T(7.5) * (x * qx + y * qy + z * qz) - T(1.5) * (Q[0] + Q[3] + Q[5])) * Ri4;
     hB[0] = w * x + v * qx;
     hB[1] = w * y + v * qy;
     hB[2] = w * z + v * qz;
@@ -106,8 +112,7 @@ __device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, T iMA, T iMB,
     const T qx = Q[0] * x + Q[1] * y + Q[2] * z;
     const T qy = Q[1] * x + Q[3] * y + Q[4] * z;
     const T qz = Q[2] * x + Q[4] * y + Q[5] * z;
-    const T w = (T(7.5) * (x * qx + y * qy + z * qz) - T(1.5) * (Q[0] + Q[3] + Q[5])) * Ri2 * Ri2;
-    const T v = T(-3) * Ri2 * Ri2;
+    const T w = (T(7.5) * (x * qx + y * qy + z * qz) - T(1.5) * (Q[0] + Q[3] + Q[5])) * Ri4;
     hA[0] = w * x + v * qx;
     hA[1] = w * y + v * qy;
     hA[2] = w * z + v * qz;
@@ -129,14 +134,15 @@ __device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, T iMA, T iMB,
     CB[9 + k] = -(MA4 * U3[k]);
   }
   if (VARIANT != FMM_UC) {
-    // S = M_A O_B - M_B O_A (xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)
+    // Sh = Oh_B - Oh_A = S / (M_A M_B) (xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)
     T S[10];
 #pragma unroll
-    for (int k = 0; k < 10; ++k) S[k] = MA * OB[k] - MB * OA[k];
+    for (int k = 0; k < 10; ++k) S[k] = OhB[k] - OhA[k];
     // u_i = S_ikl n_k n_l, t_i = S_ijj
-    const T ux = S[0] * xx + S[3] * yy + S[5] * zz + T(2) * (S[1] * xy + S[2] * xz + S[4] * yz);
-    const T uy = S[1] * xx + S[6] * yy + S[8] * zz + T(2) * (S[3] * xy + S[4] * xz + S[7] * yz);
-    const T uz = S[2] * xx + S[7] * yy + S[9] * zz + T(2) * (S[4] * xy + S[5] * xz + S[8] * yz);
+    const T xy2 = T(2) * xy, xz2 = T(2) * xz, yz2 = T(2) * yz;
+    const T ux = S[0] * xx + S[3] * yy + S[5] * zz + S[1] * xy2 + S[2] * xz2 + S[4] * yz2;
+    const T uy = S[1] * xx + S[6] * yy + S[8] * zz + S[3] * xy2 + S[4] * xz2 + S[7] * yz2;
+    const T uz = S[2] * xx + S[7] * yy + S[9] * zz + S[4] * xy2 + S[5] * xz2 + S[8] * yz2;
     const T tx = S[0] + S[3] + S[5];
     const T ty = S[1] + S[6] + S[8];
     const T tz = S[2] + S[7] + S[9];
@@ -148,11 +154,13 @@ __device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, T iMA, T iMB,
       F[1] += w * y;
       F[2] += w * z;
     }
+    // C^A_i -= F_i / M_A = M_B Fh_i R^-5,  C^B_i += F_i / M_B = M_A Fh_i R^-5
+    const T Ri5 = Ri4 * Ri;
+    const T sA = MB * Ri5, sB = MA * Ri5;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      const T f = F[i] * Ri2 * Ri2 * Ri;
-      CA[i] -= f * iMA;
-      CB[i] += f * iMB;
+      CA[i] -= F[i] * sA;
+      CB[i] += F[i] * sB;
     }
   }
 }
@@ -163,7 +171,7 @@ template <int VARIANT>
 __global__ void __launch_bounds__(kBlock) k_m2l64(int64_t K, const int2 *__restrict__ pairs,
                                                    const double *__restrict__ Z,
                                                    const double *__restrict__ M,
-                                                   const double *__restrict__ invM,
+                                                   const double *__restrict__ ohat,
                                                    const double *__restrict__ mom,
                                                    const int32_t *__restrict__ pos, double eps2,
                                                    double *__restrict__ slots) {
@@ -174,7 +182,8 @@ __global__ void __launch_bounds__(kBlock) k_m2l64(int64_t K, const int2 *__restr
   const double r[3] = {Z[3 * A] - Z[3 * B], Z[3 * A + 1] - Z[3 * B + 1], Z[3 * A + 2] - Z[3 * B + 2]};
   const double *mA = mom + static_cast<int64_t>(A) * kMomStride;
   const double *mB = mom + static_cast<int64_t>(B) * kMomStride;
-  m2l_pair<double, VARIANT>(r, M[A], M[B], invM[A], invM[B], mA + 4, mB + 4, mA + 10, mB + 10, eps2, CA, CB);
+  m2l_pair<double, VARIANT>(r, M[A], M[B], mA + 4, mB + 4, ohat + 10 * static_cast<int64_t>(A),
+                            ohat + 10 * static_cast<int64_t>(B), eps2, CA, CB);
   CA[19] = CB[19] = 0.0;
   double *sa = slots + static_cast<int64_t>(pos[2 * k]) * kLocStride;
   double *sb = slots + static_cast<int64_t>(pos[2 * k + 1]) * kLocStride;
@@ -346,6 +355,16 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_m2l32_gather(int32_t ncel
   }
 }
 
+// octupoles per unit mass, Oh = O / M, for the FP64 order-3 M2L
+__global__ void k_ohat(int32_t ncell, const double *__restrict__ invM, const double *__restrict__ mom,
+                       double *__restrict__ ohat) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= static_cast<int64_t>(ncell) * 10) return;
+  const int64_t c = t / 10;
+  const int q = static_cast<int>(t - c * 10);
+  ohat[t] = mom[c * kMomStride + 10 + q] * invM[c];
+}
+
 // FP32 copy of the cell data for the mixed form
 __global__ void k_cell32(int32_t ncell, const double *__restrict__ Z, const double *__restrict__ M,
                          const double *__restrict__ invM, const double *__restrict__ mom,
@@ -379,8 +398,14 @@ __global__ void k_pair_locals(int64_t K, const int2 *__restrict__ pairs, const d
   const double r[3] = {Z[3 * A] - Z[3 * B], Z[3 * A + 1] - Z[3 * B + 1], Z[3 * A + 2] - Z[3 * B + 2]};
   const double *mA = mom + static_cast<int64_t>(A) * kMomStride;
   const double *mB = mom + static_cast<int64_t>(B) * kMomStride;
+  double OhA[10], OhB[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) {
+    OhA[q] = mA[10 + q] * invM[A];
+    OhB[q] = mB[10 + q] * invM[B];
+  }
   // the labels are errors of the unsoftened expansion
-  m2l_pair<double, FMM_TC>(r, M[A], M[B], invM[A], invM[B], mA + 4, mB + 4, mA + 10, mB + 10, 0.0, CA, CB);
+  m2l_pair<double, FMM_TC>(r, M[A], M[B], mA + 4, mB + 4, OhA, OhB, 0.0, CA, CB);
   CA[19] = CB[19] = 0.0;
 #pragma unroll
   for (int q = 0; q < kLocStride; ++q) {
@@ -488,15 +513,15 @@ __global__ void __launch_bounds__(kRedWarps * 32) k_m2l_reduce(int32_t ncell, co
 int launch_m2l64(fmm_ctx *c, int64_t K) {
   const int2 *pairs = ptr<int2>(c->m2l);
   const unsigned g = grid_for(K, kBlock);
-  const double *Z = ptr<double>(c->Z), *M = ptr<double>(c->M), *iM = ptr<double>(c->invM),
+  const double *Z = ptr<double>(c->Z), *M = ptr<double>(c->M), *oh = ptr<double>(c->ohat),
                *mom = ptr<double>(c->mom);
   const int32_t *pos = ptr<int32_t>(c->m2l_pos);
   double *slots = ptr<double>(c->m2l_slots);
   cudaStream_t st = c->stream;
   switch (c->opts.variant) {
-    case FMM_UC: k_m2l64<FMM_UC><<<g, kBlock, 0, st>>>(K, pairs, Z, M, iM, mom, pos, c->eps2, slots); break;
-    case FMM_TC: k_m2l64<FMM_TC><<<g, kBlock, 0, st>>>(K, pairs, Z, M, iM, mom, pos, c->eps2, slots); break;
-    default: k_m2l64<FMM_TCO><<<g, kBlock, 0, st>>>(K, pairs, Z, M, iM, mom, pos, c->eps2, slots); break;
+    case FMM_UC: k_m2l64<FMM_UC><<<g, kBlock, 0, st>>>(K, pairs, Z, M, oh, mom, pos, c->eps2, slots); break;
+    case FMM_TC: k_m2l64<FMM_TC><<<g, kBlock, 0, st>>>(K, pairs, Z, M, oh, mom, pos, c->eps2, slots); break;
+    default: k_m2l64<FMM_TCO><<<g, kBlock, 0, st>>>(K, pairs, Z, M, oh, mom, pos, c->eps2, slots); break;
   }
   return launched(c, "m2l");
 }
@@ -564,6 +589,11 @@ int m2l_prepare(fmm_ctx *c) {
     k_cell32<<<grid_for(nc, 256), 256, 0, st>>>(static_cast<int32_t>(nc), ptr<double>(c->Z), ptr<double>(c->M),
                                                 ptr<double>(c->invM), ptr<double>(c->mom), ptr<float>(c->cell32));
     AMFMM_TRY(launched(c, "cell32"));
+  } else if (c->opts.order_P == 3 && c->opts.variant != FMM_UC) {
+    AMFMM_TRY(ensure<double>(c, c->ohat, static_cast<size_t>(10) * nc));
+    k_ohat<<<grid_for(nc * 10, 256), 256, 0, st>>>(static_cast<int32_t>(nc), ptr<double>(c->invM),
+                                                   ptr<double>(c->mom), ptr<double>(c->ohat));
+    AMFMM_TRY(launched(c, "ohat"));
   }
   return FMM_OK;
 }
