@@ -167,6 +167,38 @@ int fmm_solve(fmm_ctx *ctx, const double *x, const double *y, const double *z, c
 int fmm_solve_batch(fmm_ctx *ctx, const double *x, const double *y, const double *z, const double *m,
                     const int64_t *offsets, int nsys, double *ax, double *ay, double *az);
 
+/* a13: graph-captured solves.  With enable = 1, fmm_solve, fmm_solve_batch
+ * and fmm_solve_host run each solve as one CUDA-graph launch on the
+ * context's stream, no host round trip inside it:
+ *  - The first solve (and any solve whose key differs from the captured
+ *    one: caller buffers, n, nsys, options, softening, leaf tile, or a device
+ *    buffer of the context reallocated since) is solved plainly, keeping
+ *    every device value the host reads back to size its launches; the same
+ *    host code then runs again under stream capture, taking those values
+ *    instead of reading them.
+ *  - Where a plain solve reads back (the octree's level counts, the leaf
+ *    count, the walk's list lengths, the near field's totals) the graph holds
+ *    a check kernel and an IF node: the rest of the solve runs only if the
+ *    device values equal the captured ones.
+ *  - Later solves with the same key replay the graph and read one record
+ *    back.  Every kernel reads its data from the device, so new coordinates
+ *    or masses with the same sizes are solved by the replay, bit-identical
+ *    to a plain solve; when a size differs (or an input is invalid) the
+ *    record says so and the call solves plainly and captures again.
+ * Results, statistics and errors are those of a plain solve; a replay has no
+ * stage timers.  Order 3 only, without the learned selector (other solves
+ * run plainly).  Synchronises the stream.  enable = 0 (the default) keeps
+ * the plain path. */
+int fmm_set_graph(fmm_ctx *ctx, int enable);
+/* Counters of the graph-captured solves: out[0] replays that completed,
+ * out[1] captures, out[2] replays that found other sizes and fell back to a
+ * plain solve, out[3] captures abandoned (the solve itself succeeded; e.g.
+ * its planning solve had to grow a buffer), out[4] kernels in the current
+ * graph (0 if none).  out: HOST, 5 entries. */
+int fmm_graph_stats(const fmm_ctx *ctx, int64_t *out);
+/* Why the last capture was abandoned ("" if none was). */
+const char *fmm_graph_error(const fmm_ctx *ctx);
+
 /* a13: picks the leaf size for an ensemble.  Runs fmm_solve_batch once per
  * candidate n_crit (warm-up) and then `reps` timed times (CUDA events on the
  * context's stream), writes the mean ms per candidate to ms_out (HOST, ncand

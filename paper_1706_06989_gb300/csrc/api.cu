@@ -19,6 +19,9 @@ int set_error(fmm_ctx *c, int code, const char *fmt, ...) {
 
 int ensure_bytes(fmm_ctx *c, DBuf &b, size_t bytes) {
   if (bytes <= b.cap) return FMM_OK;
+  // a captured solve runs on the buffers its planning solve sized
+  if (c->gmode == kGraphCapture) return set_error(c, FMM_ECUDA, "graph capture: a buffer would grow");
+  ++c->alloc_gen;
   size_t cap = std::max(bytes, b.cap + b.cap / 2);
   cap = (cap + 255) & ~static_cast<size_t>(255);
   if (b.p) {
@@ -41,6 +44,8 @@ int ensure_bytes(fmm_ctx *c, DBuf &b, size_t bytes) {
 
 int ensure_keep_bytes(fmm_ctx *c, DBuf &b, size_t bytes, size_t used) {
   if (bytes <= b.cap) return FMM_OK;
+  if (c->gmode == kGraphCapture) return set_error(c, FMM_ECUDA, "graph capture: a buffer would grow");
+  ++c->alloc_gen;
   size_t cap = std::max(bytes, b.cap * 2);
   cap = (cap + 255) & ~static_cast<size_t>(255);
   void *p = nullptr;
@@ -68,7 +73,8 @@ int launched(fmm_ctx *c, const char *what) {
 }
 
 void timer(fmm_ctx *c, int slot) {
-  if (c->timing) cudaEventRecord(c->ev[slot], c->stream);
+  // (event records are not allowed in the conditional bodies of a graph)
+  if (c->timing && c->gmode != kGraphCapture) cudaEventRecord(c->ev[slot], c->stream);
 }
 
 }  // namespace amfmm
@@ -159,6 +165,10 @@ void fmm_destroy(fmm_ctx *c) {
                  &c->p2p_len, &c->p2p_slots, &c->p2p_colOff, &c->p2p_cols, &c->p2p_nb, &c->p2p_pre, &c->p2p_bodyf, &c->p2p_items, &c->p2p_itemOff, &c->p2p_extraOff, &c->p2p_extra, &c->scan_tmp, &c->sort_hist, &c->totals, &c->diag, &c->sel_params, &c->sel_cellfeat, &c->sel_cand, &c->sel_lga, &c->sel_scratch, &c->sel_part, &c->sel_score, &c->sel_grad, &c->sel_perm, &c->sel_xb, &c->sel_yb, &c->gen_tab, &c->hx, &c->hy,
                  &c->hz, &c->hm, &c->hax, &c->hay, &c->haz};
   for (DBuf *b : all) free_buf(*b);
+  free_buf(c->grec);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (cudaStream_t s : c->gstream)
+    if (s) cudaStreamDestroy(s);
   for (int k = 0; k < kNumTimers; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   if (c->hpin) cudaFreeHost(c->hpin);
@@ -197,13 +207,30 @@ int fmm_set_timing(fmm_ctx *c, int enable) {
   return FMM_OK;
 }
 
+int fmm_set_graph(fmm_ctx *c, int enable) {
+  if (!c) return FMM_EINVAL;
+  c->graph_enabled = enable != 0;
+  return FMM_OK;
+}
+
+int fmm_graph_stats(const fmm_ctx *c, int64_t *out) {
+  if (!c || !out) return FMM_EINVAL;
+  out[0] = c->g_replays;
+  out[1] = c->g_captures;
+  out[2] = c->g_fallbacks;
+  out[3] = c->g_capture_failures;
+  out[4] = c->gexec ? c->glaunches : 0;
+  return FMM_OK;
+}
+
 }  // extern "C"
 
 namespace {
 
 // Common start of a solve of nsys >= 1 independent systems; offsets (host,
-// nsys + 1 entries) or NULL for a single system of n bodies.
-int start_solve(fmm_ctx *c, const double *x, const double *y, const double *z, const double *m, int64_t n,
+// nsys + 1 entries) or NULL for a single system of n bodies: checks the
+// arguments and puts the system offsets on the device (synchronously).
+int begin_solve(fmm_ctx *c, const double *x, const double *y, const double *z, const double *m, int64_t n,
                 double theta, const int64_t *offsets, int nsys) {
   if (!c) return FMM_EINVAL;
   c->stage = kNone;
@@ -247,6 +274,11 @@ int start_solve(fmm_ctx *c, const double *x, const double *y, const double *z, c
     h[1] = n;
     AMFMM_CUDA(c, cudaMemcpyAsync(c->sys_off.p, h, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
   }
+  c->last_replay = false;
+  return FMM_OK;
+}
+
+int tree_stage(fmm_ctx *c) {
   timer(c, kTreeBeg);
   AMFMM_TRY(build_tree(c));
   timer(c, kTreeEnd);
@@ -254,7 +286,26 @@ int start_solve(fmm_ctx *c, const double *x, const double *y, const double *z, c
   return FMM_OK;
 }
 
+int start_solve(fmm_ctx *c, const double *x, const double *y, const double *z, const double *m, int64_t n,
+                double theta, const int64_t *offsets, int nsys) {
+  AMFMM_TRY(begin_solve(c, x, y, z, m, n, theta, offsets, nsys));
+  return tree_stage(c);
+}
+
 }  // namespace
+
+namespace amfmm {
+
+// The stages of a solve after begin_solve.
+int run_stages(fmm_ctx *c, double *ax, double *ay, double *az) {
+  AMFMM_TRY(tree_stage(c));
+  AMFMM_TRY(fmm_upward(c));
+  AMFMM_TRY(fmm_interact(c));
+  AMFMM_TRY(fmm_downward(c));
+  return fmm_forces(c, ax, ay, az);
+}
+
+}  // namespace amfmm
 
 extern "C" {
 
@@ -270,11 +321,10 @@ int fmm_solve_batch(fmm_ctx *c, const double *x, const double *y, const double *
   if (offsets[0] != 0) return set_error(c, FMM_EINVAL, "offsets[0] must be 0");
   for (int s = 0; s < nsys; ++s)
     if (offsets[s + 1] <= offsets[s]) return set_error(c, FMM_EINVAL, "system %d is empty or offsets decrease", s);
-  AMFMM_TRY(start_solve(c, x, y, z, m, offsets[nsys], 0.0, offsets, nsys));
-  AMFMM_TRY(fmm_upward(c));
-  AMFMM_TRY(fmm_interact(c));
-  AMFMM_TRY(fmm_downward(c));
-  return fmm_forces(c, ax, ay, az);
+  AMFMM_TRY(begin_solve(c, x, y, z, m, offsets[nsys], 0.0, offsets, nsys));
+  if (!ax || !ay || !az) return set_error(c, FMM_EINVAL, "NULL output array");
+  if (graph_usable(c)) return graph_solve(c, ax, ay, az);
+  return run_stages(c, ax, ay, az);
 }
 
 int fmm_upward(fmm_ctx *c) {
@@ -332,11 +382,10 @@ int fmm_forces(fmm_ctx *c, double *ax, double *ay, double *az) {
 
 int fmm_solve(fmm_ctx *c, const double *x, const double *y, const double *z, const double *m, int64_t n,
               double *ax, double *ay, double *az) {
-  AMFMM_TRY(fmm_build_tree(c, x, y, z, m, n, 0.0));
-  AMFMM_TRY(fmm_upward(c));
-  AMFMM_TRY(fmm_interact(c));
-  AMFMM_TRY(fmm_downward(c));
-  return fmm_forces(c, ax, ay, az);
+  AMFMM_TRY(begin_solve(c, x, y, z, m, n, 0.0, nullptr, 1));
+  if (!ax || !ay || !az) return set_error(c, FMM_EINVAL, "NULL output array");
+  if (graph_usable(c)) return graph_solve(c, ax, ay, az);
+  return run_stages(c, ax, ay, az);
 }
 
 int fmm_solve_host(fmm_ctx *c, const double *x, const double *y, const double *z, const double *m, int64_t n,
@@ -382,7 +431,7 @@ int fmm_get_stats(fmm_ctx *c, fmm_stats *s) {
       s->n_scored = v;
     }
   }
-  if (c->timing && c->stage >= kDown) {
+  if (c->timing && c->stage >= kDown && !c->last_replay) {
     float *ms[] = {&s->ms_tree, &s->ms_upward, &s->ms_walk, &s->ms_m2l, &s->ms_p2p, &s->ms_reduce, &s->ms_downward};
     const int beg[] = {kTreeBeg, kUpBeg, kWalkBeg, kM2LBeg, kP2PBeg, kRedBeg, kDownBeg};
     for (int k = 0; k < 7; ++k) {

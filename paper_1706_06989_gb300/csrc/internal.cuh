@@ -43,6 +43,61 @@ struct Sizes {
 
 enum Stage { kNone = 0, kTree = 1, kUp = 2, kInteract = 3, kDown = 4 };
 
+// Graph-captured solves (graph.cu).  kGraphRecord: a plain solve that keeps
+// every value it reads back from the device; kGraphCapture: the same host
+// code run again under stream capture, taking those values instead of
+// reading them.
+enum GraphMode { kGraphOff = 0, kGraphRecord = 1, kGraphCapture = 2 };
+constexpr int kMaxGraphDepth = 24;  // capture streams: the graph and one per nested check
+constexpr int kMaxExpect = 96;      // device words one check compares
+
+// What a solve's graph was captured for: a replay is valid only for the
+// same caller buffers, sizes and options, and only while no device buffer
+// of the context has been reallocated since.
+struct GraphKey {
+  const void *p[7] = {};
+  int64_t n = 0;
+  int nsys = 0;
+  double theta = 0, eps2 = 0, G = 0;
+  int n_crit = 0, order_P = 0, variant = 0, precision = 0, rows = 0;
+  int64_t alloc_gen = -1;
+  bool operator==(const GraphKey &o) const {
+    for (int k = 0; k < 7; ++k)
+      if (p[k] != o.p[k]) return false;
+    return n == o.n && nsys == o.nsys && theta == o.theta && eps2 == o.eps2 && G == o.G && n_crit == o.n_crit &&
+           order_P == o.order_P && variant == o.variant && precision == o.precision && rows == o.rows &&
+           alloc_gen == o.alloc_gen;
+  }
+};
+
+// Device words with the values the planning solve read there: a captured
+// check lets the rest of the graph run only if every word still holds its
+// value (passed to the check kernel by value).
+struct Expect {
+  const uint32_t *addr[kMaxExpect];
+  uint32_t val[kMaxExpect];
+  int n = 0;
+  bool add(const void *dev_word, uint32_t v) {
+    if (n >= kMaxExpect) return false;
+    addr[n] = static_cast<const uint32_t *>(dev_word);
+    val[n++] = v;
+    return true;
+  }
+  bool add64(const void *dev_dword, uint64_t v) {
+    const uint32_t *w = static_cast<const uint32_t *>(dev_dword);
+    return add(w, static_cast<uint32_t>(v)) && add(w + 1, static_cast<uint32_t>(v >> 32));
+  }
+};
+
+// Result record of a replay: done = 1 once the innermost check passed and
+// the solve's last kernel ran; the bounding cube for the statistics.
+struct GraphRec {
+  uint32_t done;
+  uint32_t pad;
+  double lo[3], scale;
+};
+constexpr size_t kGraphRecHostOff = 12288;  // its pinned host copy inside hpin
+
 enum TimerSlot {
   kTreeBeg = 0, kTreeEnd, kUpBeg, kUpEnd, kWalkBeg, kWalkEnd, kM2LBeg, kM2LEnd,
   kP2PBeg, kP2PEnd, kRedBeg, kRedEnd, kDownBeg, kDownEnd, kNumTimers
@@ -105,6 +160,24 @@ struct fmm_ctx {
   amfmm::DBuf gen_tab;
   // host-solve staging
   amfmm::DBuf hx, hy, hz, hm, hax, hay, haz;
+  // graph-captured solves
+  bool graph_enabled = false;
+  int gmode = amfmm::kGraphOff;
+  std::vector<std::vector<unsigned char>> gplan;  // read-backs of the planning solve, in order
+  std::vector<std::vector<unsigned char>> gplan_prev;  // those of the solve before
+  size_t gplan_pos = 0;
+  bool gwait = false;  // after a failed replay: capture again only once a plan repeats
+  char gerrbuf[512] = {0};  // why the last capture was abandoned
+  cudaStream_t gstream[amfmm::kMaxGraphDepth] = {};  // [0] the graph, [d] the body of the d-th check
+  int gdepth = 0;
+  cudaGraphExec_t gexec = nullptr;
+  amfmm::GraphKey gkey;
+  amfmm::Sizes gsz;          // sizes of the captured solve
+  int64_t glaunches = 0;     // kernels in the captured graph
+  int64_t alloc_gen = 0;     // device (re)allocations so far
+  int64_t g_replays = 0, g_captures = 0, g_fallbacks = 0, g_capture_failures = 0;
+  bool last_replay = false;  // the last solve was a graph replay (no stage timers)
+  amfmm::DBuf grec;          // GraphRec of the replays
 };
 
 namespace amfmm {
@@ -197,5 +270,30 @@ int walk_scores(fmm_ctx *c, const long long *nf_dev, int64_t cap, const int2 *fr
 int pair_locals_tc(fmm_ctx *c, const int2 *pairs, int64_t K, double *out);
 
 void timer(fmm_ctx *c, int slot);
+
+// ---------------------------------------------------------------------------
+// read-backs and graph capture (graph.cu)
+// ---------------------------------------------------------------------------
+// Device values that steer the host's launches: copied and waited for in a
+// plain solve (and kept when recording a plan); taken from the plan, in the
+// same order, while capturing.  `host` must be pinned (hpin).
+struct HostRead {
+  void *host;
+  const void *dev;
+  size_t bytes;
+};
+int read_back(fmm_ctx *c, const HostRead *r, int nr);
+inline bool capturing(const fmm_ctx *c) { return c->gmode == kGraphCapture; }
+// While capturing: a check that the device words hold the planned values,
+// and a conditional node under which the rest of the solve is captured
+// (c->stream becomes the body's capture stream).  No-op otherwise.
+int graph_expect(fmm_ctx *c, const Expect &e);
+// Copies the bounding cube (4 doubles: lo, scale) into the replay record.
+int graph_record_bbox(fmm_ctx *c, const double *bbox);
+// The solve as one graph launch (graph.cu); begin_solve has run.
+bool graph_usable(const fmm_ctx *c);
+int graph_solve(fmm_ctx *c, double *ax, double *ay, double *az);
+// The stages of a solve after begin_solve (api.cu).
+int run_stages(fmm_ctx *c, double *ax, double *ay, double *az);
 
 }  // namespace amfmm

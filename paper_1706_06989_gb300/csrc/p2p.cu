@@ -665,7 +665,6 @@ int p2p_prepare(fmm_ctx *c) {
     AMFMM_TRY(launched(c, "p2p_bpos"));
     int64_t *ptot = ptr<int64_t>(c->totals) + 12;
     AMFMM_TRY(exclusive_scan_i64(c, len, ptr<int64_t>(c->p2p_poff), K, ptot));
-    AMFMM_CUDA(c, cudaMemcpyAsync(h, ptot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   }
   // column stream per leaf: pre = prefix sums of n_B over the A-sorted pairs
   // (K + 1 entries, so pre[K] is the total)
@@ -693,8 +692,22 @@ int p2p_prepare(fmm_ctx *c) {
   AMFMM_TRY(exclusive_scan_i32(c, icnt, itemOff, nleaf + 1, itot));
   AMFMM_TRY(exclusive_scan_i32(c, ecnt, extraOff, nleaf + 1, etot));
   int32_t *hc = reinterpret_cast<int32_t *>(h + 1);
-  AMFMM_CUDA(c, cudaMemcpyAsync(hc, ctot, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  AMFMM_CUDA(c, cudaStreamSynchronize(st));
+  {
+    // (totals[12], the slot total, is not written after its scan)
+    const int64_t *ptot = ptr<int64_t>(c->totals) + 12;
+    HostRead rb[2];
+    int nr = 0;
+    if (K > 0) rb[nr++] = HostRead{h, ptot, sizeof(int64_t)};
+    rb[nr++] = HostRead{hc, ctot, 3 * sizeof(int32_t)};
+    AMFMM_TRY(read_back(c, rb, nr));
+    if (capturing(c)) {
+      Expect e;
+      if (K > 0) e.add64(ptot, static_cast<uint64_t>(h[0]));
+      for (int k = 0; k < 3; ++k) e.add(ctot + k, static_cast<uint32_t>(hc[k]));
+      AMFMM_TRY(graph_expect(c, e));
+      st = c->stream;
+    }
+  }
   const int64_t nslot = h[0], ncol = hc[0];
   const int64_t nitem = hc[1], nextra = hc[2];
   // the slots are addressed with int32 offsets: refuse before anything is

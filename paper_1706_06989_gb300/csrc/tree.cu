@@ -705,8 +705,16 @@ int build_tree(fmm_ctx *c) {
                                                              ptr<int32_t>(c->parent), ptr<int32_t>(c->nchild), ovf);
         AMFMM_TRY(launched(c, "cell_counts"));
       }
-      AMFMM_CUDA(c, cudaMemcpyAsync(h, status, sizeof(int) * (8 + kMaxLevel + 3), cudaMemcpyDeviceToHost, st));
-      AMFMM_CUDA(c, cudaStreamSynchronize(st));
+      const HostRead rb{h, status, sizeof(int) * (8 + kMaxLevel + 3)};
+      AMFMM_TRY(read_back(c, &rb, 1));
+      if (capturing(c)) {
+        // a captured solve keeps the planned cell room
+        if (h[1]) return set_error(c, FMM_ECUDA, "graph capture: the planning solve grew the cell room");
+        Expect e;
+        for (int k = 0; k < 8 + kMaxLevel + 3; ++k) e.add(status + k, static_cast<uint32_t>(h[k]));
+        AMFMM_TRY(graph_expect(c, e));
+        st = c->stream;
+      }
       const int32_t *hl = h + 8;
       if (h[1]) {  // out of cell room: grow beyond what the levels so far asked for
         int64_t need = cap;
@@ -748,12 +756,18 @@ int build_tree(fmm_ctx *c) {
   AMFMM_TRY(launched(c, "leaf_compact"));
   {
     int32_t *h = static_cast<int32_t *>(c->hpin);
-    AMFMM_CUDA(c, cudaMemcpyAsync(h, total, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    AMFMM_CUDA(c, cudaMemcpyAsync(h + 1, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     double *hb = reinterpret_cast<double *>(h + 4);
-    AMFMM_CUDA(c, cudaMemcpyAsync(hb, c->sz.nsys == 1 ? c->bbox.p : c->sbox.p, 4 * sizeof(double),
-                                  cudaMemcpyDeviceToHost, st));
-    AMFMM_CUDA(c, cudaStreamSynchronize(st));
+    const double *bbox = c->sz.nsys == 1 ? ptr<double>(c->bbox) : ptr<double>(c->sbox);
+    const HostRead rb[3] = {{h, total, sizeof(int32_t)}, {h + 1, status, sizeof(int32_t)},
+                            {hb, bbox, 4 * sizeof(double)}};
+    AMFMM_TRY(read_back(c, rb, 3));
+    if (capturing(c)) {
+      AMFMM_TRY(graph_record_bbox(c, bbox));
+      Expect e;
+      e.add(total, static_cast<uint32_t>(h[0]));
+      e.add(status, static_cast<uint32_t>(h[1]));
+      AMFMM_TRY(graph_expect(c, e));
+    }
     c->sz.nleaf = h[0];
     for (int d = 0; d < 3; ++d) c->sz.lo[d] = hb[d];
     c->sz.scale = hb[3];

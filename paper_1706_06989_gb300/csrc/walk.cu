@@ -360,9 +360,11 @@ __global__ void __launch_bounds__(kGenBlock, kGenBlocksPerSM) k_walk_gen(
   }
 }
 
-__global__ void k_roots_front(int32_t nsys, int2 *__restrict__ front) {
+// one self pair per root, and the first generation's inputs
+__global__ void k_roots_front(int32_t nsys, int2 *__restrict__ front, GenState *__restrict__ gs) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < nsys) front[s] = make_int2(s, s);
+  if (s == 0) gs[0].in = GenIn{nsys, 0, 0, 0};
 }
 
 }  // namespace
@@ -410,8 +412,6 @@ int walk(fmm_ctx *c) {
   // one self pair per root: systems of a forest never interact
   const int64_t nsys = c->sz.nsys;
   if (nsys > static_cast<int64_t>(c->front[0].cap / sizeof(int2))) AMFMM_TRY(ensure<int2>(c, c->front[0], nsys));
-  k_roots_front<<<grid_for(nsys, kBlock), kBlock, 0, st>>>(static_cast<int32_t>(nsys), ptr<int2>(c->front[0]));
-  AMFMM_TRY(launched(c, "walk_roots"));
   // The walk lasts at most 2 depth + 1 generations with pairs (a generation
   // raises the sum of the two cells' levels by one, or by two for a pair of
   // a cell with itself); one more finds the frontier empty.
@@ -423,9 +423,8 @@ int walk(fmm_ctx *c) {
   const unsigned grid = static_cast<unsigned>(std::max(1, c->num_sms * kGenBlocksPerSM));
   // generation records: zero, then the first generation's inputs (the roots)
   AMFMM_CUDA(c, cudaMemsetAsync(gs, 0, sizeof(GenState) * (ngen + 1), st));
-  GenIn *hin = reinterpret_cast<GenIn *>(static_cast<char *>(c->hpin) + 8192);
-  *hin = GenIn{nsys, 0, 0, 0};
-  AMFMM_CUDA(c, cudaMemcpyAsync(&gs[0].in, hin, sizeof(GenIn), cudaMemcpyHostToDevice, st));
+  k_roots_front<<<grid_for(nsys, kBlock), kBlock, 0, st>>>(static_cast<int32_t>(nsys), ptr<int2>(c->front[0]), gs);
+  AMFMM_TRY(launched(c, "walk_roots"));
   int gstart = 0;  // first generation to (re)run
   for (int attempt = 0;; ++attempt) {
     if (attempt > 16) return set_error(c, FMM_EINVAL, "walk: outputs still overflow after growing the buffers");
@@ -446,6 +445,9 @@ int walk(fmm_ctx *c) {
     int4 *agg = static_cast<int4 *>(c->walk_lb.p);
     int4 *inc = agg + nbc;
     int *flg = reinterpret_cast<int *>(inc + nbc);
+    // A replayed graph repeats the epochs it was captured with: clear the
+    // look-back records so that no flag of an earlier replay matches.
+    if (capturing(c)) AMFMM_CUDA(c, cudaMemsetAsync(c->walk_lb.p, 0, c->walk_lb.cap, st));
     const unsigned epoch0 = c->walk_epoch + 1;
     c->walk_epoch = (c->walk_epoch + ngen + 1) & 0x3fffffffu;
     if (c->walk_epoch < epoch0) c->walk_epoch = ngen + 1;  // wrapped: restart above zero
@@ -466,12 +468,25 @@ int walk(fmm_ctx *c) {
       AMFMM_TRY(launched(c, "walk_gen"));
     }
     GenState *h = static_cast<GenState *>(c->hpin);
-    AMFMM_CUDA(c, cudaMemcpyAsync(h, gs, sizeof(GenState) * (ngen + 1), cudaMemcpyDeviceToHost, st));
-    AMFMM_CUDA(c, cudaStreamSynchronize(st));
+    const HostRead rb{h, gs, sizeof(GenState) * (ngen + 1)};
+    AMFMM_TRY(read_back(c, &rb, 1));
     int first_bad = -1;
     for (int g = gstart; g < ngen; ++g) {
       if (h[g].status & 2) return set_error(c, FMM_ETIMEOUT, "walk: a block waited too long for its predecessor");
       if ((h[g].status & 5) && first_bad < 0) first_bad = g;
+    }
+    if (capturing(c)) {
+      // a captured walk keeps the planned buffers: the plan's walk fitted
+      if (first_bad >= 0 || gstart != 0) return set_error(c, FMM_ECUDA, "graph capture: the planning walk grew its buffers");
+      Expect e;
+      for (int g = 0; g < ngen; ++g) e.add(&gs[g].status, static_cast<uint32_t>(h[g].status));
+      e.add64(&gs[ngen].in.nf, static_cast<uint64_t>(h[ngen].in.nf));
+      e.add64(&gs[ngen].in.m2l, static_cast<uint64_t>(h[ngen].in.m2l));
+      e.add64(&gs[ngen].in.p2p, static_cast<uint64_t>(h[ngen].in.p2p));
+      if (!e.add64(&gs[ngen].in.self, static_cast<uint64_t>(h[ngen].in.self)))
+        return set_error(c, FMM_ECUDA, "graph capture: too many walk generations to check");
+      AMFMM_TRY(graph_expect(c, e));
+      st = c->stream;
     }
     if (first_bad < 0) {
       if (h[ngen].in.nf != 0) return set_error(c, FMM_EINVAL, "walk: more generations than the depth allows");

@@ -66,6 +66,8 @@ def load() -> ctypes.CDLL:
                 "fmm_set_timing": [P, I],
                 "fmm_set_softening": [P, D],
                 "fmm_set_tile": [P, I],
+                "fmm_set_graph": [P, I],
+                "fmm_graph_stats": [P, P],
                 "fmm_autotune": [P, P, P, P, P, P, I, P, I, P, I, I, P, P, P, P, P, P],
                 "fmm_build_tree": [P, P, P, P, P, I64, D],
                 "fmm_upward": [P],
@@ -101,6 +103,8 @@ def load() -> ctypes.CDLL:
             lib.fmm_alu_peak.restype = I
             lib.fmm_selector_nparams.argtypes = []
             lib.fmm_selector_nparams.restype = I
+            lib.fmm_graph_error.argtypes = [P]
+            lib.fmm_graph_error.restype = ctypes.c_char_p
             lib.fmm_destroy.argtypes = [P]
             lib.fmm_destroy.restype = None
             lib.fmm_last_error.argtypes = [P]
@@ -206,6 +210,17 @@ class FMM:
 
     def set_timing(self, on: bool = True):
         self._check(self.lib.fmm_set_timing(self._h, int(bool(on))), "fmm_set_timing")
+
+    def set_graph(self, on: bool = True):
+        """Solves as one CUDA-graph launch (captured on the first solve of a
+        configuration, replayed while the sizes stay the same)."""
+        self._check(self.lib.fmm_set_graph(self._h, int(bool(on))), "fmm_set_graph")
+
+    def graph_stats(self) -> dict:
+        out = (ctypes.c_int64 * 5)()
+        self._check(self.lib.fmm_graph_stats(self._h, ctypes.cast(out, ctypes.c_void_p)), "fmm_graph_stats")
+        return dict(replays=out[0], captures=out[1], fallbacks=out[2], capture_failures=out[3], kernels=out[4],
+                    error=self.lib.fmm_graph_error(self._h).decode())
 
     # ---- stages ------------------------------------------------------------
     def _as_dev(self, a):
