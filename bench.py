@@ -70,6 +70,7 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-other", action="store_true", help="skip timing the other precision form")
+    p.add_argument("--no-graph", action="store_true", help="skip timing the graph-captured solve")
     p.add_argument("--no-targets", action="store_true",
                    help="skip the 4M-body comparison of the FP64 and mixed forms")
     p.add_argument("--experiment", choices=["none", "leapfrog", "ensemble", "selector", "orders", "sweep",
@@ -352,6 +353,56 @@ def run_ours(a):
         e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * a.n,
                "d2h_bytes_per_step": 3 * 8 * a.n, "ms_per_step": 1e3 * etot / a.steps}
 
+    # the same solves as one CUDA-graph launch each (fmm_set_graph: captured
+    # on the first solve, replayed after), same timing rules; device-resident
+    # and through the host-buffer entry point
+    graph = None
+    if not a.no_graph and a.order_p == 3:
+        sg = fmm.FMM(theta=a.theta, n_crit=a.n_crit, variant=a.variant, precision=a.precision, stream=stream)
+        sg.set_graph(True)
+        outg = tuple(torch.empty(a.n, dtype=torch.float64, device=dev) for _ in range(3))
+        for _ in range(max(3, a.warmup)):
+            sg.solve(x, y, z, m, outg)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        evg = []
+        for k in range(a.steps):
+            flush.fill_(k & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sg.solve(x, y, z, m, outg)
+            e1.record(stream)
+            evg.append((e0, e1))
+        torch.cuda.synchronize()
+        tgs = [e0.elapsed_time(e1) for e0, e1 in evg]
+        gval, gtot = job_throughput(sum(tgs) / 1e3, a.n, a.steps, ws, dev)
+        same = bool(torch.equal(torch.stack(outg), torch.stack(out)))
+        graph = {"value": gval, "unit": UNIT, "ms_per_step": 1e3 * gtot / a.steps,
+                 "bit_identical_to_plain": same}
+        if not a.no_e2e:
+            hb = [torch.from_numpy(v).pin_memory() for v in (b.x, b.y, b.z, b.m)]
+            ho = [torch.empty(a.n, dtype=torch.float64).pin_memory() for _ in range(3)]
+            for _ in range(3):
+                sg.solve_host(*hb, out=ho)
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            es = []
+            for k in range(a.steps):
+                flush.fill_(k & 0xff)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sg.solve_host(*hb, out=ho)
+                es.append(time.perf_counter() - t0)
+            ev_, etot_ = job_throughput(sum(es), a.n, a.steps, ws, dev)
+            graph["e2e"] = {"value": ev_, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * a.n,
+                            "d2h_bytes_per_step": 3 * 8 * a.n, "ms_per_step": 1e3 * etot_ / a.steps}
+        gs = sg.graph_stats()
+        graph.update({"kernels_per_launch": gs["kernels"], "replays": gs["replays"], "captures": gs["captures"],
+                      "fallbacks": gs["fallbacks"]})
+        sg.close()
+
     # accuracy of this solve: rms relative force error against exact direct
     # summation on 4096 bodies (seed 1), and the Sec. 3 balance metric
     tg = ics.error_subset(a.n, 4096, seed=1)
@@ -420,7 +471,7 @@ def run_ours(a):
                            "l2": "flushed (256 MiB write between timed steps)",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "accuracy": accuracy,
-                "other_form": other, "targets": targets,
+                "other_form": other, "targets": targets, "graph": graph,
                 "gpu_launches": int(st.launches) * a.steps, "clocks": clocks,
                 "counts": {"ncell": st.ncell, "nleaf": st.nleaf, "depth": st.depth, "n_m2l": st.n_m2l,
                            "n_p2p": st.n_p2p, "p2p_body_pairs": st.p2p_body_pairs},
@@ -463,6 +514,12 @@ def run_targets(a, flush, n: int = 4194304) -> dict:
         ms = _time_solves(s, x, y, z, m, out, flush, reps=3)
         key = prec + ("_selector" if p is not None else "")
         res[key] = {"ms": ms, "bodies_per_s": n / (ms / 1e3), "rms_force_err": _rms_err(s, x, y, z, m, out, tg, ref)}
+        if p is None:  # the same form as one graph launch (the selector runs plainly)
+            s.set_graph(True)
+            for _ in range(2):
+                s.solve(x, y, z, m, out)
+            res[key]["graph_ms"] = _time_solves(s, x, y, z, m, out, flush, reps=3)
+            res[key]["graph_replays"] = s.graph_stats()["replays"]
         s.close()
     for k in res:
         if k != "fp64":
@@ -568,6 +625,23 @@ def run_ensemble(a):
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
     batched_ms = statistics.mean(ts)
+    # the same forest solve as one CUDA-graph launch (captured on the first
+    # solve, replayed after), same timing rules
+    s.set_graph(True)
+    for _ in range(3):
+        s.solve_batch(x, y, z, m, off, out)
+    tg_ = []
+    for k in range(a.steps):
+        flush.fill_(k & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.solve_batch(x, y, z, m, off, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tg_.append(e0.elapsed_time(e1))
+    graph_ms = statistics.mean(tg_)
+    gstats = s.graph_stats()
+    s.set_graph(False)
     # one solve per system (the same n_crit), same timing rules
     views = [tuple(v[int(off[k]):int(off[k + 1])] for v in (x, y, z, m)) for k in range(len(off) - 1)]
     for v in views[:8]:
@@ -588,8 +662,11 @@ def run_ensemble(a):
                       "n_total": n, "precision": prec, "variant": a.variant, "theta": a.theta,
                       "autotune_ms": tune, "n_crit": best, "tile": tile,
                       "batched": {"ms": batched_ms, "bodies_per_s": n / (batched_ms / 1e3)},
+                      "batched_graph": {"ms": graph_ms, "bodies_per_s": n / (graph_ms / 1e3),
+                                        "kernels_per_launch": gstats["kernels"], "replays": gstats["replays"],
+                                        "captures": gstats["captures"], "fallbacks": gstats["fallbacks"]},
                       "one_solve_per_system": {"ms": loop_ms, "bodies_per_s": n / (loop_ms / 1e3)},
-                      "speedup": loop_ms / batched_ms}), flush=True)
+                      "speedup": loop_ms / batched_ms, "speedup_graph": loop_ms / graph_ms}), flush=True)
 
 
 def _rms_err(solver, x, y, z, m, out, tg_dev, ref):
