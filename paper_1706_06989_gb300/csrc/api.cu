@@ -160,7 +160,7 @@ void fmm_destroy(fmm_ctx *c) {
                  &c->first_child, &c->nchild, &c->S, &c->M, &c->Z, &c->invM, &c->Rmax, &c->rmax2, &c->mom,
                  &c->loc, &c->leaves, &c->front[0], &c->front[1],
                  &c->m2l, &c->p2p, &c->self_list, &c->walk_zr, &c->walk_zf, &c->walk_nl, &c->walk_state, &c->walk_lb, &c->ekey[0], &c->ekey[1], &c->eval[0], &c->eval[1],
-                 &c->m2l_pos, &c->m2l_off, &c->m2l_slots, &c->cell32, &c->ohat, &c->pkey[0], &c->pkey[1], &c->pval[0],
+                 &c->m2l_pos, &c->m2l_off, &c->m2l_slots, &c->cell32, &c->qoh, &c->pkey[0], &c->pkey[1], &c->pval[0],
                  &c->pval[1], &c->p2p_A, &c->p2p_offA, &c->p2p_offB, &c->p2p_pos, &c->p2p_poff,
                  &c->p2p_len, &c->p2p_slots, &c->p2p_colOff, &c->p2p_cols, &c->p2p_nb, &c->p2p_pre, &c->p2p_bodyf, &c->p2p_items, &c->p2p_itemOff, &c->p2p_extraOff, &c->p2p_extra, &c->scan_tmp, &c->sort_hist, &c->totals, &c->diag, &c->sel_params, &c->sel_cellfeat, &c->sel_cand, &c->sel_lga, &c->sel_scratch, &c->sel_part, &c->sel_score, &c->sel_grad, &c->sel_perm, &c->sel_xb, &c->sel_yb, &c->gen_tab, &c->hx, &c->hy,
                  &c->hz, &c->hm, &c->hax, &c->hay, &c->haz};

@@ -140,7 +140,7 @@ struct fmm_ctx {
   int last_depth = 0;        // depth of the previous tree: levels of the first batch of the next build
   unsigned walk_epoch = 0;  // epochs of the single-pass walk generations
   // M2L scatter
-  amfmm::DBuf ekey[2], eval[2], m2l_pos, m2l_off, m2l_slots, cell32, ohat;
+  amfmm::DBuf ekey[2], eval[2], m2l_pos, m2l_off, m2l_slots, cell32, qoh;
   // P2P grouping
   amfmm::DBuf pkey[2], pval[2], p2p_A, p2p_offA, p2p_offB, p2p_pos, p2p_poff, p2p_len,
       p2p_slots, p2p_colOff, p2p_cols, p2p_nb, p2p_pre, p2p_bodyf, p2p_items, p2p_itemOff, p2p_extraOff,

@@ -44,6 +44,7 @@ namespace {
 
 constexpr int kBlock = 128;
 constexpr int kCell32 = 24;  // floats per cell in the mixed form's copy
+constexpr int kQOh = 16;     // doubles per cell of the FP64 form's quadrupole and octupole per mass
 
 __device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
 __device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
@@ -71,7 +72,17 @@ __device__ __forceinline__ float min_r2<float>() { return 1e-30f; }
 // F / M_B = M_A (F / (M_A M_B)), so the pair needs 10 subtractions for S and
 // no divisions.  (The FP64 form runs at the FP64 pipe's rate: every
 // operation per pair counts.)
-template <class T, int VARIANT>
+//
+// HARM: the unsoftened 1/R is harmonic away from R = 0, so every D tensor is
+// trace-free in any two indices and its contraction with the trace part of a
+// moment vanishes.  With HARM the caller passes trace-free quadrupoles
+// (Q - tr Q / 3 I), which drops the trace term of h, and for TC trace-free
+// octupoles per unit mass (t = 0 for their difference), which drops every
+// t term of the correction: F = R^-5 [7.5 u - 17.5 n (n.u)].  Same sums up
+// to rounding, about 24 fewer FP64 operations per pair.  (Softened
+// derivatives are not trace-free, and TCO's correction is not a contraction
+// with the full D: both keep the raw moments.)
+template <class T, int VARIANT, bool HARM = false>
 __device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, const T *QA, const T *QB, const T *OhA,
                                          const T *OhB, T eps2, T *CA, T *CB) {
   const T r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
@@ -96,13 +107,15 @@ __device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, const T *QA, 
   const T Ri4 = Ri2 * Ri2;
   // h = Q_jk D_ijk / 2 = R^-4 [n_i (15 n.Q.n - 3 trQ) - 6 (Q n)_i] / 2
   const T v = T(-3) * Ri4;
+  const T c75 = T(7.5) * Ri4;
   T hA[3], hB[3];
   {
     const T *Q = QB;
     const T qx = Q[0] * x + Q[1] * y + Q[2] * z;
     const T qy = Q[1] * x + Q[3] * y + Q[4] * z;
     const T qz = Q[2] * x + Q[4] * y + Q[5] * z;
-    const T w = (T(7.5) * (x * qx + y * qy + z * qz) - T(1.5) * (Q[0] + Q[3] + Q[5])) * Ri4;
+    const T w = HARM ? c75 * (x * qx + y * qy + z * qz)
+                     : (T(7.5) * (x * qx + y * qy + z * qz) - T(1.5) * (Q[0] + Q[3] + Q[5])) * Ri4;
     hB[0] = w * x + v * qx;
     hB[1] = w * y + v * qy;
     hB[2] = w * z + v * qz;
@@ -112,7 +125,8 @@ __device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, const T *QA, 
     const T qx = Q[0] * x + Q[1] * y + Q[2] * z;
     const T qy = Q[1] * x + Q[3] * y + Q[4] * z;
     const T qz = Q[2] * x + Q[4] * y + Q[5] * z;
-    const T w = (T(7.5) * (x * qx + y * qy + z * qz) - T(1.5) * (Q[0] + Q[3] + Q[5])) * Ri4;
+    const T w = HARM ? c75 * (x * qx + y * qy + z * qz)
+                     : (T(7.5) * (x * qx + y * qy + z * qz) - T(1.5) * (Q[0] + Q[3] + Q[5])) * Ri4;
     hA[0] = w * x + v * qx;
     hA[1] = w * y + v * qy;
     hA[2] = w * z + v * qz;
@@ -133,7 +147,26 @@ __device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, const T *QA, 
     CA[9 + k] = MB4 * U3[k];
     CB[9 + k] = -(MA4 * U3[k]);
   }
-  if (VARIANT != FMM_UC) {
+  if (VARIANT == FMM_TC && HARM) {
+    // trace-free Sh: F = 7.5 R^-5 [u + (-7/3) n (n.u)], the 7.5 R^-5 folded
+    // into the scale factors
+    T S[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) S[k] = OhB[k] - OhA[k];
+    const T xy2 = T(2) * xy, xz2 = T(2) * xz, yz2 = T(2) * yz;
+    const T ux = S[0] * xx + S[3] * yy + S[5] * zz + S[1] * xy2 + S[2] * xz2 + S[4] * yz2;
+    const T uy = S[1] * xx + S[6] * yy + S[8] * zz + S[3] * xy2 + S[4] * xz2 + S[7] * yz2;
+    const T uz = S[2] * xx + S[7] * yy + S[9] * zz + S[4] * xy2 + S[5] * xz2 + S[8] * yz2;
+    const T w = T(-7.0 / 3.0) * (x * ux + y * uy + z * uz);
+    const T F[3] = {ux + w * x, uy + w * y, uz + w * z};
+    const T c5 = c75 * Ri;
+    const T sA = MB * c5, sB = MA * c5;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      CA[i] -= F[i] * sA;
+      CB[i] += F[i] * sB;
+    }
+  } else if (VARIANT != FMM_UC) {
     // Sh = Oh_B - Oh_A = S / (M_A M_B) (xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)
     T S[10];
 #pragma unroll
@@ -167,12 +200,13 @@ __device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, const T *QA, 
 
 // One thread per accepted pair.  Slots are kLocStride wide (19 used).
 // FP64 form: reads the FP64 cell data.
-template <int VARIANT>
+// qoh: per cell the quadrupole (6) and the octupole per unit mass (10) the
+// pair function takes, trace-free where HARM allows (k_qoh).
+template <int VARIANT, bool HARM>
 __global__ void __launch_bounds__(kBlock) k_m2l64(int64_t K, const int2 *__restrict__ pairs,
                                                    const double *__restrict__ Z,
                                                    const double *__restrict__ M,
-                                                   const double *__restrict__ ohat,
-                                                   const double *__restrict__ mom,
+                                                   const double *__restrict__ qoh,
                                                    const int32_t *__restrict__ pos, double eps2,
                                                    double *__restrict__ slots) {
   const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -180,10 +214,9 @@ __global__ void __launch_bounds__(kBlock) k_m2l64(int64_t K, const int2 *__restr
   const int A = pairs[k].x, B = pairs[k].y;
   double CA[kLocStride], CB[kLocStride];
   const double r[3] = {Z[3 * A] - Z[3 * B], Z[3 * A + 1] - Z[3 * B + 1], Z[3 * A + 2] - Z[3 * B + 2]};
-  const double *mA = mom + static_cast<int64_t>(A) * kMomStride;
-  const double *mB = mom + static_cast<int64_t>(B) * kMomStride;
-  m2l_pair<double, VARIANT>(r, M[A], M[B], mA + 4, mB + 4, ohat + 10 * static_cast<int64_t>(A),
-                            ohat + 10 * static_cast<int64_t>(B), eps2, CA, CB);
+  const double *qA = qoh + static_cast<int64_t>(A) * kQOh;
+  const double *qB = qoh + static_cast<int64_t>(B) * kQOh;
+  m2l_pair<double, VARIANT, HARM>(r, M[A], M[B], qA, qB, qA + 6, qB + 6, eps2, CA, CB);
   CA[19] = CB[19] = 0.0;
   double *sa = slots + static_cast<int64_t>(pos[2 * k]) * kLocStride;
   double *sb = slots + static_cast<int64_t>(pos[2 * k + 1]) * kLocStride;
@@ -355,14 +388,45 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_m2l32_gather(int32_t ncel
   }
 }
 
-// octupoles per unit mass, Oh = O / M, for the FP64 order-3 M2L
-__global__ void k_ohat(int32_t ncell, const double *__restrict__ invM, const double *__restrict__ mom,
-                       double *__restrict__ ohat) {
-  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (t >= static_cast<int64_t>(ncell) * 10) return;
-  const int64_t c = t / 10;
-  const int q = static_cast<int>(t - c * 10);
-  ohat[t] = mom[c * kMomStride + 10 + q] * invM[c];
+// Per cell for the FP64 order-3 M2L: the quadrupole Q (6) and the octupole
+// per unit mass Oh = O / M (10; xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz).
+// tf_q: Q - (tr Q / 3) I; tf_o: Oh - (1/5)(d_ij t_k + d_ik t_j + d_jk t_i),
+// t_i = Oh_ijj (both trace-free).
+__global__ void k_qoh(int32_t ncell, const double *__restrict__ invM, const double *__restrict__ mom, int tf_q,
+                      int tf_o, double *__restrict__ qoh) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const double *m = mom + static_cast<int64_t>(c) * kMomStride;
+  double *o = qoh + static_cast<int64_t>(c) * kQOh;
+  double Q[6], O[10];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) Q[q] = m[4 + q];
+  const double im = invM[c];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) O[q] = m[10 + q] * im;
+  if (tf_q) {
+    const double t3 = (Q[0] + Q[3] + Q[5]) / 3.0;
+    Q[0] -= t3;
+    Q[3] -= t3;
+    Q[5] -= t3;
+  }
+  if (tf_o) {
+    const double tx = (O[0] + O[3] + O[5]) * 0.2, ty = (O[1] + O[6] + O[8]) * 0.2,
+                 tz = (O[2] + O[7] + O[9]) * 0.2;
+    O[0] -= 3.0 * tx;
+    O[1] -= ty;
+    O[2] -= tz;
+    O[3] -= tx;
+    O[5] -= tx;
+    O[6] -= 3.0 * ty;
+    O[7] -= tz;
+    O[8] -= ty;
+    O[9] -= 3.0 * tz;
+  }
+#pragma unroll
+  for (int q = 0; q < 6; ++q) o[q] = Q[q];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) o[6 + q] = O[q];
 }
 
 // FP32 copy of the cell data for the mixed form
@@ -513,15 +577,26 @@ __global__ void __launch_bounds__(kRedWarps * 32) k_m2l_reduce(int32_t ncell, co
 int launch_m2l64(fmm_ctx *c, int64_t K) {
   const int2 *pairs = ptr<int2>(c->m2l);
   const unsigned g = grid_for(K, kBlock);
-  const double *Z = ptr<double>(c->Z), *M = ptr<double>(c->M), *oh = ptr<double>(c->ohat),
-               *mom = ptr<double>(c->mom);
+  const double *Z = ptr<double>(c->Z), *M = ptr<double>(c->M), *qoh = ptr<double>(c->qoh);
   const int32_t *pos = ptr<int32_t>(c->m2l_pos);
   double *slots = ptr<double>(c->m2l_slots);
   cudaStream_t st = c->stream;
+  const double e2 = c->eps2;
+  // the trace-free forms hold for the unsoftened 1/R (k_qoh wrote them)
+  const bool harm = e2 == 0.0;
   switch (c->opts.variant) {
-    case FMM_UC: k_m2l64<FMM_UC><<<g, kBlock, 0, st>>>(K, pairs, Z, M, oh, mom, pos, c->eps2, slots); break;
-    case FMM_TC: k_m2l64<FMM_TC><<<g, kBlock, 0, st>>>(K, pairs, Z, M, oh, mom, pos, c->eps2, slots); break;
-    default: k_m2l64<FMM_TCO><<<g, kBlock, 0, st>>>(K, pairs, Z, M, oh, mom, pos, c->eps2, slots); break;
+    case FMM_UC:
+      if (harm) k_m2l64<FMM_UC, true><<<g, kBlock, 0, st>>>(K, pairs, Z, M, qoh, pos, e2, slots);
+      else k_m2l64<FMM_UC, false><<<g, kBlock, 0, st>>>(K, pairs, Z, M, qoh, pos, e2, slots);
+      break;
+    case FMM_TC:
+      if (harm) k_m2l64<FMM_TC, true><<<g, kBlock, 0, st>>>(K, pairs, Z, M, qoh, pos, e2, slots);
+      else k_m2l64<FMM_TC, false><<<g, kBlock, 0, st>>>(K, pairs, Z, M, qoh, pos, e2, slots);
+      break;
+    default:
+      if (harm) k_m2l64<FMM_TCO, true><<<g, kBlock, 0, st>>>(K, pairs, Z, M, qoh, pos, e2, slots);
+      else k_m2l64<FMM_TCO, false><<<g, kBlock, 0, st>>>(K, pairs, Z, M, qoh, pos, e2, slots);
+      break;
   }
   return launched(c, "m2l");
 }
@@ -589,11 +664,12 @@ int m2l_prepare(fmm_ctx *c) {
     k_cell32<<<grid_for(nc, 256), 256, 0, st>>>(static_cast<int32_t>(nc), ptr<double>(c->Z), ptr<double>(c->M),
                                                 ptr<double>(c->invM), ptr<double>(c->mom), ptr<float>(c->cell32));
     AMFMM_TRY(launched(c, "cell32"));
-  } else if (c->opts.order_P == 3 && c->opts.variant != FMM_UC) {
-    AMFMM_TRY(ensure<double>(c, c->ohat, static_cast<size_t>(10) * nc));
-    k_ohat<<<grid_for(nc * 10, 256), 256, 0, st>>>(static_cast<int32_t>(nc), ptr<double>(c->invM),
-                                                   ptr<double>(c->mom), ptr<double>(c->ohat));
-    AMFMM_TRY(launched(c, "ohat"));
+  } else if (c->opts.order_P == 3) {
+    AMFMM_TRY(ensure<double>(c, c->qoh, static_cast<size_t>(kQOh) * nc));
+    const int harm = c->eps2 == 0.0;
+    k_qoh<<<grid_for(nc, 128), 128, 0, st>>>(static_cast<int32_t>(nc), ptr<double>(c->invM), ptr<double>(c->mom),
+                                             harm, harm && c->opts.variant == FMM_TC, ptr<double>(c->qoh));
+    AMFMM_TRY(launched(c, "qoh"));
   }
   return FMM_OK;
 }
