@@ -43,7 +43,8 @@ namespace amfmm {
 namespace {
 
 constexpr int kBlock = 128;
-constexpr int kCell32 = 24;  // floats per cell in the mixed form's copy
+constexpr int kCell32 = 24;    // floats per cell in the mixed form's copy (raw moments)
+constexpr int kCell32TF = 20;  // the same with trace-free moments (unsoftened UC and TC)
 constexpr int kQOh = 16;     // doubles per cell of the FP64 form's quadrupole and octupole per mass
 
 __device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
@@ -296,6 +297,79 @@ __device__ __forceinline__ void m2l_one(const T r[3], T MT, T iMT, T MS, const T
   }
 }
 
+// m2l_one for the unsoftened UC and TC forms, on trace-free moments (see
+// HARM of m2l_pair): QS5 = the source's trace-free quadrupole (xx xy xz yy
+// yz; zz = -xx - yy), OhT and OhS its target's and its own trace-free
+// octupoles per unit mass (xxx xxy xxz xyy xyz yyy yyz; xzz = -xxx - xyy,
+// yzz = -xxy - yyy, zzz = -xxz - yyz).  The correction becomes
+// F = 7.5 R^-5 M_S [u + (-7/3) n (n.u)] of Sh = Oh_S - Oh_T: the target's
+// mass and its inverse drop out.
+template <int VARIANT>
+__device__ __forceinline__ void m2l_one_tf(const float r[3], float MS, const float *QS5, const float *OhT,
+                                           const float *OhS, float *C) {
+  const float r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  if (!(r2 > min_r2<float>())) {
+#pragma unroll
+    for (int q = 0; q < 19; ++q) C[q] = 0.f;
+    return;
+  }
+  const float Ri = rsqrtf(r2);
+  const float x = r[0] * Ri, y = r[1] * Ri, z = r[2] * Ri;
+  const float xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+  const float fxx = 15.f * xx, fyy = 15.f * yy, fzz = 15.f * zz;
+  const float M2 = MS * Ri * Ri, M3 = M2 * Ri, M4 = M3 * Ri;
+  const float Ri2 = Ri * Ri;
+  const float Ri4 = Ri2 * Ri2;
+  const float Q[6] = {QS5[0], QS5[1], QS5[2], QS5[3], QS5[4], -(QS5[0] + QS5[3])};
+  const float qx = Q[0] * x + Q[1] * y + Q[2] * z;
+  const float qy = Q[1] * x + Q[3] * y + Q[4] * z;
+  const float qz = Q[2] * x + Q[4] * y + Q[5] * z;
+  const float c75 = 7.5f * Ri4;
+  const float w = c75 * (x * qx + y * qy + z * qz);
+  const float v = -3.f * Ri4;
+  C[0] = M2 * x + (w * x + v * qx);
+  C[1] = M2 * y + (w * y + v * qy);
+  C[2] = M2 * z + (w * z + v * qz);
+  C[3] = M3 * (1.f - 3.f * xx);
+  C[4] = M3 * (-3.f * xy);
+  C[5] = M3 * (-3.f * xz);
+  C[6] = M3 * (1.f - 3.f * yy);
+  C[7] = M3 * (-3.f * yz);
+  C[8] = M3 * (1.f - 3.f * zz);
+  C[9] = M4 * ((fxx - 9.f) * x);
+  C[10] = M4 * ((fxx - 3.f) * y);
+  C[11] = M4 * ((fxx - 3.f) * z);
+  C[12] = M4 * ((fyy - 3.f) * x);
+  C[13] = M4 * (15.f * xy * z);
+  C[14] = M4 * ((fzz - 3.f) * x);
+  C[15] = M4 * ((fyy - 9.f) * y);
+  C[16] = M4 * ((fyy - 3.f) * z);
+  C[17] = M4 * ((fzz - 3.f) * y);
+  C[18] = M4 * ((fzz - 9.f) * z);
+  if (VARIANT == FMM_TC) {
+    // Sh in the order xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
+    float S[10];
+    S[0] = OhS[0] - OhT[0];
+    S[1] = OhS[1] - OhT[1];
+    S[2] = OhS[2] - OhT[2];
+    S[3] = OhS[3] - OhT[3];
+    S[4] = OhS[4] - OhT[4];
+    S[6] = OhS[5] - OhT[5];
+    S[7] = OhS[6] - OhT[6];
+    S[5] = -(S[0] + S[3]);
+    S[8] = -(S[1] + S[6]);
+    S[9] = -(S[2] + S[7]);
+    const float ux = S[0] * xx + S[3] * yy + S[5] * zz + 2.f * (S[1] * xy + S[2] * xz + S[4] * yz);
+    const float uy = S[1] * xx + S[6] * yy + S[8] * zz + 2.f * (S[3] * xy + S[4] * xz + S[7] * yz);
+    const float uz = S[2] * xx + S[7] * yy + S[9] * zz + 2.f * (S[4] * xy + S[5] * xz + S[8] * yz);
+    const float g = (-7.f / 3.f) * (x * ux + y * uy + z * uz);
+    const float s5 = c75 * Ri * MS;
+    C[0] -= (ux + g * x) * s5;
+    C[1] -= (uy + g * y) * s5;
+    C[2] -= (uz + g * z) * s5;
+  }
+}
+
 // Mixed form, gathered: one warp per cell T, its lanes over T's partners in
 // the stably sorted order of the list.  Every lane keeps FP32 sums of the
 // partners it visits, compensated (Kahan) for C_i.  The 32 lane sums of a coefficient
@@ -311,7 +385,9 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-template <int VARIANT>
+// TF: records of kCell32TF floats with trace-free moments (m2l_one_tf),
+// else kCell32 floats with the raw ones.
+template <int VARIANT, bool TF>
 __global__ void __launch_bounds__(kGatherWarps * 32) k_m2l32_gather(int32_t ncell, const int32_t *__restrict__ off,
                                                                     const uint32_t *__restrict__ partner,
                                                                     const float *__restrict__ cell32,
@@ -330,27 +406,31 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_m2l32_gather(int32_t ncel
   if (lane == 0) c = atomicAdd(queue, 1);
   c = __shfl_sync(0xffffffffu, c, 0);
   if (c >= ncell) break;
-  const float *t = cell32 + static_cast<int64_t>(c) * kCell32;
+  constexpr int kRec = TF ? kCell32TF : kCell32;
+  // float4 loads of a partner record: the UC form needs no octupole
+  constexpr int kLoads = TF ? (VARIANT == FMM_UC ? 3 : kCell32TF / 4) : kCell32 / 4;
+  const float *t = cell32 + static_cast<int64_t>(c) * kRec;
   const float thx = t[0], thy = t[1], thz = t[2], tlx = t[3], tly = t[4], tlz = t[5];
-  const float MT = t[6], iMT = t[7];
+  const float MT = t[6], iMT = TF ? 0.f : t[7];
   float OT[10];
 #pragma unroll
-  for (int k = 0; k < 10; ++k) OT[k] = VARIANT != FMM_UC ? t[14 + k] : 0.f;
+  for (int k = 0; k < 10; ++k) OT[k] = VARIANT != FMM_UC ? (TF ? (k < 7 ? t[12 + k] : 0.f) : t[14 + k]) : 0.f;
   float sum[19], cmp[19];
 #pragma unroll
   for (int q = 0; q < 19; ++q) sum[q] = cmp[q] = 0.f;
   const int e1 = off[c + 1];
   for (int e = off[c] + lane; e < e1; e += 32) {
-    const float4 *ps = reinterpret_cast<const float4 *>(cell32 + static_cast<int64_t>(partner[e]) * kCell32);
+    const float4 *ps = reinterpret_cast<const float4 *>(cell32 + static_cast<int64_t>(partner[e]) * kRec);
     float b[kCell32];
 #pragma unroll
-    for (int u = 0; u < kCell32 / 4; ++u) {
+    for (int u = 0; u < kLoads; ++u) {
       const float4 vb = ps[u];
       b[4 * u] = vb.x; b[4 * u + 1] = vb.y; b[4 * u + 2] = vb.z; b[4 * u + 3] = vb.w;
     }
     const float r[3] = {(thx - b[0]) + (tlx - b[3]), (thy - b[1]) + (tly - b[4]), (thz - b[2]) + (tlz - b[5])};
     float C[19];
-    m2l_one<float, VARIANT>(r, MT, iMT, b[6], b + 8, OT, b + 14, eps2, C);
+    if constexpr (TF) m2l_one_tf<VARIANT>(r, b[6], b + 7, OT, b + 12, C);
+    else m2l_one<float, VARIANT>(r, MT, iMT, b[6], b + 8, OT, b + 14, eps2, C);
     // compensated sums for the field coefficients C_i, which take the
     // cancellation of contributions from opposite sides; plain FP32 sums for
     // C_ij and C_ijk, which reach the force multiplied by the body's offset
@@ -448,6 +528,45 @@ __global__ void k_cell32(int32_t ncell, const double *__restrict__ Z, const doub
   const double *m = mom + static_cast<int64_t>(c) * kMomStride;
 #pragma unroll
   for (int q = 0; q < 16; ++q) o[8 + q] = static_cast<float>(m[4 + q]);
+}
+
+// The same with trace-free moments, kCell32TF floats: Z hi (3), Z lo (3), M,
+// Q - tr Q / 3 I (xx xy xz yy yz), Oh = O / M less its trace part (xxx xxy
+// xxz xyy xyz yyy yyz), one pad; the traces are removed in FP64.
+__global__ void k_cell32_tf(int32_t ncell, const double *__restrict__ Z, const double *__restrict__ M,
+                            const double *__restrict__ invM, const double *__restrict__ mom,
+                            float *__restrict__ cell32) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  float *o = cell32 + static_cast<int64_t>(c) * kCell32TF;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double z = Z[3 * c + d];
+    const float hi = static_cast<float>(z);
+    o[d] = hi;
+    o[3 + d] = static_cast<float>(z - static_cast<double>(hi));
+  }
+  o[6] = static_cast<float>(M[c]);
+  const double *m = mom + static_cast<int64_t>(c) * kMomStride;
+  const double t3 = (m[4] + m[7] + m[9]) / 3.0;
+  o[7] = static_cast<float>(m[4] - t3);
+  o[8] = static_cast<float>(m[5]);
+  o[9] = static_cast<float>(m[6]);
+  o[10] = static_cast<float>(m[7] - t3);
+  o[11] = static_cast<float>(m[8]);
+  const double im = invM[c];
+  double O[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) O[q] = m[10 + q] * im;
+  const double tx = (O[0] + O[3] + O[5]) * 0.2, ty = (O[1] + O[6] + O[8]) * 0.2, tz = (O[2] + O[7] + O[9]) * 0.2;
+  o[12] = static_cast<float>(O[0] - 3.0 * tx);
+  o[13] = static_cast<float>(O[1] - ty);
+  o[14] = static_cast<float>(O[2] - tz);
+  o[15] = static_cast<float>(O[3] - tx);
+  o[16] = static_cast<float>(O[4]);
+  o[17] = static_cast<float>(O[6] - 3.0 * ty);
+  o[18] = static_cast<float>(O[7] - tz);
+  o[19] = 0.f;
 }
 
 // The two order-3 TC locals of given pairs, [k][side][20] (labels of the
@@ -601,6 +720,10 @@ int launch_m2l64(fmm_ctx *c, int64_t K) {
   return launched(c, "m2l");
 }
 
+// the mixed form's cell records carry trace-free moments when the kernel
+// may use them: unsoftened, and a correction that is a contraction with D
+bool cell32_tf(const fmm_ctx *c) { return c->eps2 == 0.0 && c->opts.variant != FMM_TCO; }
+
 int launch_m2l32_gather(fmm_ctx *c) {
   const int32_t nc = static_cast<int32_t>(c->sz.ncell);
   const int32_t *off = ptr<int32_t>(c->m2l_off);
@@ -610,9 +733,10 @@ int launch_m2l32_gather(fmm_ctx *c) {
   cudaStream_t st = c->stream;
   int *queue = ptr<int32_t>(c->totals) + 41;
   AMFMM_CUDA(c, cudaMemsetAsync(queue, 0, sizeof(int), st));
-  auto kern = c->opts.variant == FMM_UC   ? k_m2l32_gather<FMM_UC>
-              : c->opts.variant == FMM_TC ? k_m2l32_gather<FMM_TC>
-                                          : k_m2l32_gather<FMM_TCO>;
+  const bool tf = cell32_tf(c);
+  auto kern = c->opts.variant == FMM_UC   ? (tf ? k_m2l32_gather<FMM_UC, true> : k_m2l32_gather<FMM_UC, false>)
+              : c->opts.variant == FMM_TC ? (tf ? k_m2l32_gather<FMM_TC, true> : k_m2l32_gather<FMM_TC, false>)
+                                          : k_m2l32_gather<FMM_TCO, false>;
   int per_sm = 0;
   AMFMM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGatherWarps * 32, 0));
   const int64_t resident = static_cast<int64_t>(std::max(1, per_sm)) * std::max(1, c->num_sms);
@@ -661,8 +785,12 @@ int m2l_prepare(fmm_ctx *c) {
   }
   if (fp32) {
     AMFMM_TRY(ensure<float>(c, c->cell32, static_cast<size_t>(kCell32) * nc));
-    k_cell32<<<grid_for(nc, 256), 256, 0, st>>>(static_cast<int32_t>(nc), ptr<double>(c->Z), ptr<double>(c->M),
-                                                ptr<double>(c->invM), ptr<double>(c->mom), ptr<float>(c->cell32));
+    if (cell32_tf(c))
+      k_cell32_tf<<<grid_for(nc, 256), 256, 0, st>>>(static_cast<int32_t>(nc), ptr<double>(c->Z), ptr<double>(c->M),
+                                                     ptr<double>(c->invM), ptr<double>(c->mom), ptr<float>(c->cell32));
+    else
+      k_cell32<<<grid_for(nc, 256), 256, 0, st>>>(static_cast<int32_t>(nc), ptr<double>(c->Z), ptr<double>(c->M),
+                                                  ptr<double>(c->invM), ptr<double>(c->mom), ptr<float>(c->cell32));
     AMFMM_TRY(launched(c, "cell32"));
   } else if (c->opts.order_P == 3) {
     AMFMM_TRY(ensure<double>(c, c->qoh, static_cast<size_t>(kQOh) * nc));
