@@ -41,8 +41,13 @@ SM_MAX_MHZ = 2070.0
 FP64_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 4
 FP32_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 256
 # algorithmic flops (FMA = 2, rsqrt = 1) per unit of work, counted from the
-# kernels' expressions: an accepted M2L pair of each variant, a body pair
-M2L_FLOPS = {"UC": 174, "TC": 295, "TCO": 276}
+# kernels' expressions: an accepted M2L pair of each variant (unsoftened:
+# trace-free quadrupoles, and for TC trace-free octupoles), a body pair
+M2L_FLOPS = {"UC": 162, "TC": 235, "TCO": 238}
+# the selector experiment's measure of interaction work: a fixed weight per
+# accepted pair (the TC pair's flops written with the trace terms) and per
+# body pair, so that its gains compare interaction sets, not kernel versions
+WORK_PER_M2L_PAIR = 295
 # DRAM traffic of the dominant kernel per unit it processes, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of k_p2p<double, 16>
 # on a Plummer sphere of N = 262,144 (theta = 0.5, TC): 116,642,304 B read and
@@ -698,7 +703,7 @@ def _time_solves(solver, x, y, z, m, out, flush, reps=3):
 
 def _work(c):
     """Algorithmic flops of a solve's interactions (M2L TC + P2P)."""
-    return M2L_FLOPS["TC"] * c["n_m2l"] + P2P_FLOPS_PER_BODY_PAIR * c["p2p_body_pairs"]
+    return WORK_PER_M2L_PAIR * c["n_m2l"] + P2P_FLOPS_PER_BODY_PAIR * c["p2p_body_pairs"]
 
 
 def _interp_time_at_error(curve, err, key="ms"):
