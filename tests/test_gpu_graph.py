@@ -162,3 +162,22 @@ def test_leapfrog_with_graph_equals_plain():
             gs = s.graph_stats()
             assert gs["captures"] >= 1 and gs["replays"] + gs["fallbacks"] + gs["captures"] >= 2
     assert np.array_equal(res[0], res[1])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_softened_replay_is_bit_identical(precision):
+    """Softening selects the kernels on raw moments; the captured graph
+    holds them and replays bit-identically."""
+    b = ics.plummer(20000, seed=25)
+    x, y, z, m = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (b.x, b.y, b.z, b.m))
+    p = _solver(theta=0.5, precision=precision)
+    p.set_softening(0.01)
+    ref = _acc(p.solve(x, y, z, m))
+    g = _solver(theta=0.5, precision=precision)
+    g.set_softening(0.01)
+    g.set_graph(True)
+    out = _out(b.n)
+    assert np.array_equal(_acc(g.solve(x, y, z, m, out=out)), ref)
+    assert np.array_equal(_acc(g.solve(x, y, z, m, out=out)), ref)
+    gs = g.graph_stats()
+    assert gs["replays"] == 1 and gs["captures"] == 1

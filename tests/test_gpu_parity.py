@@ -243,11 +243,13 @@ def test_plummer_1m_full_size():
     assert fb <= 1e-13 and tb <= 1e-13
 
 
-@pytest.mark.parametrize("variant", ["TC", "TCO"])
+@pytest.mark.parametrize("variant", ["UC", "TC", "TCO"])
 def test_mixed_precision_against_oracle(variant):
     """Mixed form: FP32 interactions on cell-relative coordinates, FP64 tree,
     moments and accumulation.  rms relative force error against the FP64
-    oracle <= 1e-6; force and torque balance <= 1e-6."""
+    oracle <= 1e-6; force balance <= 1e-6, and the torque balance too where
+    the variant conserves it.  (UC and TC read trace-free cell records, TCO
+    the raw ones.)"""
     b = ics.plummer(65536, seed=0)
     s, got = _solve(b, theta=0.5, variant=variant, precision="mixed")
     o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25)
@@ -258,7 +260,9 @@ def test_mixed_precision_against_oracle(variant):
     rel = _rel_dev(got[t], ref)
     assert np.sqrt(np.mean(rel ** 2)) <= 1e-6, np.sqrt(np.mean(rel ** 2))
     fb, tb = oracle.balance(b.x, b.y, b.z, b.m, got)
-    assert fb <= 1e-6 and tb <= 1e-6, (fb, tb)
+    assert fb <= 1e-6, fb
+    if variant != "UC":
+        assert tb <= 1e-6, tb
 
 
 @pytest.mark.slow
