@@ -85,6 +85,8 @@ def _args():
     p.add_argument("--ics", choices=["plummer", "dwd"], default="plummer",
                    help="sweep inputs: Plummer sphere, or the double white dwarf of Sec. 3")
     p.add_argument("--lf-steps", type=int, default=200)
+    p.add_argument("--lf-eps", type=float, default=0.0,
+                   help="Plummer softening length of the leapfrog experiment (0: the unsoftened 1/R)")
     p.add_argument("--sel-steps", type=int, default=3000)
     p.add_argument("--lf-variants", default="TC:mixed,UC:mixed,TC:fp64")
     return p.parse_args()
@@ -568,6 +570,8 @@ def run_leapfrog(a):
         variant, prec = spec.split(":")
         st = [torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (b.x, b.y, b.z, b.vx, b.vy, b.vz, b.m)]
         s = fmm.FMM(theta=a.theta, n_crit=a.n_crit, variant=variant, precision=prec)
+        if a.lf_eps > 0:
+            s.set_softening(a.lf_eps)
         stream = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -593,7 +597,8 @@ def run_leapfrog(a):
         s.close()
         del st
     print(json.dumps({"experiment": "leapfrog", "workload": f"binary_plummer_n{n}_dt_porb_over_1000",
-                      "theta": a.theta, "n_crit": a.n_crit, "scales": {"sum_m_abs_v": p_scale,
+                      "theta": a.theta, "n_crit": a.n_crit, "softening": a.lf_eps,
+                      "scales": {"sum_m_abs_v": p_scale,
                                                                       "sum_m_abs_xv": l_scale},
                       "results": results}), flush=True)
 
