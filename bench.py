@@ -50,11 +50,11 @@ M2L_FLOPS = {"UC": 162, "TC": 235, "TCO": 238}
 WORK_PER_M2L_PAIR = 295
 # DRAM traffic of the dominant kernel per unit it processes, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of k_p2p<double, 16>
-# on a Plummer sphere of N = 262,144 (theta = 0.5, TC): 116,642,304 B read and
-# 203,638,784 B written for 115,126,406 body pairs.  Scaled by the body pairs
+# on a Plummer sphere of N = 262,144 (theta = 0.5, TC): 116,205,568 B read and
+# 203,413,248 B written for 115,126,406 body pairs.  Scaled by the body pairs
 # of the launch timed (the traffic grows with them: column stream, B-side
 # partial slots and near-field sums are all per pair or per body).
-TRAFFIC_PER_UNIT = {("p2p", "fp64"): (116642304 + 203638784) / 115126406}
+TRAFFIC_PER_UNIT = {("p2p", "fp64"): (116205568 + 203413248) / 115126406}
 P2P_FLOPS_PER_BODY_PAIR = 25
 ORACLE_SAMPLE_N = 131072      # single-core oracle sample (bodies)
 REFERENCE_N = 262144          # bodies per step of the reference arm (all cores)
