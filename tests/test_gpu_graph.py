@@ -181,3 +181,38 @@ def test_softened_replay_is_bit_identical(precision):
     assert np.array_equal(_acc(g.solve(x, y, z, m, out=out)), ref)
     gs = g.graph_stats()
     assert gs["replays"] == 1 and gs["captures"] == 1
+
+
+@pytest.mark.parametrize("case", ["one", "two", "coincident", "forest_with_singletons"])
+def test_degenerate_systems_replay(case):
+    """Solves without accepted pairs or without leaf pairs skip stages and
+    read back less; their graphs replay bit-identically too."""
+    rng = np.random.default_rng(11)
+    off = None
+    if case == "one":
+        p, m = np.zeros((1, 3)), np.ones(1)
+    elif case == "two":
+        p, m = np.array([[0.0, 0.0, 0.0], [1.0, 0.5, -0.25]]), np.array([1.0, 2.0])
+    elif case == "coincident":
+        p, m = np.tile([0.3, -0.2, 0.1], (40, 1)), rng.uniform(0.5, 1.5, 40)
+    else:
+        sizes = [1, 500, 1, 1, 2, 3000, 1]
+        p = np.concatenate([rng.normal(size=(k, 3)) for k in sizes])
+        m = rng.uniform(0.5, 1.5, p.shape[0])
+        off = np.concatenate([[0], np.cumsum(sizes)])
+    b = ics.Bodies(p[:, 0].copy(), p[:, 1].copy(), p[:, 2].copy(), m)
+    x, y, z, mm = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (b.x, b.y, b.z, b.m))
+    plain = _solver(theta=0.5)
+    g = _solver(theta=0.5)
+    g.set_graph(True)
+    out = _out(b.n)
+    if off is None:
+        ref = _acc(plain.solve(x, y, z, mm))
+        runs = [_acc(g.solve(x, y, z, mm, out=out)) for _ in range(3)]
+    else:
+        ref = _acc(plain.solve_batch(x, y, z, mm, off))
+        runs = [_acc(g.solve_batch(x, y, z, mm, off, out=out)) for _ in range(3)]
+    for r in runs:
+        assert np.array_equal(r, ref)
+    gs = g.graph_stats()
+    assert gs["captures"] == 1 and gs["replays"] == 2, gs
