@@ -52,13 +52,53 @@ __device__ __forceinline__ int mi_idx(int a0, int a1, int a2) {
 //   ifact[i] = 1 / a!
 //   uoff[g] .. uoff[g+1]: the terms of U^g, each a coefficient and the
 //   exponents of n packed as px | py << 8 | pz << 16
+//   and per order P (3 .. kTabMaxP) the M2L's work split over a warp's 32
+//   lanes: the derivatives U^g and the local coefficients assigned to lanes
+//   largest first, each to the least loaded lane (their costs differ by an
+//   order of magnitude), and the (a, b) products of the corrective force as
+//   one flat list that the lanes stride through.
+constexpr int kTabMinP = 3;
+constexpr int kTabNP = kTabMaxP - kTabMinP + 1;
 struct TabHost {
   std::vector<int4> expo;
   std::vector<double> ifact;
   std::vector<int> uoff;
   std::vector<double> ucoef;
   std::vector<int> uexp;
+  std::vector<int> u_lane, l_lane;  // [P - kTabMinP][33]: lane ranges in u_items / l_items
+  std::vector<int> u_items, l_items;
+  std::vector<int> c_off;            // [P - kTabMinP + 1]: ranges in c_pairs
+  std::vector<int2> c_pairs;         // (ia | ib << 16, U index of a + b + e_x | e_y << 8 | e_z << 16)
 };
+
+int mi_idx_host(int a0, int a1, int a2) {
+  const int n = a0 + a1 + a2, s = a1 + a2;
+  return n * (n + 1) * (n + 2) / 6 + s * (s + 1) / 2 + a2;
+}
+
+// items 0 .. n-1 with costs w, assigned largest first to the least loaded of
+// 32 lanes (ties: lower item, lower lane); per lane in increasing item order
+void lane_split(const std::vector<int> &w, std::vector<int> &lane_ranges, std::vector<int> &items) {
+  const int n = static_cast<int>(w.size());
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return w[a] > w[b]; });
+  std::vector<long long> load(32, 0);
+  std::vector<std::vector<int>> per(32);
+  for (int i : order) {
+    int best = 0;
+    for (int l = 1; l < 32; ++l)
+      if (load[l] < load[best]) best = l;
+    load[best] += w[i];
+    per[best].push_back(i);
+  }
+  for (int l = 0; l < 32; ++l) {
+    std::sort(per[l].begin(), per[l].end());
+    lane_ranges.push_back(static_cast<int>(items.size()));
+    items.insert(items.end(), per[l].begin(), per[l].end());
+  }
+  lane_ranges.push_back(static_cast<int>(items.size()));
+}
 
 double fact(int k) {
   double f = 1.0;
@@ -95,6 +135,26 @@ const TabHost &tables() {
           }
       t.uoff.push_back(static_cast<int>(t.ucoef.size()));
     }
+    for (int P = kTabMinP; P <= kTabMaxP; ++P) {
+      const int NM = mi_off(P + 1), NU = mi_off(P + 2), NL = NM - 1;
+      std::vector<int> wu(NU), wl(NL);
+      for (int g = 0; g < NU; ++g) wu[g] = t.uoff[g + 1] - t.uoff[g];
+      for (int o = 0; o < NL; ++o) wl[o] = mi_off(P - t.expo[o + 1].w + 1);
+      lane_split(wu, t.u_lane, t.u_items);
+      lane_split(wl, t.l_lane, t.l_items);
+      t.c_off.push_back(static_cast<int>(t.c_pairs.size()));
+      for (int ia = 0; ia < NM; ++ia) {
+        const int4 a = t.expo[ia];
+        const int nb = P - a.w;
+        for (int ib = mi_off(nb); ib < mi_off(nb + 1); ++ib) {
+          const int4 b = t.expo[ib];
+          const int x = a.x + b.x, y = a.y + b.y, z = a.z + b.z;
+          t.c_pairs.push_back(make_int2(ia | (ib << 16), mi_idx_host(x + 1, y, z) | (mi_idx_host(x, y + 1, z) << 8) |
+                                                             (mi_idx_host(x, y, z + 1) << 16)));
+        }
+      }
+    }
+    t.c_off.push_back(static_cast<int>(t.c_pairs.size()));
   });
   return t;
 }
@@ -105,34 +165,53 @@ struct TabDev {
   const int *uoff;
   const double *ucoef;
   const int *uexp;
+  const int *u_lane, *l_lane, *u_items, *l_items, *c_off;
+  const int2 *c_pairs;
 };
 
 // the device copy of the tables, in one context-owned buffer
 int device_tables(fmm_ctx *c, TabDev *out) {
   const TabHost &t = tables();
-  const size_t b_expo = t.expo.size() * sizeof(int4), b_if = t.ifact.size() * sizeof(double),
-               b_uoff = t.uoff.size() * sizeof(int), b_uc = t.ucoef.size() * sizeof(double),
-               b_ue = t.uexp.size() * sizeof(int);
   auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
-  const size_t o_if = up(b_expo), o_uoff = o_if + up(b_if), o_uc = o_uoff + up(b_uoff), o_ue = o_uc + up(b_uc),
-               total = o_ue + up(b_ue);
+  struct Part {
+    const void *src;
+    size_t bytes, off;
+  };
+  Part parts[] = {{t.expo.data(), t.expo.size() * sizeof(int4), 0},
+                  {t.ifact.data(), t.ifact.size() * sizeof(double), 0},
+                  {t.uoff.data(), t.uoff.size() * sizeof(int), 0},
+                  {t.ucoef.data(), t.ucoef.size() * sizeof(double), 0},
+                  {t.uexp.data(), t.uexp.size() * sizeof(int), 0},
+                  {t.u_lane.data(), t.u_lane.size() * sizeof(int), 0},
+                  {t.l_lane.data(), t.l_lane.size() * sizeof(int), 0},
+                  {t.u_items.data(), t.u_items.size() * sizeof(int), 0},
+                  {t.l_items.data(), t.l_items.size() * sizeof(int), 0},
+                  {t.c_off.data(), t.c_off.size() * sizeof(int), 0},
+                  {t.c_pairs.data(), t.c_pairs.size() * sizeof(int2), 0}};
+  size_t total = 0;
+  for (Part &q : parts) {
+    q.off = total;
+    total += up(q.bytes);
+  }
   if (c->gen_tab.cap < total) {
     AMFMM_TRY(ensure_bytes(c, c->gen_tab, total));
     std::vector<char> h(total, 0);
-    memcpy(h.data(), t.expo.data(), b_expo);
-    memcpy(h.data() + o_if, t.ifact.data(), b_if);
-    memcpy(h.data() + o_uoff, t.uoff.data(), b_uoff);
-    memcpy(h.data() + o_uc, t.ucoef.data(), b_uc);
-    memcpy(h.data() + o_ue, t.uexp.data(), b_ue);
+    for (const Part &q : parts) memcpy(h.data() + q.off, q.src, q.bytes);
     // synchronous: the host vector goes out of scope afterwards
     AMFMM_CUDA(c, cudaMemcpy(c->gen_tab.p, h.data(), total, cudaMemcpyHostToDevice));
   }
-  char *base = static_cast<char *>(c->gen_tab.p);
-  out->expo = reinterpret_cast<const int4 *>(base);
-  out->ifact = reinterpret_cast<const double *>(base + o_if);
-  out->uoff = reinterpret_cast<const int *>(base + o_uoff);
-  out->ucoef = reinterpret_cast<const double *>(base + o_uc);
-  out->uexp = reinterpret_cast<const int *>(base + o_ue);
+  const char *base = static_cast<const char *>(c->gen_tab.p);
+  out->expo = reinterpret_cast<const int4 *>(base + parts[0].off);
+  out->ifact = reinterpret_cast<const double *>(base + parts[1].off);
+  out->uoff = reinterpret_cast<const int *>(base + parts[2].off);
+  out->ucoef = reinterpret_cast<const double *>(base + parts[3].off);
+  out->uexp = reinterpret_cast<const int *>(base + parts[4].off);
+  out->u_lane = reinterpret_cast<const int *>(base + parts[5].off);
+  out->l_lane = reinterpret_cast<const int *>(base + parts[6].off);
+  out->u_items = reinterpret_cast<const int *>(base + parts[7].off);
+  out->l_items = reinterpret_cast<const int *>(base + parts[8].off);
+  out->c_off = reinterpret_cast<const int *>(base + parts[9].off);
+  out->c_pairs = reinterpret_cast<const int2 *>(base + parts[10].off);
   return FMM_OK;
 }
 
@@ -177,7 +256,7 @@ __global__ void __launch_bounds__(kTabWarps * 32) k_m2l_tab(int P, int64_t K, co
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   PairSmem &sm = sm_all[w];
-  const int NM = mi_off(P + 1), NU = mi_off(P + 2), NL = NM - 1;
+  const int NM = mi_off(P + 1), NL = NM - 1;
   for (int64_t k = blockIdx.x * static_cast<int64_t>(kTabWarps) + w; k < K;
        k += static_cast<int64_t>(gridDim.x) * kTabWarps) {
     const int A = pairs[k].x, B = pairs[k].y;
@@ -212,8 +291,10 @@ __global__ void __launch_bounds__(kTabWarps * 32) k_m2l_tab(int P, int64_t K, co
       sm.sB[i] = (o % 2 == 0 ? f : -f) * mB[i];
     }
     __syncwarp();
-    // U^g(n) for |g| <= P + 1
-    for (int g = lane; g < NU; g += 32) {
+    // U^g(n) for |g| <= P + 1, each lane its share of the terms
+    const int sp = (P - kTabMinP) * 33;
+    for (int it = tab.u_lane[sp + lane]; it < tab.u_lane[sp + lane + 1]; ++it) {
+      const int g = tab.u_items[it];
       double u = 0.0;
       for (int t = tab.uoff[g]; t < tab.uoff[g + 1]; ++t) {
         const int e = tab.uexp[t];
@@ -222,20 +303,17 @@ __global__ void __launch_bounds__(kTabWarps * 32) k_m2l_tab(int P, int64_t K, co
       sm.U[g] = u;
     }
     __syncwarp();
-    // corrective force: lanes over a, b over the order P - |a|
+    // corrective force: the lanes stride through the (a, b) products with
+    // |a| + |b| = P
     double f0 = 0.0, f1 = 0.0, f2 = 0.0;
     if (VARIANT != FMM_UC) {
-      for (int ia = lane; ia < NM; ia += 32) {
-        const int pa = ex[ia];
-        const int nb = P - (pa >> 24);
-        const double ca = -sm.sA[ia];
-        for (int ib = mi_off(nb); ib < mi_off(nb + 1); ++ib) {
-          const double cb = ca * sm.sB[ib];  // (-1)^|b| / (a! b!) folded in
-          const int ab = (pa + ex[ib]) & 0xffffff;
-          f0 += cb * sm.U[mi_idx_sum(ab, 1)];
-          f1 += cb * sm.U[mi_idx_sum(ab, 1 << 8)];
-          f2 += cb * sm.U[mi_idx_sum(ab, 1 << 16)];
-        }
+      const int c1 = tab.c_off[P - kTabMinP + 1];
+      for (int it = tab.c_off[P - kTabMinP] + lane; it < c1; it += 32) {
+        const int2 pq = tab.c_pairs[it];
+        const double cb = -sm.sA[pq.x & 0xffff] * sm.sB[pq.x >> 16];  // (-1)^|b| / (a! b!) folded in
+        f0 += cb * sm.U[pq.y & 255];
+        f1 += cb * sm.U[(pq.y >> 8) & 255];
+        f2 += cb * sm.U[pq.y >> 16];
       }
       // lane sums in a fixed order
       sm.F[0][lane] = f0;
@@ -258,8 +336,9 @@ __global__ void __launch_bounds__(kTabWarps * 32) k_m2l_tab(int P, int64_t K, co
         f2 -= nz * nf;
       }
     }
-    // locals of order 1..P on both sides: lanes over the output index
-    for (int o = lane; o < NL; o += 32) {
+    // locals of order 1..P on both sides, each lane its share of the outputs
+    for (int it = tab.l_lane[sp + lane]; it < tab.l_lane[sp + lane + 1]; ++it) {
+      const int o = tab.l_items[it];
       const int pq = ex[o + 1] & 0xffffff;
       const int nq = ex[o + 1] >> 24;
       double accA = 0.0, accB = 0.0;
