@@ -113,3 +113,46 @@ def test_softening_arguments():
     with pytest.raises(fmm.FMMError) as e:
         s4.solve(*_dev(b))
     assert e.value.code == fmm.FMM_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("variant", ["UC", "TCO"])
+def test_softened_mixed_other_variants(variant):
+    """The mixed form's raw-moment records (softened) for the other two
+    variants: rms <= 1e-6 against the softened oracle, forces balanced, and
+    the torque too where the variant conserves it."""
+    from paper_1706_06989_gb300 import fmm
+    b = ics.plummer(40000, seed=45)
+    eps = 0.01
+    s = fmm.FMM(theta=0.5, variant=variant, precision="mixed")
+    s.set_softening(eps)
+    a = torch.stack(s.solve(*_dev(b)), 1).cpu().numpy()
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25, softening=eps)
+    t = ics.error_subset(b.n, 3000, seed=2)
+    rel = _rel(a[t], o.accel(variant, targets=t))
+    assert np.sqrt(np.mean(rel ** 2)) <= 1e-6
+    fb, tb = oracle.balance(b.x, b.y, b.z, b.m, a)
+    assert fb <= 1e-6
+    if variant != "UC":
+        assert tb <= 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_softened_forest_equals_one_solve_per_system(precision):
+    """Forests honour the softening: each system of the forest is
+    bit-identical to its own softened solve, and matches the oracle."""
+    from paper_1706_06989_gb300 import fmm
+    off, b = ics.ensemble(nsys=6, seed=9, nmin=300, nmax=3000)
+    eps = 0.02
+    s = fmm.FMM(theta=0.5, precision=precision)
+    s.set_softening(eps)
+    x, y, z, m = _dev(b)
+    got = torch.stack(s.solve_batch(x, y, z, m, off), 1).cpu().numpy()
+    for k in range(len(off) - 1):
+        sl = slice(int(off[k]), int(off[k + 1]))
+        one = torch.stack(s.solve(x[sl].contiguous(), y[sl].contiguous(), z[sl].contiguous(),
+                                  m[sl].contiguous()), 1).cpu().numpy()
+        assert np.array_equal(one, got[sl]), k
+    if precision == "fp64":
+        sl = slice(int(off[0]), int(off[1]))
+        ref = oracle.Oracle(b.x[sl], b.y[sl], b.z[sl], b.m[sl], 0.5, 25, softening=eps).accel("TC")
+        assert _rel(got[sl], ref).max() <= 1e-12
