@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
       }
       if (valid) {
         if (mutual) {
-          T *o = slots + col.y;
+          T *o = slots + 3 * static_cast<int64_t>(col.y);
           if (r0 == 0) {
             o[0] = bx;
             o[1] = by;
@@ -550,7 +550,8 @@ __global__ void k_cols_pairs(int64_t K, const int2 *__restrict__ pairs, const in
     const long long oo = __shfl_sync(0xffffffffu, o, own);
     if (j < total) {
       const int t = j - x;
-      cols[b + t] = make_int2(bb + t, static_cast<int32_t>(oo + 3 * t));
+      // the slot's index (its offset / 3): 3x the range of an int32 offset
+      cols[b + t] = make_int2(bb + t, static_cast<int32_t>(oo / 3 + t));
     }
   }
 }
@@ -710,9 +711,11 @@ int p2p_prepare(fmm_ctx *c) {
   }
   const int64_t nslot = h[0], ncol = hc[0];
   const int64_t nitem = hc[1], nextra = hc[2];
-  // the slots are addressed with int32 offsets: refuse before anything is
-  // sized or launched from these totals
-  if (nslot + 3 > 0x7fffffffLL) return set_error(c, FMM_EUNSUPPORTED, "too many near-field slots (%lld)", (long long)nslot);
+  // the columns (one per body of A and per slot: n + nslot / 3) are counted
+  // by int32 scans and a slot is named by its int32 index: refuse before
+  // anything is sized or launched from these totals
+  if (nslot / 3 + n + 1 > 0x7fffffffLL)
+    return set_error(c, FMM_EUNSUPPORTED, "too many near-field slots (%lld values)", (long long)nslot);
   c->sz.p2p_items = nitem;
   AMFMM_TRY(ensure<int4>(c, c->p2p_items, nitem + 1));
   AMFMM_TRY(ensure<double>(c, c->p2p_extra, nextra + 1));
