@@ -17,6 +17,7 @@
 // independent of the traversal order.  The walk proceeds one generation of
 // pairs at a time; an exclusive scan of the per-pair output counts places
 // every output, which makes the list order deterministic.
+#include <cmath>
 #include <cstring>
 
 #include "geom.cuh"
@@ -383,17 +384,25 @@ int pack_walk_cells(fmm_ctx *c) {
 int walk(fmm_ctx *c) {
   cudaStream_t st = c->stream;
   const int64_t n = c->sz.n;
-  int64_t cap_front = std::max<int64_t>(4096, n / 4);
+  // First sizes of the walk's buffers, per body: the lists grow about as
+  // theta^-3 (at theta = 0.5 a Plummer sphere has 24 accepted pairs and 4
+  // leaf pairs per body), bounded so that small angles do not reserve
+  // memory ahead of need; a generation that outgrows them runs again.
+  const double s3 = std::min(8.0, std::pow(0.5 / c->theta, 3.0));
+  const auto per_body = [&](double lo, double k, double hi) {
+    return static_cast<int64_t>(static_cast<double>(n) * std::min(hi, std::max(lo, k * s3)));
+  };
+  int64_t cap_front = std::max<int64_t>(4096, per_body(0.25, 8.0, 32.0));
   AMFMM_TRY(ensure<int2>(c, c->front[0], cap_front));
   AMFMM_TRY(ensure<int2>(c, c->front[1], cap_front));
   int64_t cap_m2l = c->m2l.cap / sizeof(int2), cap_p2p = c->p2p.cap / sizeof(int2),
           cap_self = c->self_list.cap / sizeof(int32_t);
   if (cap_m2l < 1024) {
-    cap_m2l = std::max<int64_t>(1024, 8 * n);
+    cap_m2l = std::max<int64_t>(1024, per_body(8.0, 32.0, 256.0));
     AMFMM_TRY(ensure<int2>(c, c->m2l, cap_m2l));
   }
   if (cap_p2p < 1024) {
-    cap_p2p = std::max<int64_t>(1024, 2 * n);
+    cap_p2p = std::max<int64_t>(1024, per_body(2.0, 6.0, 48.0));
     AMFMM_TRY(ensure<int2>(c, c->p2p, cap_p2p));
   }
   if (cap_self < 1024) {

@@ -364,15 +364,16 @@ def test_balance_diagnostic_matches_oracle():
 
 def test_lists_when_the_walk_outgrows_its_buffers():
     """A small opening angle on a uniform cube makes the frontier and the
-    near-field list outgrow their first buffers (front n/4 >= 4096 pairs, P2P
-    2n pairs): the generation is flagged, the buffers grow and the generation
-    runs again.  Lists must still match the oracle bit for bit, and a second
-    solve (buffers already large) must give the same accelerations."""
-    b = ics.uniform_cube(3000, seed=11)
+    near-field list outgrow their first buffers (at most 32 n and 48 n
+    pairs): every leaf pair is summed directly.  The generation is flagged,
+    the buffers grow and the generation runs again.  Lists must still match
+    the oracle bit for bit, and a second solve (buffers already large) must
+    give the same accelerations."""
+    b = ics.uniform_cube(20000, seed=11)
     s, a = _solve(b, theta=0.05)
     o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.05, 25)
     st = s.stats()
-    assert st.n_p2p > 2 * b.n  # the first P2P buffer held 2n pairs
+    assert st.n_p2p > 48 * b.n  # beyond the first P2P buffer
     m2l, p2p, slf = s.export_lists()
     om2l, op2p, oslf = o.lists()
     assert np.array_equal(_canon_pairs(m2l.cpu().numpy()), _canon_pairs(om2l))
