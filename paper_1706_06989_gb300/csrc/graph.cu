@@ -283,7 +283,3 @@ int graph_solve(fmm_ctx *c, double *ax, double *ay, double *az) {
 }  // namespace amfmm
 
 extern "C" const char *fmm_graph_error(const fmm_ctx *c) { return c ? c->gerrbuf : "NULL context"; }
-
-namespace amfmm {
-
-}  // namespace amfmm
