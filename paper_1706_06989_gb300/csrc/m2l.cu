@@ -46,6 +46,7 @@ constexpr int kBlock = 128;
 constexpr int kCell32 = 24;    // floats per cell in the mixed form's copy (raw moments)
 constexpr int kCell32TF = 20;  // the same with trace-free moments (unsoftened UC and TC)
 constexpr int kQOh = 16;     // doubles per cell of the FP64 form's quadrupole and octupole per mass
+constexpr int kSlot64 = 24;  // doubles per slot of the FP64 order-3 M2L (21 used: m2l_pair's SLOT form)
 
 __device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
 __device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
@@ -83,13 +84,19 @@ __device__ __forceinline__ float min_r2<float>() { return 1e-30f; }
 // to rounding, about 24 fewer FP64 operations per pair.  (Softened
 // derivatives are not trace-free, and TCO's correction is not a contraction
 // with the full D: both keep the raw moments.)
-template <class T, int VARIANT, bool HARM = false>
+//
+// SLOT: the pair's slot form for the FP64 reduction (kSlot64 values per
+// side): C_i as above, then the unit tensors U2 and U3 themselves, then the
+// side's scale factors of the two (C^A: M_B R^-3, M_B R^-4; C^B: M_A R^-3,
+// -M_A R^-4), which the reduction applies with one FMA per value where it
+// would otherwise add (32 products fewer per pair).
+template <class T, int VARIANT, bool HARM = false, bool SLOT = false>
 __device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, const T *QA, const T *QB, const T *OhA,
                                          const T *OhB, T eps2, T *CA, T *CB) {
   const T r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
   if (!(r2 > min_r2<T>())) {
 #pragma unroll
-    for (int q = 0; q < 19; ++q) CA[q] = CB[q] = T(0);
+    for (int q = 0; q < (SLOT ? 21 : 19); ++q) CA[q] = CB[q] = T(0);
     return;
   }
   const T Ri = rsqrt_t(r2 + eps2);
@@ -138,15 +145,26 @@ __device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, const T *QA, 
     CA[i] = MB2 * nv[i] + hB[i];
     CB[i] = -(MA2 * nv[i] + hA[i]);
   }
+  if (SLOT) {
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    CA[3 + k] = MB3 * U2[k];
-    CB[3 + k] = MA3 * U2[k];
-  }
+    for (int k = 0; k < 6; ++k) CA[3 + k] = CB[3 + k] = U2[k];
 #pragma unroll
-  for (int k = 0; k < 10; ++k) {
-    CA[9 + k] = MB4 * U3[k];
-    CB[9 + k] = -(MA4 * U3[k]);
+    for (int k = 0; k < 10; ++k) CA[9 + k] = CB[9 + k] = U3[k];
+    CA[19] = MB3;
+    CA[20] = MB4;
+    CB[19] = MA3;
+    CB[20] = -MA4;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      CA[3 + k] = MB3 * U2[k];
+      CB[3 + k] = MA3 * U2[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+      CA[9 + k] = MB4 * U3[k];
+      CB[9 + k] = -(MA4 * U3[k]);
+    }
   }
   if (VARIANT == FMM_TC && HARM) {
     // trace-free Sh: F = 7.5 R^-5 [u + (-7/3) n (n.u)], the 7.5 R^-5 folded
@@ -199,7 +217,8 @@ __device__ __forceinline__ void m2l_pair(const T r[3], T MA, T MB, const T *QA, 
   }
 }
 
-// One thread per accepted pair.  Slots are kLocStride wide (19 used).
+// One thread per accepted pair.  Slots are kSlot64 wide (m2l_pair's SLOT
+// form, 21 used).
 // FP64 form: reads the FP64 cell data.
 // qoh: per cell the quadrupole (6) and the octupole per unit mass (10) the
 // pair function takes, trace-free where HARM allows (k_qoh).
@@ -213,16 +232,16 @@ __global__ void __launch_bounds__(kBlock) k_m2l64(int64_t K, const int2 *__restr
   const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (k >= K) return;
   const int A = pairs[k].x, B = pairs[k].y;
-  double CA[kLocStride], CB[kLocStride];
+  double CA[kSlot64], CB[kSlot64];
   const double r[3] = {Z[3 * A] - Z[3 * B], Z[3 * A + 1] - Z[3 * B + 1], Z[3 * A + 2] - Z[3 * B + 2]};
   const double *qA = qoh + static_cast<int64_t>(A) * kQOh;
   const double *qB = qoh + static_cast<int64_t>(B) * kQOh;
-  m2l_pair<double, VARIANT, HARM>(r, M[A], M[B], qA, qB, qA + 6, qB + 6, eps2, CA, CB);
-  CA[19] = CB[19] = 0.0;
-  double *sa = slots + static_cast<int64_t>(pos[2 * k]) * kLocStride;
-  double *sb = slots + static_cast<int64_t>(pos[2 * k + 1]) * kLocStride;
+  m2l_pair<double, VARIANT, HARM, true>(r, M[A], M[B], qA, qB, qA + 6, qB + 6, eps2, CA, CB);
+  CA[21] = CB[21] = CA[22] = CB[22] = CA[23] = CB[23] = 0.0;
+  double *sa = slots + static_cast<int64_t>(pos[2 * k]) * kSlot64;
+  double *sb = slots + static_cast<int64_t>(pos[2 * k + 1]) * kSlot64;
 #pragma unroll
-  for (int q = 0; q < kLocStride; q += 2) {
+  for (int q = 0; q < kSlot64; q += 2) {
     *reinterpret_cast<double2 *>(sa + q) = make_double2(CA[q], CA[q + 1]);
     *reinterpret_cast<double2 *>(sb + q) = make_double2(CB[q], CB[q + 1]);
   }
@@ -645,51 +664,104 @@ __global__ void k_inverse(int64_t E, const uint32_t *__restrict__ sval, int32_t 
   if (s < E) pos[sval[s]] = static_cast<int32_t>(s);
 }
 
-// Every cell sums its FP64 slots (kLocStride = 20 doubles per slot, in the
+// Every cell sums its FP64 slots (kSlot64 = 24 doubles per slot, in the
 // stable order of the sort): one warp per cell reads the cell's slot rows as
 // one flat array, 32 consecutive doubles per load, so every lane is busy and
-// every load is two full 128-byte lines.  Element e of the block belongs to
-// coefficient e mod 20; lane l meets, at its j-th load, coefficient
-// (l + 32 j) mod 20, which repeats with period 5 (32 = 12 mod 20 and
-// 5 x 12 = 60 = 0 mod 20), so every lane keeps five partial sums (phase
-// u = j mod 5).  The partials of a coefficient are then added by one lane
-// in a fixed order (phase, then lane).
+// every load is two full 128-byte lines.  Element e of the block is value
+// e mod 24 of its slot; lane l meets, at its j-th load, value (l + 32 j) mod
+// 24, which repeats with period 3 (3 x 32 = 4 x 24), so every lane keeps
+// three partial sums (phase u = j mod 3), each of one coefficient.  A field
+// coefficient (value < 3) is added; a U2 or U3 value is multiplied by its
+// slot's scale factor (value 19 or 20 of the same slot, held by lane l + so
+// of the same load or of the next) in one FMA; the partials of the lanes
+// that meet scale factors and the pad are never read.  The partials of a
+// coefficient are then added by one lane in a fixed order (phase, then
+// lane).
 constexpr int kRedWarps = 8;
+constexpr int kRedPhases = 3;   // loads per period
+constexpr int kRedPeriods = 2;  // periods per loop trip: six loads in flight
+
+// Lane t sends, in the shuffle of phase u, its element of the NEXT load
+// (position 32 (u + 1) + t of the period) when that element is a scale
+// factor whose first user lies in load u; otherwise its own element of load u.
+__host__ __device__ constexpr int red_scale_off(int q) { return q < 9 ? 19 - q : 20 - q; }
+__host__ __device__ constexpr bool red_sends_next(int u, int t) {
+  const int p = 32 * (u + 1) + t, r = p % kSlot64, first = p - r + (r == 19 ? 3 : 9);
+  return u + 1 < kRedPhases && (r == 19 || r == 20) && first < 32 * (u + 1);
+}
+// Every value of load u that needs a scale factor finds it in the phase's
+// shuffle: at lane l + so of load u (a lane that does not send ahead) or at
+// lane l + so - 32 of load u + 1 (a lane that does).
+constexpr bool red_plan_ok() {
+  for (int u = 0; u < kRedPhases; ++u)
+    for (int l = 0; l < 32; ++l) {
+      const int q = (l + 32 * u) % kSlot64;
+      if (q < 3 || q >= 19) continue;
+      const int t = l + red_scale_off(q);
+      if (t < 32 ? red_sends_next(u, t) : (u + 1 >= kRedPhases || !red_sends_next(u, t - 32))) return false;
+    }
+  return true;
+}
+static_assert(red_plan_ok(), "one shuffle per phase must carry every scale factor");
+static_assert((kRedPhases * 32) % kSlot64 == 0, "a period of loads covers whole slots");
 
 __global__ void __launch_bounds__(kRedWarps * 32) k_m2l_reduce(int32_t ncell, const int32_t *__restrict__ off,
                                                                const double *__restrict__ slots,
                                                                double *__restrict__ loc) {
-  __shared__ double part[kRedWarps][5][32];
+  __shared__ double part[kRedWarps][kRedPhases][32];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int c = blockIdx.x * kRedWarps + w;
   if (c >= ncell) return;  // a whole warp: no block-wide synchronisation below
-  const int64_t e0 = static_cast<int64_t>(off[c]) * kLocStride, e1 = static_cast<int64_t>(off[c + 1]) * kLocStride;
-  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  int64_t e = e0 + l;
-  // whole periods of 5 x 32 elements: five independent loads in flight
-  for (; e + 4 * 32 < e1; e += 5 * 32) {
-    double v[5];
+  const int64_t e0 = static_cast<int64_t>(off[c]) * kSlot64, e1 = static_cast<int64_t>(off[c + 1]) * kSlot64;
+  double acc[kRedPhases];
+  int src[kRedPhases];
+  bool ahead[kRedPhases], field[kRedPhases];
 #pragma unroll
-    for (int u = 0; u < 5; ++u) v[u] = __ldg(&slots[e + 32 * u]);
+  for (int u = 0; u < kRedPhases; ++u) {
+    acc[u] = 0.0;
+    const int q = (l + 32 * u) % kSlot64;
+    src[u] = (l + red_scale_off(q)) & 31;
+    ahead[u] = red_sends_next(u, l);
+    field[u] = q < 3;
+  }
+  // The block is a whole number of slots and a slot never straddles two
+  // periods, so every scale factor a loaded value needs is loaded too.
+  for (int64_t b = e0; b < e1; b += kRedPeriods * kRedPhases * 32) {
+    double v[kRedPeriods][kRedPhases];
 #pragma unroll
-    for (int u = 0; u < 5; ++u) acc[u] += v[u];
+    for (int h = 0; h < kRedPeriods; ++h)
+#pragma unroll
+      for (int u = 0; u < kRedPhases; ++u) {
+        const int64_t e = b + l + 32 * (h * kRedPhases + u);
+        v[h][u] = e < e1 ? __ldg(&slots[e]) : 0.0;
+      }
+#pragma unroll
+    for (int h = 0; h < kRedPeriods; ++h)
+#pragma unroll
+      for (int u = 0; u < kRedPhases; ++u) {
+        const double send = u + 1 < kRedPhases && ahead[u] ? v[h][u + 1 < kRedPhases ? u + 1 : u] : v[h][u];
+        const double f = __shfl_sync(0xffffffffu, send, src[u]);
+        // one FP64 instruction per load for every lane (the FP64 pipe, not
+        // DRAM, bounds this kernel): a field value is taken with factor 1;
+        // the lanes of scale factors and pad fill partials that nothing reads
+        if (b + l + 32 * (h * kRedPhases + u) < e1) acc[u] = fma(v[h][u], field[u] ? 1.0 : f, acc[u]);
+      }
   }
 #pragma unroll
-  for (int u = 0; u < 5; ++u)
-    if (e + 32 * u < e1) acc[u] += __ldg(&slots[e + 32 * u]);
-#pragma unroll
-  for (int u = 0; u < 5; ++u) part[w][u][l] = acc[u];
+  for (int u = 0; u < kRedPhases; ++u) part[w][u][l] = acc[u];
   __syncwarp();
-  if (l < kLocStride) {
-    // lanes holding coefficient q at phase u: l = (q - 12 u) mod 20, and that + 20
+  if (l < 19) {
+    // lanes holding coefficient q at phase u: l = (q - 32 u) mod 24, and that + 24
     double s = 0.0;
 #pragma unroll
-    for (int u = 0; u < 5; ++u) {
-      const int r = ((l - 12 * u) % 20 + 20) % 20;
+    for (int u = 0; u < kRedPhases; ++u) {
+      const int r = ((l - 32 * u) % kSlot64 + kSlot64) % kSlot64;
       s += part[w][u][r];
-      if (r + 20 < 32) s += part[w][u][r + 20];
+      if (r + kSlot64 < 32) s += part[w][u][r + kSlot64];
     }
     loc[static_cast<int64_t>(c) * kLocStride + l] = s;
+  } else if (l == 19) {
+    loc[static_cast<int64_t>(c) * kLocStride + 19] = 0.0;
   }
 }
 
@@ -781,7 +853,8 @@ int m2l_prepare(fmm_ctx *c) {
     k_inverse<<<grid_for(E, 256), 256, 0, st>>>(E, ptr<uint32_t>(c->eval[which]), ptr<int32_t>(c->m2l_pos));
     AMFMM_TRY(launched(c, "m2l_inverse"));
     const size_t esz = fp32 ? sizeof(float) : sizeof(double);
-    AMFMM_TRY(ensure_bytes(c, c->m2l_slots, static_cast<size_t>(E) * loc_stride(c->opts.order_P) * esz));
+    const int stride = c->opts.order_P == 3 ? kSlot64 : loc_stride(c->opts.order_P);
+    AMFMM_TRY(ensure_bytes(c, c->m2l_slots, static_cast<size_t>(E) * stride * esz));
   }
   if (fp32) {
     AMFMM_TRY(ensure<float>(c, c->cell32, static_cast<size_t>(kCell32) * nc));
