@@ -36,8 +36,38 @@ constexpr int kWarps = 4;
 // 19.8 -> 18.2 ms); 8 costs more column passes than it gains (1.22 / 18.4
 // ms).  Ensembles of small systems may prefer another tile.
 
-__device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
-__device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
+// r^-3 from r^2 > 0, the factor of every pair force.
+// FP32: the hardware reciprocal square root, cubed.
+__device__ __forceinline__ float inv_r3(float r2) {
+  const float ri = rsqrtf(r2);
+  return ri * ri * ri;
+}
+// FP64, where the FP64 pipe bounds the kernel: a 24-bit seed y0 ~ r^-1 from
+// the FP32 unit, then r^-3 = y0^3 (1 - e)^(-3/2) with e = 1 - r^2 y0^2,
+// expanded by the binomial series to 1 + 3/2 e + 15/8 e^2 (|e| < 2^-21, so
+// the first omitted term, 35/16 e^3, lies below 2^-60): six FP64 operations
+// in all.  The seed comes from r^2 = m 4^k with m in [1, 4): m's leading 23
+// bits make an FP32 number, and its reciprocal root scaled by 2^-k goes back
+// to FP64 by integer operations on the bit patterns, not by conversions.
+// y0 has 24 significant bits, so y0^2 is exact and e carries one rounding.
+// Subnormal, infinite or NaN r^2 take the library's reciprocal square root.
+__device__ __forceinline__ double inv_r3(double r2) {
+  const long long bits = __double_as_longlong(r2);
+  const int ex = static_cast<int>(bits >> 52);  // r2 >= 0: the biased exponent
+  if (ex == 0 || ex == 0x7ff) {
+    const double ri = rsqrt(r2);
+    return ri * ri * ri;
+  }
+  const int E = ex - 1023, k = E >> 1;  // r2 = m 2^(2k), m in [1, 4)
+  const unsigned mf = (static_cast<unsigned>(E - 2 * k + 127) << 23) | static_cast<unsigned>((bits >> 29) & 0x7fffff);
+  const unsigned yf = __float_as_uint(rsqrtf(__uint_as_float(mf)));  // in (1/2, 1]
+  const double y0 = __longlong_as_double((static_cast<long long>(static_cast<int>(yf >> 23) - 127 + 1023 - k) << 52) |
+                                         (static_cast<long long>(yf & 0x7fffff) << 29));
+  const double y2 = y0 * y0;
+  const double e = fma(-r2, y2, 1.0);
+  const double y3 = y2 * y0;
+  return fma(y3, e * fma(e, 1.875, 1.5), y3);
+}
 
 // Shared memory per warp: the rows (bodies of A) and, per row and component,
 // one running partial of the A-side sum for every lane.
@@ -270,8 +300,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
         // operation; eps2 = 0 gives the unsoftened sum)
         const T r2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps2)));
         if (valid && p2p_apart(r2)) {
-          const T ri = rsqrt_t(r2);
-          const T r3 = ri * ri * ri;
+          const T r3 = inv_r3(r2);
           const T si = sm.row[i][3] * r3;
           bx += si * dx;
           by += si * dy;
