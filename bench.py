@@ -44,17 +44,20 @@ FP32_PEAK = SM_COUNT * SM_MAX_MHZ * 1e6 * 256
 # kernels' expressions: an accepted M2L pair of each variant (unsoftened:
 # trace-free quadrupoles, and for TC trace-free octupoles), a body pair
 M2L_FLOPS = {"UC": 162, "TC": 235, "TCO": 238}
+# of those, the FP64 form's pair kernel leaves the 32 products of the unit
+# tensors U2 and U3 by their scale factors to the per-cell reduction
+M2L_FLOPS_IN_REDUCE_FP64 = 32
 # the selector experiment's measure of interaction work: a fixed weight per
 # accepted pair (the TC pair's flops written with the trace terms) and per
 # body pair, so that its gains compare interaction sets, not kernel versions
 WORK_PER_M2L_PAIR = 295
 # DRAM traffic of the dominant kernel per unit it processes, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of k_p2p<double, 16>
-# on a Plummer sphere of N = 262,144 (theta = 0.5, TC): 116,205,568 B read and
-# 203,413,248 B written for 115,126,406 body pairs.  Scaled by the body pairs
+# on a Plummer sphere of N = 262,144 (theta = 0.5, TC): 118,164,736 B read and
+# 204,189,184 B written for 115,126,406 body pairs.  Scaled by the body pairs
 # of the launch timed (the traffic grows with them: column stream, B-side
 # partial slots and near-field sums are all per pair or per body).
-TRAFFIC_PER_UNIT = {("p2p", "fp64"): (116205568 + 203413248) / 115126406}
+TRAFFIC_PER_UNIT = {("p2p", "fp64"): (118164736 + 204189184) / 115126406}
 P2P_FLOPS_PER_BODY_PAIR = 25
 ORACLE_SAMPLE_N = 131072      # single-core oracle sample (bodies)
 REFERENCE_N = 262144          # bodies per step of the reference arm (all cores)
@@ -317,7 +320,7 @@ def run_ours(a):
     # roofline of the dominant interaction kernel (alu bound, FP64 or FP32)
     m2l_ms = statistics.mean(kern["m2l"])
     p2p_ms = statistics.mean(kern["p2p"])
-    m2l_flops = M2L_FLOPS[a.variant] * st.n_m2l
+    m2l_flops = (M2L_FLOPS[a.variant] - (M2L_FLOPS_IN_REDUCE_FP64 if a.precision == "fp64" else 0)) * st.n_m2l
     p2p_flops = P2P_FLOPS_PER_BODY_PAIR * st.p2p_body_pairs
     peak = FP64_PEAK if a.precision == "fp64" else FP32_PEAK
     if a.order_p != 3:
