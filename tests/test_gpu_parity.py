@@ -88,6 +88,30 @@ def test_plummer_2000_matches_oracle(variant):
         assert tb <= 1e-13
 
 
+@pytest.mark.parametrize("k", [-90, 90])
+def test_fp64_far_from_unit_scale(k):
+    """Positions scaled by 2^k (masses unchanged): the FP64 path keeps its
+    1e-12 parity against the oracle, which takes the same scaled inputs.
+    Morton keys, tree and lists are unchanged by a power-of-two scale, and
+    the pair factor r^-3 of the near field builds its seed from the
+    exponent of r^2 (here near 2^(2k)), so both signs of a large exponent
+    are exercised.  (The oracle is exactly covariant at this scale; at
+    2^+-120 intermediate powers of R in the oracle leave the FP64 range.)"""
+    b0 = ics.plummer(2000, seed=9)
+    f = np.ldexp(1.0, k)
+    b = ics.Bodies(b0.x * f, b0.y * f, b0.z * f, b0.m)
+    s, got = _solve(b)
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25)
+    _compare_lists(s, o)
+    rel = _rel_dev(got, o.accel("TC"))
+    assert rel.max() <= 1e-12, rel.max()
+    # the same lists as the unscaled system, and accelerations 2^(-2k) times its own
+    s0, got0 = _solve(b0)
+    assert s0.stats().n_m2l == s.stats().n_m2l and s0.stats().p2p_body_pairs == s.stats().p2p_body_pairs
+    rel0 = _rel_dev(np.ldexp(got, 2 * k), got0)
+    assert rel0.max() <= 1e-13, rel0.max()
+
+
 def test_moments_match_definition():
     b = ics.plummer(2000, seed=3)
     s, _ = _solve(b)
