@@ -124,6 +124,7 @@ struct fmm_ctx {
   int p2p_rows = 16;  // leaf tile: rows of a leaf staged per pass of the near field (8, 16 or 32)
   amfmm::Sizes sz;
   int m2l_which = 0;  // which of the ekey/eval buffers holds the sorted M2L entries
+  int p2p_order = -1;  // which pval buffer holds the near field's item order (-1: items in index order)
 
   // pinned host scratch for small read-backs
   void *hpin = nullptr;

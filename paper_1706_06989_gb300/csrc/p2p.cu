@@ -198,7 +198,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
     const int32_t *__restrict__ count, const double *__restrict__ Zc, const double *__restrict__ X,
     const double *__restrict__ Y, const double *__restrict__ Zb, const double *__restrict__ Mb,
     const int2 *__restrict__ cols, double *__restrict__ near, double *__restrict__ extra,
-    T *__restrict__ slots, const BodyF *__restrict__ bodyf, T eps2, int *__restrict__ queue) {
+    T *__restrict__ slots, const BodyF *__restrict__ bodyf, T eps2, const int32_t *__restrict__ order,
+    int *__restrict__ queue) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   P2PSmem<T, ROWS> &sm = reinterpret_cast<P2PSmem<T, ROWS> *>(smem_raw)[w];
@@ -206,7 +207,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
   // from a queue until it is empty instead of taking a fixed one: a block's
   // warps then never wait for one another's items (the grid is as large as
   // fits on the GPU at once).  Which warp takes an item does not change what
-  // it computes or where it writes.
+  // it computes or where it writes.  order (FP64 form; may be NULL) hands the
+  // items out largest first.
   for (;;) {
   int q = 0;
   if (l == 0) q = atomicAdd(queue, 1);
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_p2p(
   // work item: leaf, column range; w < 0 marks the leaf's first chunk (which
   // owns the near-field sums of the leaf), w >= 0 the offset of a later
   // chunk's A-side partials in `extra`
-  const int4 it = items[q];
+  const int4 it = items[order ? order[q] : q];
   const int L = it.x;
   const bool first = it.w < 0;
   const int bA = begin[L], nA = count[L];
@@ -425,6 +427,21 @@ __global__ void k_item_fill(int32_t nleaf, const int32_t *__restrict__ leaves, c
   }
 }
 
+// Sort keys that hand the FP64 near field's work items out largest first
+// (rows x columns, coarsened to 16 bits and complemented; the sort is stable,
+// so equal keys keep the item order).  The last items a launch draws are
+// then short, and its tail shrinks.
+__global__ void k_item_keys(int32_t nitem, const int4 *__restrict__ items, const int32_t *__restrict__ count,
+                            uint32_t *__restrict__ key, uint32_t *__restrict__ val) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nitem) return;
+  const int4 it = items[q];
+  const int64_t cost = static_cast<int64_t>(count[it.x]) * (it.z - it.y);
+  const int64_t c8 = cost >> 3;
+  key[q] = 0xffffu - static_cast<uint32_t>(c8 < 0xffff ? c8 : 0xffff);
+  val[q] = static_cast<uint32_t>(q);
+}
+
 // Each body adds, in sorted order, the partials that the pairs in which its
 // leaf is the larger id left for it.
 template <class T>
@@ -605,7 +622,7 @@ int launch_p2p_rows(fmm_ctx *c) {
       ptr<double>(c->Z), ptr<double>(c->X), ptr<double>(c->Y), ptr<double>(c->Zb), ptr<double>(c->Mb),
       ptr<int2>(c->p2p_cols), ptr<double>(c->near), ptr<double>(c->p2p_extra),
       static_cast<T *>(c->p2p_slots.p), sizeof(T) == sizeof(float) ? ptr<BodyF>(c->p2p_bodyf) : nullptr,
-      static_cast<T>(c->eps2), queue);
+      static_cast<T>(c->eps2), c->p2p_order >= 0 ? ptr<int32_t>(c->pval[c->p2p_order]) : nullptr, queue);
   AMFMM_TRY(launched(c, "p2p"));
   if (nitem > nleaf) {
     k_p2p_chunks<<<grid_for(static_cast<int64_t>(nleaf) * 32, 256), 256, 0, c->stream>>>(
@@ -751,6 +768,20 @@ int p2p_prepare(fmm_ctx *c) {
   k_item_fill<<<grid_for(nleaf, 256), 256, 0, st>>>(nleaf, ptr<int32_t>(c->leaves), ptr<int32_t>(c->count), colOff,
                                                     itemOff, extraOff, ptr<int4>(c->p2p_items));
   AMFMM_TRY(launched(c, "p2p_item_fill"));
+  // FP64: the items largest first (the pair sort's buffers are free here).
+  // (The FP32 form gains less from the shorter tail than the sort costs.)
+  c->p2p_order = -1;
+  if (!fp32 && nitem > 1) {
+    AMFMM_TRY(ensure<uint32_t>(c, c->pkey[0], nitem));
+    AMFMM_TRY(ensure<uint32_t>(c, c->pval[0], nitem));
+    k_item_keys<<<grid_for(nitem, 256), 256, 0, st>>>(static_cast<int32_t>(nitem), ptr<int4>(c->p2p_items),
+                                                      ptr<int32_t>(c->count), ptr<uint32_t>(c->pkey[0]),
+                                                      ptr<uint32_t>(c->pval[0]));
+    AMFMM_TRY(launched(c, "p2p_item_keys"));
+    int which = 0;
+    AMFMM_TRY(radix_sort_u32(c, c->pkey, c->pval, nitem, 16, &which));
+    c->p2p_order = which;
+  }
   AMFMM_TRY(ensure_bytes(c, c->p2p_slots, static_cast<size_t>(nslot + 3) * (fp32 ? sizeof(float) : sizeof(double))));
   AMFMM_TRY(ensure<int2>(c, c->p2p_cols, ncol + 1));
   k_cols_self<<<grid_for(nleaf, 256), 256, 0, st>>>(nleaf, ptr<int32_t>(c->leaves), ptr<int32_t>(c->begin),
