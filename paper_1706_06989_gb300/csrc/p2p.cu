@@ -388,42 +388,46 @@ __global__ void k_p2p_chunks(int32_t nleaf, int64_t n, const int32_t *__restrict
 }
 
 // Work items: the column stream of a leaf is cut into chunks of at most
-// kChunk columns (the first chunk also holds all of the leaf's own bodies, so
-// that the one-sided self sums stay in one warp).  One warp per chunk keeps a
-// leaf that the walk paired with millions of bodies (a large sparse leaf next
-// to a dense region) from serialising the kernel.
-constexpr int kChunk = 4096;
+// `chunk` columns (the first chunk also holds all of the leaf's own bodies,
+// so that the one-sided self sums stay in one warp).  One warp per chunk
+// keeps a leaf that the walk paired with millions of bodies (a large sparse
+// leaf next to a dense region) from serialising the kernel.  The FP64 form
+// takes shorter chunks, whose items it hands out largest first (a short
+// tail); the FP32 form keeps longer ones in leaf order, where neighbouring
+// warps share partner columns in cache.
+constexpr int kChunk64 = 2048;
+constexpr int kChunk32 = 4096;
 
-__device__ __forceinline__ int chunks_of(int ncol, int nself) {
-  const int first = max(kChunk, nself);
-  return ncol <= first ? 1 : 1 + (ncol - first + kChunk - 1) / kChunk;
+__device__ __forceinline__ int chunks_of(int ncol, int nself, int chunk) {
+  const int first = max(chunk, nself);
+  return ncol <= first ? 1 : 1 + (ncol - first + chunk - 1) / chunk;
 }
 
 __global__ void k_item_counts(int32_t nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ count,
-                              const int32_t *__restrict__ colOff, int32_t *__restrict__ nitems,
+                              const int32_t *__restrict__ colOff, int chunk, int32_t *__restrict__ nitems,
                               int32_t *__restrict__ nextra) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nleaf) return;
   const int L = leaves[q];
-  const int k = chunks_of(colOff[L + 1] - colOff[L], count[L]);
+  const int k = chunks_of(colOff[L + 1] - colOff[L], count[L], chunk);
   nitems[q] = k;
   nextra[q] = (k - 1) * 3 * count[L];
 }
 
 __global__ void k_item_fill(int32_t nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ count,
-                            const int32_t *__restrict__ colOff, const int32_t *__restrict__ itemOff,
+                            const int32_t *__restrict__ colOff, int chunk, const int32_t *__restrict__ itemOff,
                             const int32_t *__restrict__ extraOff, int4 *__restrict__ items) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nleaf) return;
   const int L = leaves[q];
   const int cb = colOff[L], ce = colOff[L + 1], nA = count[L];
-  const int k = chunks_of(ce - cb, nA);
-  const int first = max(kChunk, nA);
+  const int k = chunks_of(ce - cb, nA, chunk);
+  const int first = max(chunk, nA);
   int o = itemOff[q];
   items[o] = make_int4(L, cb, min(ce, cb + first), -1);
   for (int j = 1; j < k; ++j) {
-    const int c0 = cb + first + (j - 1) * kChunk;
-    items[o + j] = make_int4(L, c0, min(ce, c0 + kChunk), extraOff[q] + (j - 1) * 3 * nA);
+    const int c0 = cb + first + (j - 1) * chunk;
+    items[o + j] = make_int4(L, c0, min(ce, c0 + chunk), extraOff[q] + (j - 1) * 3 * nA);
   }
 }
 
@@ -733,8 +737,9 @@ int p2p_prepare(fmm_ctx *c) {
   int32_t *icnt = cnt, *ecnt = ptr<int32_t>(c->flag);  // free scratch of >= nleaf + 1
   AMFMM_CUDA(c, cudaMemsetAsync(icnt + nleaf, 0, sizeof(int32_t), st));
   AMFMM_CUDA(c, cudaMemsetAsync(ecnt + nleaf, 0, sizeof(int32_t), st));
+  const int chunk = fp32 ? kChunk32 : kChunk64;
   k_item_counts<<<grid_for(nleaf, 256), 256, 0, st>>>(nleaf, ptr<int32_t>(c->leaves), ptr<int32_t>(c->count),
-                                                      colOff, icnt, ecnt);
+                                                      colOff, chunk, icnt, ecnt);
   AMFMM_TRY(launched(c, "p2p_item_counts"));
   AMFMM_TRY(exclusive_scan_i32(c, icnt, itemOff, nleaf + 1, itot));
   AMFMM_TRY(exclusive_scan_i32(c, ecnt, extraOff, nleaf + 1, etot));
@@ -766,10 +771,11 @@ int p2p_prepare(fmm_ctx *c) {
   AMFMM_TRY(ensure<int4>(c, c->p2p_items, nitem + 1));
   AMFMM_TRY(ensure<double>(c, c->p2p_extra, nextra + 1));
   k_item_fill<<<grid_for(nleaf, 256), 256, 0, st>>>(nleaf, ptr<int32_t>(c->leaves), ptr<int32_t>(c->count), colOff,
-                                                    itemOff, extraOff, ptr<int4>(c->p2p_items));
+                                                    chunk, itemOff, extraOff, ptr<int4>(c->p2p_items));
   AMFMM_TRY(launched(c, "p2p_item_fill"));
   // FP64: the items largest first (the pair sort's buffers are free here).
-  // (The FP32 form gains less from the shorter tail than the sort costs.)
+  // (In the FP32 form the leaf order's cache sharing is worth more than a
+  // shorter tail.)
   c->p2p_order = -1;
   if (!fp32 && nitem > 1) {
     AMFMM_TRY(ensure<uint32_t>(c, c->pkey[0], nitem));

@@ -417,9 +417,9 @@ _CHUNK_REF = {}
 def test_long_column_streams_are_split(precision):
     """At a small opening angle every leaf sums directly with most others, so
     its column stream runs to tens of thousands of bodies and is cut into
-    chunks of at most 4,096 columns handled by separate warps (the later chunks'
-    A-side partials are added in chunk order afterwards).  The accelerations
-    must still match the oracle."""
+    chunks (at most 2,048 columns in FP64, 4,096 in FP32) handled by separate
+    warps (the later chunks' A-side partials are added in chunk order
+    afterwards).  The accelerations must still match the oracle."""
     b = ics.uniform_cube(40000, seed=12)
     s, a = _solve(b, theta=0.05, precision=precision)
     st = s.stats()
