@@ -53,11 +53,11 @@ M2L_FLOPS_IN_REDUCE_FP64 = 32
 WORK_PER_M2L_PAIR = 295
 # DRAM traffic of the dominant kernel per unit it processes, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of k_p2p<double, 16>
-# on a Plummer sphere of N = 262,144 (theta = 0.5, TC): 118,164,736 B read and
-# 204,189,184 B written for 115,126,406 body pairs.  Scaled by the body pairs
+# on a Plummer sphere of N = 262,144 (theta = 0.5, TC): 137,841,920 B read and
+# 215,840,000 B written for 115,126,406 body pairs.  Scaled by the body pairs
 # of the launch timed (the traffic grows with them: column stream, B-side
 # partial slots and near-field sums are all per pair or per body).
-TRAFFIC_PER_UNIT = {("p2p", "fp64"): (118164736 + 204189184) / 115126406}
+TRAFFIC_PER_UNIT = {("p2p", "fp64"): (137841920 + 215840000) / 115126406}
 P2P_FLOPS_PER_BODY_PAIR = 25
 ORACLE_SAMPLE_N = 131072      # single-core oracle sample (bodies)
 REFERENCE_N = 262144          # bodies per step of the reference arm (all cores)
