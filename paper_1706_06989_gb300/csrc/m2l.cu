@@ -42,7 +42,10 @@
 namespace amfmm {
 namespace {
 
-constexpr int kBlock = 128;
+// threads per block of the FP64 pair kernel (Plummer, FP64: 256 against 128
+// took 6.90 against 7.17 ms at N = 1M, 27.6 against 28.7 ms at 4M; 512 was
+// slower)
+constexpr int kBlock = 256;
 constexpr int kCell32 = 24;    // floats per cell in the mixed form's copy (raw moments)
 constexpr int kCell32TF = 20;  // the same with trace-free moments (unsoftened UC and TC)
 constexpr int kQOh = 16;     // doubles per cell of the FP64 form's quadrupole and octupole per mass
@@ -677,7 +680,7 @@ __global__ void k_inverse(int64_t E, const uint32_t *__restrict__ sval, int32_t 
 // that meet scale factors and the pad are never read.  The partials of a
 // coefficient are then added by one lane in a fixed order (phase, then
 // lane).
-constexpr int kRedWarps = 8;
+constexpr int kRedWarps = 4;  // warps (cells) per block (reduce stage 2.51 against 2.55 ms with 8 at N = 1M)
 constexpr int kRedPhases = 3;   // loads per period
 constexpr int kRedPeriods = 2;  // periods per loop trip: six loads in flight
 
