@@ -88,8 +88,8 @@ def test_plummer_2000_matches_oracle(variant):
         assert tb <= 1e-13
 
 
-@pytest.mark.parametrize("k", [-90, 90])
-def test_fp64_far_from_unit_scale(k):
+@pytest.mark.parametrize("k,variant", [(-90, "TC"), (90, "TC"), (-90, "UC"), (90, "TCO")])
+def test_fp64_far_from_unit_scale(k, variant):
     """Positions scaled by 2^k (masses unchanged): the FP64 path keeps its
     1e-12 parity against the oracle, which takes the same scaled inputs.
     Morton keys, tree and lists are unchanged by a power-of-two scale, and
@@ -100,16 +100,32 @@ def test_fp64_far_from_unit_scale(k):
     b0 = ics.plummer(2000, seed=9)
     f = np.ldexp(1.0, k)
     b = ics.Bodies(b0.x * f, b0.y * f, b0.z * f, b0.m)
-    s, got = _solve(b)
+    s, got = _solve(b, variant=variant)
     o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25)
     _compare_lists(s, o)
-    rel = _rel_dev(got, o.accel("TC"))
+    rel = _rel_dev(got, o.accel(variant))
     assert rel.max() <= 1e-12, rel.max()
     # the same lists as the unscaled system, and accelerations 2^(-2k) times its own
-    s0, got0 = _solve(b0)
+    s0, got0 = _solve(b0, variant=variant)
     assert s0.stats().n_m2l == s.stats().n_m2l and s0.stats().p2p_body_pairs == s.stats().p2p_body_pairs
     rel0 = _rel_dev(np.ldexp(got, 2 * k), got0)
     assert rel0.max() <= 1e-13, rel0.max()
+
+
+@pytest.mark.parametrize("k", [-10, 10])
+def test_mixed_away_from_unit_scale(k):
+    """The mixed form on a Plummer sphere scaled by 2^k (masses unchanged):
+    its FP32 terms stay well inside the FP32 range, the lists (decided in
+    FP64, with the FP32 filter in front) stay bit-exact, and the rms force
+    deviation from the oracle stays within the mixed form's bound."""
+    b0 = ics.plummer(2000, seed=10)
+    f = np.ldexp(1.0, k)
+    b = ics.Bodies(b0.x * f, b0.y * f, b0.z * f, b0.m)
+    s, got = _solve(b, precision="mixed")
+    o = oracle.Oracle(b.x, b.y, b.z, b.m, 0.5, 25)
+    _compare_lists(s, o)
+    dev = _rel_dev(got, o.accel("TC"))
+    assert np.sqrt(np.mean(dev ** 2)) <= 1e-6
 
 
 def test_moments_match_definition():
